@@ -1,0 +1,515 @@
+/*
+ * simt_oracle.c - plain CPU oracle for the SIMT race/barrier checker.
+ *
+ * TEST INFRASTRUCTURE ONLY (see simt_oracle.h): used by tests, the smoke check and
+ * the benchmark's CPU baseline; never by the product path.
+ *
+ * Structure mirrors the definitions, not any GPU design:
+ *   run_program      - launches in order over one arena (Sec. 2: implicit sync at the
+ *                      end of each kernel call; Fig. 1 lines 33-34)
+ *   run_block        - one thread block: rounds, barrier resolution, step budget
+ *   exec_one         - one instruction of one thread
+ *   finish_epoch     - race check of the accesses since the last barrier (Sec. 3.1:
+ *                      pairwise definition; the history is cleared at the barrier)
+ *   resolve          - barrier check at the point where no thread can run
+ *                      (Sec. 3 "Barrier synchronization"; Sec. 3.1 deadlock paragraph)
+ */
+#include "simt_oracle.h"
+
+#include <pthread.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_CODE 4096u
+#define ORC_MAX_BDIM 1024u
+#define ORC_MAX_SHMEM 12288u
+#define ORC_DEFAULT_BUDGET (1u << 24)
+
+enum { ST_RUN = 0, ST_WAIT = 1, ST_EXIT = 2 };
+enum { K_R = 0, K_W = 1, K_A = 2 };
+
+static char g_err[256];
+const char* orc_last_error(void) { return g_err; }
+
+/* ------------------------------------------------------------ growable arrays */
+typedef struct { orc_report* v; uint64_t n, cap; } rep_vec;
+typedef struct { uint32_t addr, tid, kind, pc; } access_t;
+typedef struct { access_t* v; uint64_t n, cap; } acc_vec;
+typedef struct { int32_t addr, val; } store_t;
+typedef struct { store_t* v; uint64_t n, cap; } st_vec;
+
+static void* xrealloc(void* p, size_t bytes) {
+  void* q = realloc(p, bytes ? bytes : 1);
+  if (!q) { fprintf(stderr, "oracle: out of memory\n"); abort(); }
+  return q;
+}
+static void rep_push(rep_vec* r, orc_report x) {
+  if (r->n == r->cap) { r->cap = r->cap ? 2 * r->cap : 64; r->v = xrealloc(r->v, r->cap * sizeof(*r->v)); }
+  r->v[r->n++] = x;
+}
+static void acc_push(acc_vec* r, access_t x) {
+  if (r->n == r->cap) { r->cap = r->cap ? 2 * r->cap : 256; r->v = xrealloc(r->v, r->cap * sizeof(*r->v)); }
+  r->v[r->n++] = x;
+}
+static void st_push(st_vec* r, int32_t addr, int32_t val) {
+  if (r->n == r->cap) { r->cap = r->cap ? 2 * r->cap : 256; r->v = xrealloc(r->v, r->cap * sizeof(*r->v)); }
+  r->v[r->n].addr = addr; r->v[r->n].val = val; r->n++;
+}
+
+/* int32 two's-complement helpers (conversions written out, no signed overflow) */
+static int32_t as_i32(uint32_t x) { return (x & 0x80000000u) ? -(int32_t)(~x) - 1 : (int32_t)x; }
+static int32_t add32(int32_t a, int32_t b) { return as_i32((uint32_t)a + (uint32_t)b); }
+static int32_t sub32(int32_t a, int32_t b) { return as_i32((uint32_t)a - (uint32_t)b); }
+static int32_t mul32(int32_t a, int32_t b) { return as_i32((uint32_t)a * (uint32_t)b); }
+
+/* ------------------------------------------------------------ one block */
+typedef struct {
+  const orc_program* P;
+  uint32_t prog_idx, launch_idx;
+  const orc_launch* L;
+  const orc_opts* O;
+  uint32_t budget;
+  /* outputs (private to the host thread running the block) */
+  rep_vec* reps;
+  uint64_t thread_instrs, shared_accesses, rounds;
+  uint32_t status;               /* ORC_ST_* seen in this launch */
+  /* inter-block conflict bookkeeping (serial mode only) */
+  int32_t* writer; int32_t* reader; uint64_t conflicts;
+} launch_ctx;
+
+typedef struct {
+  launch_ctx* C;
+  uint32_t block, n, nwarps, shw;
+  uint32_t* pc; uint8_t* st; uint32_t* wpc;
+  int32_t* regs;                 /* [n][16] */
+  int32_t* sh;                   /* shared array of this block */
+  uint32_t* err_cnt; uint32_t* err_min;   /* per pc, current epoch */
+  uint8_t err_any;
+  acc_vec acc;                   /* accesses of the current epoch */
+  st_vec sst, gst, ats;          /* deferred shared stores, global stores, atomics (round) */
+  uint32_t epoch;
+  int deferred;                  /* 1 = lockstep rounds, 0 = immediate (sequential) */
+} block_t;
+
+static int32_t reg_read(block_t* B, uint32_t t, uint32_t r) {
+  return r == ORC_RZ ? 0 : B->regs[t * 16 + r];
+}
+static void reg_write(block_t* B, uint32_t t, uint32_t r, int32_t v) {
+  if (r != ORC_RZ) B->regs[t * 16 + r] = v;
+}
+static void note_err(block_t* B, uint32_t pc, uint32_t t) {
+  B->err_cnt[pc]++;
+  if (t < B->err_min[pc]) B->err_min[pc] = t;
+  B->err_any = 1;
+}
+static void note_global(block_t* B, int32_t addr, int is_write) {
+  launch_ctx* C = B->C;
+  if (!C->writer) return;
+  int32_t me = (int32_t)B->block;
+  if (is_write) {
+    if (C->writer[addr] != -1 && C->writer[addr] != me) C->conflicts++;
+    if (C->reader[addr] != -1 && C->reader[addr] != me) C->conflicts++;
+    C->writer[addr] = me;
+  } else {
+    if (C->writer[addr] != -1 && C->writer[addr] != me) C->conflicts++;
+    if (C->reader[addr] == -1) C->reader[addr] = me;
+    else if (C->reader[addr] != me) C->reader[addr] = -2;
+  }
+}
+
+static int32_t alu(block_t* B, uint32_t op, int32_t va, int32_t vb, uint32_t pc, uint32_t t) {
+  switch (op) {
+    case ORC_MOV: return vb;
+    case ORC_ADD: return add32(va, vb);
+    case ORC_SUB: return sub32(va, vb);
+    case ORC_MUL: return mul32(va, vb);
+    case ORC_DIV:
+      if (vb == 0) { note_err(B, pc, t); return 0; }
+      if (va == INT32_MIN && vb == -1) return INT32_MIN;
+      return va / vb;                          /* C99: truncation toward zero */
+    case ORC_REM:
+      if (vb == 0) { note_err(B, pc, t); return 0; }
+      if (va == INT32_MIN && vb == -1) return 0;
+      return va % vb;                          /* sign follows the dividend */
+    case ORC_AND: return va & vb;
+    case ORC_OR:  return va | vb;
+    case ORC_XOR: return va ^ vb;
+    case ORC_SHL: return as_i32((uint32_t)va << ((uint32_t)vb & 31u));
+    case ORC_SHR: {
+      uint32_t s = (uint32_t)vb & 31u;
+      return va < 0 ? ~((~va) >> s) : (va >> s);   /* arithmetic shift written out */
+    }
+    case ORC_MIN: return va < vb ? va : vb;
+    case ORC_MAX: return va > vb ? va : vb;
+    case ORC_SLT: return va < vb;
+    case ORC_SLE: return va <= vb;
+    case ORC_SEQ: return va == vb;
+    case ORC_SNE: return va != vb;
+  }
+  return 0;
+}
+
+/* which operand fields an opcode reads (unused fields are never decoded) */
+static int uses_d(uint32_t b) { return (b >= ORC_MOV && b <= ORC_SNE) || b == ORC_S2R || b == ORC_LDG || b == ORC_LDS; }
+static int uses_a(uint32_t b) {
+  return (b >= ORC_ADD && b <= ORC_SNE) || b == ORC_LDG || b == ORC_STG || b == ORC_LDS ||
+         b == ORC_STS || b == ORC_ATOMS || b == ORC_BRZ || b == ORC_BRNZ;
+}
+static int uses_b(uint32_t op) {
+  uint32_t b = op & 0x7Fu;
+  return ((b >= ORC_MOV && b <= ORC_SNE) && !(op & ORC_BIMM)) || b == ORC_STG || b == ORC_STS || b == ORC_ATOMS;
+}
+
+/* execute the instruction at pc for thread t (pc == ncode is the implicit EXIT) */
+static void exec_one(block_t* B, uint32_t t, uint32_t pc) {
+  const orc_program* P = B->C->P;
+  const orc_launch* L = B->C->L;
+  B->C->thread_instrs++;
+  if (pc >= P->ncode) { B->st[t] = ST_EXIT; return; }
+  uint32_t w = P->code[pc].op_d_a_b;
+  int32_t imm = P->code[pc].imm;
+  uint32_t op = w & 0xFFu, base = op & 0x7Fu;
+  uint32_t d = (w >> 8) & 0xFFu, a = (w >> 16) & 0xFFu, b = (w >> 24) & 0xFFu;
+  int32_t va = uses_a(base) ? reg_read(B, t, a) : 0;
+  int32_t vb = (op & ORC_BIMM) ? imm : (uses_b(op) ? reg_read(B, t, b) : 0);
+  uint32_t next = pc + 1;
+
+  if (base >= ORC_MOV && base <= ORC_SNE) {
+    reg_write(B, t, d, alu(B, base, va, vb, pc, t));
+  } else switch (base) {
+    case ORC_S2R: {
+      int32_t v = 0;
+      switch (imm) {
+        case 0: v = (int32_t)t; break;
+        case 1: v = (int32_t)B->block; break;
+        case 2: v = (int32_t)L->block_dim; break;
+        case 3: v = (int32_t)L->grid; break;
+        case 4: v = 32; break;
+      }
+      reg_write(B, t, d, v);
+      break;
+    }
+    case ORC_LDS: {
+      int32_t addr = add32(va, imm), v = 0;
+      if (addr < 0 || (uint32_t)addr >= B->shw) note_err(B, pc, t);
+      else {
+        v = B->sh[addr];                   /* deferred writes: pre-round value */
+        acc_push(&B->acc, (access_t){(uint32_t)addr, t, K_R, pc});
+      }
+      reg_write(B, t, d, v);
+      break;
+    }
+    case ORC_STS: case ORC_ATOMS: {
+      int32_t addr = add32(va, imm);
+      if (addr < 0 || (uint32_t)addr >= B->shw) { note_err(B, pc, t); break; }
+      acc_push(&B->acc, (access_t){(uint32_t)addr, t, base == ORC_STS ? K_W : K_A, pc});
+      if (base == ORC_STS) {
+        if (B->deferred) st_push(&B->sst, addr, vb); else B->sh[addr] = vb;
+      } else {
+        if (B->deferred) st_push(&B->ats, addr, vb); else B->sh[addr] = add32(B->sh[addr], vb);
+      }
+      break;
+    }
+    case ORC_LDG: {
+      int32_t addr = add32(va, imm), v = 0;
+      if (addr < 0 || (uint64_t)addr >= P->arena_words) note_err(B, pc, t);
+      else { v = P->arena[addr]; note_global(B, addr, 0); }
+      reg_write(B, t, d, v);
+      break;
+    }
+    case ORC_STG: {
+      int32_t addr = add32(va, imm);
+      if (addr < 0 || (uint64_t)addr >= P->arena_words) { note_err(B, pc, t); break; }
+      note_global(B, addr, 1);
+      if (B->deferred) st_push(&B->gst, addr, vb); else P->arena[addr] = vb;
+      break;
+    }
+    case ORC_BRA: next = (uint32_t)imm; break;
+    case ORC_BRZ: if (va == 0) next = (uint32_t)imm; break;
+    case ORC_BRNZ: if (va != 0) next = (uint32_t)imm; break;
+    case ORC_BAR: B->st[t] = ST_WAIT; B->wpc[t] = pc; break;
+    case ORC_EXIT: B->st[t] = ST_EXIT; break;
+  }
+  B->pc[t] = next;
+}
+
+/* one lockstep round: every warp with a runnable thread issues its lowest pc */
+static void exec_round(block_t* B) {
+  B->sst.n = B->gst.n = B->ats.n = 0;
+  for (uint32_t w = 0; w < B->nwarps; ++w) {
+    uint32_t lo = 32 * w, hi = lo + 32 < B->n ? lo + 32 : B->n;
+    uint32_t p = UINT32_MAX;
+    for (uint32_t t = lo; t < hi; ++t)
+      if (B->st[t] == ST_RUN && B->pc[t] < p) p = B->pc[t];
+    if (p == UINT32_MAX) continue;
+    for (uint32_t t = lo; t < hi; ++t)
+      if (B->st[t] == ST_RUN && B->pc[t] == p) exec_one(B, t, p);
+  }
+  /* stores in ascending tid order (the lists were filled in that order), then atomics */
+  for (uint64_t i = 0; i < B->sst.n; ++i) B->sh[B->sst.v[i].addr] = B->sst.v[i].val;
+  for (uint64_t i = 0; i < B->gst.n; ++i) B->C->P->arena[B->gst.v[i].addr] = B->gst.v[i].val;
+  for (uint64_t i = 0; i < B->ats.n; ++i)
+    B->sh[B->ats.v[i].addr] = add32(B->sh[B->ats.v[i].addr], B->ats.v[i].val);
+}
+
+static int cmp_access(const void* x, const void* y) {
+  const access_t* p = x; const access_t* q = y;
+  if (p->addr != q->addr) return p->addr < q->addr ? -1 : 1;
+  if (p->tid != q->tid) return p->tid < q->tid ? -1 : 1;
+  if (p->kind != q->kind) return p->kind < q->kind ? -1 : 1;
+  if (p->pc != q->pc) return p->pc < q->pc ? -1 : 1;
+  return 0;
+}
+
+static void emit(block_t* B, uint32_t kind, uint32_t a, uint32_t b, uint32_t c) {
+  orc_report r = {kind, B->C->prog_idx, B->C->launch_idx, B->block, B->epoch, a, b, c};
+  rep_push(B->C->reps, r);
+}
+
+/* race check of one barrier interval: the pairwise definition of Sec. 3.1, then
+ * error records of the interval; the access history is then cleared */
+static void finish_epoch(block_t* B) {
+  const orc_program* P = B->C->P;
+  B->C->shared_accesses += B->acc.n;
+  if (B->C->O->check_races && B->acc.n) {
+    qsort(B->acc.v, B->acc.n, sizeof(access_t), cmp_access);
+    uint64_t i = 0;
+    while (i < B->acc.n) {
+      uint64_t j = i;
+      while (j < B->acc.n && B->acc.v[j].addr == B->acc.v[i].addr) ++j;
+      uint32_t cls = 0, t1 = UINT32_MAX, t2 = UINT32_MAX, pclo = UINT32_MAX, pchi = 0;
+      for (uint64_t x = i; x < j; ++x) {
+        const access_t* p = &B->acc.v[x];
+        if (p->pc < pclo) pclo = p->pc;
+        if (p->pc > pchi) pchi = p->pc;
+        for (uint64_t y = x + 1; y < j; ++y) {
+          const access_t* q = &B->acc.v[y];
+          if (p->tid == q->tid) continue;
+          uint32_t k1 = p->kind, k2 = q->kind, bit = 0;
+          if (k1 == K_W && k2 == K_W) bit = ORC_CLS_WW;
+          else if ((k1 == K_W && k2 == K_R) || (k1 == K_R && k2 == K_W)) bit = ORC_CLS_WR;
+          else if ((k1 == K_W && k2 == K_A) || (k1 == K_A && k2 == K_W)) bit = ORC_CLS_WA;
+          else if ((k1 == K_A && k2 == K_R) || (k1 == K_R && k2 == K_A)) bit = ORC_CLS_AR;
+          if (!bit) continue;                     /* read-read, atomic-atomic */
+          cls |= bit;
+          uint32_t lo = p->tid < q->tid ? p->tid : q->tid, hi = p->tid ^ q->tid ^ lo;
+          if (lo < t1 || (lo == t1 && hi < t2)) { t1 = lo; t2 = hi; }
+        }
+      }
+      if (cls) emit(B, ORC_REP_RACE, B->acc.v[i].addr, (t1 << 16) | t2,
+                    (cls << 24) | (pclo << 12) | pchi);
+      i = j;
+    }
+  }
+  B->acc.n = 0;
+  if (B->err_any) {
+    for (uint32_t pc = 0; pc < P->ncode; ++pc) {
+      if (!B->err_cnt[pc]) continue;
+      uint32_t base = P->code[pc].op_d_a_b & 0x7Fu, kind;
+      if (base == ORC_LDS || base == ORC_STS || base == ORC_ATOMS) kind = ORC_REP_ERR_OOB_SHARED;
+      else if (base == ORC_LDG || base == ORC_STG) kind = ORC_REP_ERR_OOB_GLOBAL;
+      else kind = ORC_REP_ERR_DIV0;
+      emit(B, kind, pc, B->err_min[pc], B->err_cnt[pc]);
+      B->err_cnt[pc] = 0; B->err_min[pc] = UINT32_MAX;
+    }
+    B->err_any = 0;
+  }
+}
+
+/* returns 1 when the block is finished (done, deadlocked or out of budget) */
+static int resolve(block_t* B) {
+  uint32_t nW = 0, nX = 0, pmin = UINT32_MAX, pmax = 0;
+  for (uint32_t t = 0; t < B->n; ++t) {
+    if (B->st[t] == ST_WAIT) {
+      ++nW;
+      if (B->wpc[t] < pmin) pmin = B->wpc[t];
+      if (B->wpc[t] > pmax) pmax = B->wpc[t];
+    } else if (B->st[t] == ST_EXIT) ++nX;
+  }
+  if (nW == 0) { finish_epoch(B); return 1; }
+  if (nX > 0) {            /* some thread will never reach the barrier the others wait at */
+    emit(B, ORC_REP_DEADLOCK, pmin, pmax, (nW << 16) | nX);
+    finish_epoch(B);
+    B->C->status |= ORC_ST_DEADLOCK;
+    return 1;
+  }
+  if (pmin != pmax)        /* all threads wait, but not at the same barrier instruction */
+    emit(B, ORC_REP_DIVERGENCE, pmin, pmax, nW << 16);
+  finish_epoch(B);
+  B->epoch++;
+  for (uint32_t t = 0; t < B->n; ++t) if (B->st[t] == ST_WAIT) B->st[t] = ST_RUN;
+  return 0;
+}
+
+static void run_block(launch_ctx* C, uint32_t block) {
+  const orc_program* P = C->P;
+  const orc_launch* L = C->L;
+  block_t B;
+  memset(&B, 0, sizeof(B));
+  B.C = C; B.block = block; B.n = L->block_dim; B.nwarps = (L->block_dim + 31) / 32;
+  B.shw = L->shmem_words;
+  B.deferred = C->O->schedule == 0;
+  B.pc = malloc(B.n * sizeof(uint32_t)); B.st = malloc(B.n); B.wpc = malloc(B.n * sizeof(uint32_t));
+  B.regs = calloc((size_t)B.n * 16, sizeof(int32_t));
+  B.sh = calloc(B.shw ? B.shw : 1, sizeof(int32_t));          /* shared memory starts at zero */
+  B.err_cnt = calloc(P->ncode + 1, sizeof(uint32_t));
+  B.err_min = malloc((P->ncode + 1) * sizeof(uint32_t));
+  for (uint32_t i = 0; i <= P->ncode; ++i) B.err_min[i] = UINT32_MAX;
+  uint32_t entry = P->kernel_entry[L->kernel];
+  for (uint32_t t = 0; t < B.n; ++t) {
+    B.pc[t] = entry; B.st[t] = ST_RUN;
+    for (uint32_t r = 0; r < L->nparams; ++r) B.regs[t * 16 + r] = L->params[r];
+  }
+  uint64_t rounds = 0;
+  for (;;) {
+    uint32_t nrun = 0, runpc = UINT32_MAX;
+    for (uint32_t t = 0; t < B.n; ++t)
+      if (B.st[t] == ST_RUN) { ++nrun; if (B.pc[t] < runpc) runpc = B.pc[t]; }
+    if (nrun == 0) {
+      if (resolve(&B)) break;
+      continue;
+    }
+    if (rounds >= C->budget) {
+      emit(&B, ORC_REP_STEP_LIMIT, (uint32_t)rounds, nrun, runpc);
+      finish_epoch(&B);
+      C->status |= ORC_ST_STEP_LIMIT;
+      break;
+    }
+    if (B.deferred) {
+      exec_round(&B);
+      ++rounds;
+    } else {
+      /* thread-sequential: each thread alone until it waits or exits */
+      for (uint32_t t = 0; t < B.n && rounds < C->budget; ++t)
+        while (B.st[t] == ST_RUN && rounds < C->budget) { exec_one(&B, t, B.pc[t]); ++rounds; }
+    }
+  }
+  C->rounds += rounds;
+  free(B.pc); free(B.st); free(B.wpc); free(B.regs); free(B.sh);
+  free(B.err_cnt); free(B.err_min); free(B.acc.v); free(B.sst.v); free(B.gst.v); free(B.ats.v);
+}
+
+/* ------------------------------------------------------------ validation */
+static int validate(const orc_program* P, uint32_t idx) {
+  if (!P->code || P->ncode == 0 || P->ncode > ORC_MAX_CODE) {
+    snprintf(g_err, sizeof g_err, "program %u: code size %u outside 1..%u", idx, P->ncode, ORC_MAX_CODE); return -1; }
+  if (P->nkernels == 0 || !P->kernel_entry) { snprintf(g_err, sizeof g_err, "program %u: no kernels", idx); return -1; }
+  for (uint32_t k = 0; k < P->nkernels; ++k)
+    if (P->kernel_entry[k] >= P->ncode) { snprintf(g_err, sizeof g_err, "program %u: kernel %u entry out of range", idx, k); return -1; }
+  for (uint32_t pc = 0; pc < P->ncode; ++pc) {
+    uint32_t w = P->code[pc].op_d_a_b, op = w & 0xFFu, base = op & 0x7Fu;
+    uint32_t d = (w >> 8) & 0xFFu, a = (w >> 16) & 0xFFu, b = (w >> 24) & 0xFFu;
+    int32_t imm = P->code[pc].imm;
+    int alu_op = base >= ORC_MOV && base <= ORC_SNE;
+    if (base < ORC_MOV || base > ORC_EXIT || (op & 0x40u) || ((op & ORC_BIMM) && !alu_op)) {
+      snprintf(g_err, sizeof g_err, "program %u pc %u: bad opcode 0x%x", idx, pc, op); return -1; }
+    int need_b = uses_b(op);
+    if ((uses_d(base) && d >= 16 && d != ORC_RZ) || (uses_a(base) && a >= 16 && a != ORC_RZ) ||
+        (need_b && b >= 16 && b != ORC_RZ)) {
+      snprintf(g_err, sizeof g_err, "program %u pc %u: bad register", idx, pc); return -1; }
+    if ((base == ORC_BRA || base == ORC_BRZ || base == ORC_BRNZ) && (imm < 0 || (uint32_t)imm > P->ncode)) {
+      snprintf(g_err, sizeof g_err, "program %u pc %u: branch target out of range", idx, pc); return -1; }
+    if (base == ORC_S2R && (imm < 0 || imm > 4)) {
+      snprintf(g_err, sizeof g_err, "program %u pc %u: bad special register", idx, pc); return -1; }
+  }
+  for (uint32_t l = 0; l < P->nlaunches; ++l) {
+    const orc_launch* L = &P->launches[l];
+    if (L->kernel >= P->nkernels || L->block_dim == 0 || L->block_dim > ORC_MAX_BDIM || L->grid == 0 ||
+        L->shmem_words > ORC_MAX_SHMEM || L->nparams > 4) {
+      snprintf(g_err, sizeof g_err, "program %u launch %u: bad configuration", idx, l); return -1; }
+  }
+  if (P->arena_words > 0x7FFFFFFFull || (P->arena_words && !P->arena)) {
+    snprintf(g_err, sizeof g_err, "program %u: bad arena", idx); return -1; }
+  return 0;
+}
+
+/* ------------------------------------------------------------ launches / programs */
+typedef struct { launch_ctx* C; uint32_t b0, b1; } worker_arg;
+static void* worker(void* p) {
+  worker_arg* w = p;
+  for (uint32_t b = w->b0; b < w->b1; ++b) run_block(w->C, b);
+  return NULL;
+}
+
+static int cmp_report(const void* x, const void* y) {
+  const uint32_t* p = x; const uint32_t* q = y;
+  static const int order[8] = {1, 2, 3, 4, 0, 5, 6, 7};   /* prog, launch, block, epoch, kind, a, b, c */
+  for (int i = 0; i < 8; ++i) {
+    uint32_t u = p[order[i]], v = q[order[i]];
+    if (u != v) return u < v ? -1 : 1;
+  }
+  return 0;
+}
+
+int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc_result* res) {
+  memset(res, 0, sizeof(*res));
+  g_err[0] = 0;
+  for (uint32_t p = 0; p < nprogs; ++p) if (validate(&progs[p], p)) return -1;
+  orc_opts O = *opts;
+  uint32_t budget = O.round_budget ? O.round_budget : ORC_DEFAULT_BUDGET;
+  uint32_t nth = O.nthreads ? O.nthreads : 1;
+  res->status = calloc(nprogs ? nprogs : 1, sizeof(uint32_t));
+  rep_vec all = {0};
+  for (uint32_t p = 0; p < nprogs; ++p) {
+    const orc_program* P = &progs[p];
+    int32_t *writer = NULL, *reader = NULL;
+    if (O.check_interblock && nth == 1 && P->arena_words) {
+      writer = malloc(P->arena_words * sizeof(int32_t));
+      reader = malloc(P->arena_words * sizeof(int32_t));
+    }
+    for (uint32_t l = 0; l < P->nlaunches; ++l) {
+      const orc_launch* L = &P->launches[l];
+      uint32_t nblocks = L->grid;
+      if (O.max_blocks && O.max_blocks < nblocks) nblocks = O.max_blocks;
+      if (writer) {
+        memset(writer, 0xFF, P->arena_words * sizeof(int32_t));
+        memset(reader, 0xFF, P->arena_words * sizeof(int32_t));
+      }
+      uint32_t nw = nth < nblocks ? nth : nblocks;
+      launch_ctx* ctx = calloc(nw, sizeof(launch_ctx));
+      rep_vec* reps = calloc(nw, sizeof(rep_vec));
+      for (uint32_t i = 0; i < nw; ++i) {
+        ctx[i].P = P; ctx[i].prog_idx = p; ctx[i].launch_idx = l; ctx[i].L = L; ctx[i].O = &O;
+        ctx[i].budget = budget; ctx[i].reps = &reps[i]; ctx[i].writer = writer; ctx[i].reader = reader;
+      }
+      if (nw == 1) {
+        for (uint32_t b = 0; b < nblocks; ++b) run_block(&ctx[0], b);
+      } else {
+        pthread_t* th = malloc(nw * sizeof(pthread_t));
+        worker_arg* wa = malloc(nw * sizeof(worker_arg));
+        for (uint32_t i = 0; i < nw; ++i) {
+          wa[i].C = &ctx[i];
+          wa[i].b0 = (uint32_t)((uint64_t)nblocks * i / nw);
+          wa[i].b1 = (uint32_t)((uint64_t)nblocks * (i + 1) / nw);
+          pthread_create(&th[i], NULL, worker, &wa[i]);
+        }
+        for (uint32_t i = 0; i < nw; ++i) pthread_join(th[i], NULL);
+        free(th); free(wa);
+      }
+      uint32_t st = 0;
+      for (uint32_t i = 0; i < nw; ++i) {
+        st |= ctx[i].status;
+        res->thread_instrs += ctx[i].thread_instrs;
+        res->shared_accesses += ctx[i].shared_accesses;
+        res->rounds += ctx[i].rounds;
+        res->interblock_conflicts += ctx[i].conflicts;
+        for (uint64_t k = 0; k < reps[i].n; ++k) rep_push(&all, reps[i].v[k]);
+        free(reps[i].v);
+      }
+      free(reps); free(ctx);
+      res->status[p] |= st;
+      if (st & (ORC_ST_DEADLOCK | ORC_ST_STEP_LIMIT)) break;   /* later launches skipped */
+    }
+    free(writer); free(reader);
+  }
+  qsort(all.v, all.n, sizeof(orc_report), cmp_report);
+  res->reports = all.v;
+  res->nreports = all.n;
+  return 0;
+}
+
+void orc_free(orc_result* res) {
+  free(res->reports); free(res->status);
+  memset(res, 0, sizeof(*res));
+}
