@@ -1,0 +1,204 @@
+/*
+ * simtcheck.h - C ABI of the GB300 SIMT race and barrier checker (libsimtcheck.so).
+ *
+ * The library executes simulated CUDA-C kernels for many threads at once and checks
+ * them the way the paper's cudak tool does (Hathhorn, Becchi, Harrison, Procter,
+ * "Formal Semantics of Heterogeneous CUDA-C", SSV 2012):
+ *   - every kernel launch creates grid x blockDim threads with a per-block dynamic
+ *     shared array; launches of one program run in order over one global arena with
+ *     the implicit grid-wide synchronisation at the end of each kernel call
+ *     (Sec. 2; Sec. 3 "Threads and memory");
+ *   - every shared-memory access is logged and each barrier interval is checked for
+ *     races: two distinct threads, same location, no barrier in between, at least one
+ *     write (Sec. 3.1, first paragraph);
+ *   - every __syncthreads() is checked: threads of a block waiting at different barrier
+ *     instructions (divergence), or waiting while other threads have exited (deadlock,
+ *     Sec. 3.1, last paragraph; Sec. 3 "Barrier synchronization").
+ * Programs are given in a small int32 register IR instead of C source.
+ *
+ * Conventions for every entry point
+ *   - Return 0 on success or a negative SR_E_* code; the message of the last failure
+ *     of a context is returned by sr_last_error().  On SR_E_INVAL nothing was enqueued.
+ *   - Host buffers passed in are owned by the caller and only read (or, for fetch_*,
+ *     written) during the call.  Device memory is owned by the library: it is obtained
+ *     through the allocator given at sr_create (default: cudaMallocAsync on the stream
+ *     of the call) and released by sr_free_batch / sr_destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  run_and_check only
+ *     enqueues work; fetch_* and sr_batch_status synchronise the batch's stream.
+ *   - Races, deadlocks, divergent barriers, out-of-bounds accesses, division by zero and
+ *     the round budget are *reports* about the simulated program, never error codes.
+ *   - A context and its batches are not thread-safe: use one host thread per context.
+ *
+ * Instruction encoding (8 bytes): op_d_a_b = op | d << 8 | a << 16 | b << 24, imm.
+ *   op bits 0..5 opcode, bit 7 SR_BIMM (second ALU operand is imm instead of register b).
+ *   Registers r0..r15; 255 (SR_RZ) reads 0 and drops writes.  Word addresses.
+ *   MOV d,B | ADD..SNE d,a,B | S2R d,#sreg | LDG d,[a+imm] | STG [a+imm],b
+ *   LDS d,[a+imm] | STS [a+imm],b | ATOMS [a+imm],b (add, no return)
+ *   BRA #t | BRZ a,#t | BRNZ a,#t (absolute pcs in 0..ncode) | BAR | EXIT
+ *   At launch r0..r(nparams-1) hold the params, every other register 0; shared memory
+ *   starts zeroed; running past the last instruction exits the thread.
+ *
+ * Execution model (the paper leaves the scheduler open, Sec. 3 "Threads and memory"
+ * and Sec. 4; this library fixes one schedule so that results are reproducible):
+ * warps of 32 consecutive tids advance in rounds; in each round every warp with a
+ * runnable thread executes the lowest pc among its runnable threads for the threads at
+ * that pc; all loads of a round see the state before the round, then stores apply in
+ * ascending tid order, then atomic adds.  When no thread of a block can run the barrier
+ * is resolved: no waiting threads -> the block is done; waiting and exited threads ->
+ * DEADLOCK (the block stops and the program's later launches are skipped); waiting at
+ * different barrier pcs -> DIVERGENCE, then release; otherwise release.
+ */
+#ifndef SIMTCHECK_H
+#define SIMTCHECK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* opaque handles: a context (one CUDA device, options, allocator) and a loaded batch */
+typedef struct sr_ctx sr_ctx;
+typedef struct sr_batch sr_batch;
+
+/* ---------------------------------------------------------------- return codes */
+#define SR_OK 0
+#define SR_E_INVAL (-1)    /* bad argument or program (validation failure) */
+#define SR_E_NOMEM (-2)    /* device or host allocation failed */
+#define SR_E_CUDA (-3)     /* a CUDA call failed; see sr_last_error */
+#define SR_E_TIMEOUT (-4)  /* a device-side wait gave up (bounded spin) */
+#define SR_E_RANGE (-5)    /* destination buffer too small (size returned) */
+
+/* ---------------------------------------------------------------- IR opcodes */
+enum {
+  SR_OP_MOV = 1, SR_OP_ADD, SR_OP_SUB, SR_OP_MUL, SR_OP_DIV, SR_OP_REM, SR_OP_AND, SR_OP_OR,
+  SR_OP_XOR, SR_OP_SHL, SR_OP_SHR, SR_OP_MIN, SR_OP_MAX, SR_OP_SLT, SR_OP_SLE, SR_OP_SEQ,
+  SR_OP_SNE, SR_OP_S2R, SR_OP_LDG, SR_OP_STG, SR_OP_LDS, SR_OP_STS, SR_OP_ATOMS, SR_OP_BRA,
+  SR_OP_BRZ, SR_OP_BRNZ, SR_OP_BAR, SR_OP_EXIT
+};
+#define SR_BIMM 0x80u
+#define SR_RZ 0xFFu
+enum { SR_SREG_TID = 0, SR_SREG_BID, SR_SREG_BDIM, SR_SREG_GDIM, SR_SREG_WARPSIZE };
+
+#define SR_MAX_CODE 4096u          /* instructions per program (pcs fit in 12 bits) */
+#define SR_MAX_BLOCK_DIM 1024u     /* threads per block (tids fit in 10 bits) */
+#define SR_MAX_SHMEM_WORDS 12288u  /* 48 KB of simulated shared memory per block */
+
+/* ---------------------------------------------------------------- report records */
+enum {
+  SR_REP_RACE = 1,           /* a = word address, b = t1 << 16 | t2 (smallest conflicting
+                                pair, t1 < t2), c = class << 24 | pc_lo << 12 | pc_hi over all
+                                accesses to the word in the interval */
+  SR_REP_DIVERGENCE = 2,     /* a = lowest, b = highest barrier pc waited at, c = nwait << 16 */
+  SR_REP_DEADLOCK = 3,       /* a, b as above, c = nwait << 16 | nexited */
+  SR_REP_STEP_LIMIT = 4,     /* a = rounds executed, b = runnable threads, c = their lowest pc */
+  SR_REP_ERR_OOB_SHARED = 5, /* a = pc, b = lowest tid, c = thread executions in the interval */
+  SR_REP_ERR_OOB_GLOBAL = 6, /* same fields */
+  SR_REP_ERR_DIV0 = 7        /* same fields */
+};
+enum { SR_CLS_WW = 1, SR_CLS_WR = 2, SR_CLS_WA = 4, SR_CLS_AR = 8 };
+
+/* per-program status bits (sr_batch_status) */
+enum {
+  SR_ST_DEADLOCK = 1,        /* a block deadlocked; later launches were skipped */
+  SR_ST_STEP_LIMIT = 2,      /* a block ran out of rounds; later launches were skipped */
+  SR_ST_LOG_OVERFLOW = 4,    /* a block's access log exceeded its region: race check incomplete */
+  SR_ST_INTERNAL = 8         /* a device-side wait timed out: results of the program are invalid */
+};
+
+typedef struct { uint32_t op_d_a_b; int32_t imm; } sr_instr;
+
+typedef struct {
+  uint32_t kernel;           /* index into the program's kernel_entry */
+  uint32_t grid;             /* blocks, >= 1 */
+  uint32_t block_dim;        /* threads per block, 1..SR_MAX_BLOCK_DIM */
+  uint32_t shmem_words;      /* dynamic shared words per block, 0..SR_MAX_SHMEM_WORDS */
+  uint32_t nparams;          /* 0..4, loaded into r0.. */
+  int32_t params[4];
+} sr_launch;
+
+typedef struct {
+  const sr_instr* code; uint32_t ncode;           /* 1..SR_MAX_CODE instructions */
+  const uint32_t* kernel_entry; uint32_t nkernels;
+  const sr_launch* launches; uint32_t nlaunches;  /* run in order */
+  const int32_t* global_init; uint64_t global_words;  /* initial global arena (< 2^31 words) */
+} sr_program;
+
+/* one report; fetch_reports returns them sorted by (prog, launch, block, epoch, kind, a, b, c) */
+typedef struct { uint32_t kind, prog, launch, block, epoch, a, b, c; } sr_report;
+
+/* optional device allocator (e.g. a framework's caching allocator) */
+typedef struct {
+  void* (*alloc)(void* user, size_t bytes, void* stream);        /* NULL return = failure */
+  void (*release)(void* user, void* ptr, size_t bytes, void* stream);
+  void* user;
+} sr_allocator;
+
+enum { SR_MODE_PLAIN = 0,    /* one kernel launch per (program, launch) */
+       SR_MODE_BATCHED = 1   /* one persistent launch over every block of every program */ };
+
+typedef struct {
+  uint32_t check_races;      /* 1 = log + race check (default), 0 = interpreter + barrier check only */
+  uint32_t round_budget;     /* rounds per block before STEP_LIMIT; 0 = 1 << 24 (max 1 << 26) */
+  uint32_t mode;             /* SR_MODE_* */
+  uint32_t ctas_per_sm;      /* batched interpreter CTAs per SM; 0 = 1 */
+  uint32_t loop_log_records; /* log region (records per block) for kernels with loops; 0 = 65536 */
+  uint32_t check_ctas_per_sm;/* checker CTAs per SM; 0 = 2 */
+  uint32_t use_graph;        /* batched mode: capture run_and_check once, replay as a CUDA graph */
+  uint32_t profile;          /* record CUDA events between stages (sr_batch_stats) */
+  uint32_t spin_limit;       /* device wait iterations before SR_ST_INTERNAL; 0 = 1 << 26 */
+  uint32_t log_budget_mb;    /* device memory for access logs resident at once (launches are
+                                processed in waves that fit); 0 = min(96 GB, half the free memory) */
+  uint32_t report_cap;       /* initial report buffer (records); grown on demand; 0 = 1 << 20 */
+  const sr_allocator* allocator;  /* NULL = cudaMallocAsync / cudaFreeAsync */
+} sr_opts;
+
+typedef struct {
+  uint64_t thread_instrs;    /* simulated thread-instructions executed */
+  uint64_t shared_accesses;  /* logged shared accesses (records through the race check) */
+  uint64_t global_accesses;  /* simulated LDG + STG thread executions */
+  uint64_t reports;          /* reports produced */
+  uint64_t log_bytes;        /* bytes of access-log capacity reserved on the device */
+  uint64_t blocks;           /* simulated blocks in the batch */
+  float ms_reset, ms_interp, ms_check, ms_compact;   /* last run, when opts.profile */
+} sr_stats;
+
+/* Create a context on the current CUDA device.  opts may be NULL (defaults). */
+int sr_create(sr_ctx** out, const sr_opts* opts);
+void sr_destroy(sr_ctx* ctx);
+
+/* Host-only validation of one program (no CUDA call).  Writes a message on failure. */
+int sr_validate_program(const sr_program* prog, char* msg, size_t msg_len);
+
+/* Validate, pack and upload n programs (code, launch tables, initial arenas) into
+ * device-resident arenas; returns a batch handle.  The initial arenas stay resident so
+ * that run_and_check can be repeated.  Enqueued on `stream`. */
+int load_programs(sr_ctx* ctx, const sr_program* progs, uint32_t n, void* stream, sr_batch** out);
+
+/* Reset every program's global arena to its initial image, run all launches of all
+ * programs, check the access logs and barriers, and order the reports.  Asynchronous
+ * on `stream`. */
+int run_and_check(sr_ctx* ctx, sr_batch* batch, void* stream);
+
+/* Copy the sorted reports to dst (capacity cap records) and the total into *n_total.
+ * dst == NULL only queries the size.  SR_E_RANGE if cap < total (dst untouched). */
+int fetch_reports(sr_ctx* ctx, sr_batch* batch, sr_report* dst, uint64_t cap, uint64_t* n_total);
+
+/* Copy program `prog`'s final global arena (n_words = its size) to dst. */
+int fetch_memory(sr_ctx* ctx, sr_batch* batch, uint32_t prog, int32_t* dst, uint64_t cap_words,
+                 uint64_t* n_words);
+
+/* SR_ST_* bits of program `prog` after the last run_and_check. */
+int sr_batch_status(sr_ctx* ctx, sr_batch* batch, uint32_t prog, uint32_t* status);
+
+/* Counters of the last run (synchronises). */
+int sr_batch_stats(sr_ctx* ctx, sr_batch* batch, sr_stats* out);
+
+void sr_free_batch(sr_ctx* ctx, sr_batch* batch);
+const char* sr_last_error(sr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

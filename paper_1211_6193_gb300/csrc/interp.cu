@@ -1,0 +1,605 @@
+// interp.cu - the SIMT interpreter: one real warp per simulated warp.
+//
+// What it computes (Hathhorn et al., SSV 2012): every thread of every block runs the
+// kernel (Sec. 3 "Threads and memory"), blocks own a dynamic shared array (same
+// section), __syncthreads() is a block-wide barrier (Sec. 3 "Barrier synchronization"),
+// and every shared access is hooked (Sec. 3 "Modularity": the read/write check hook)
+// - here the hook appends an 8-byte record to the block's access log for the race
+// check of check.cu.  At each barrier the block's waiting threads are examined for
+// divergence and deadlock (Sec. 3.1, last paragraph).
+//
+// GPU design.  A simulated block of B threads runs on ceil(B/32) real warps; simulated
+// registers (row-major [reg][tid]) and the simulated shared array live in shared
+// memory, the program's code is staged into shared memory with a TMA bulk copy.  The
+// canonical schedule is round-lockstep across the block, but warps are NOT barrier-
+// synchronised every round: each warp counts its own rounds (within a barrier interval
+// a warp executes exactly one instruction per round while it has runnable lanes) and
+// publishes a logical clock 4*round + stage in shared memory.  Only memory
+// instructions wait, and only for what the round semantics needs:
+//   stage 0 (loads)   : every other warp has finished all earlier rounds;
+//   stage 1 (stores)  : every other warp has done its loads of this round, and lower
+//                       warps with an overlapping store in this round have stored
+//                       (highest tid wins; within a warp via __match_any_sync);
+//   stage 2 (atomics) : every other warp has done its stores of this round.
+// ALU and branch instructions never wait, so warps drift freely between memory
+// operations.  A warp whose lanes all wait at a barrier or exited publishes +inf; when
+// all warps of the block have parked, warp 0 resolves the barrier.  Every wait is
+// bounded (spin_limit) and reports SR_ST_INTERNAL instead of hanging.
+#include <climits>
+
+#include "sr_internal.h"
+
+namespace sr {
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+enum : uint32_t { DEC_RELEASE = 1, DEC_DONE = 2, DEC_STOP = 3 };
+
+struct BlockVars {
+  unsigned long long cursor;   // log records reserved by the block
+  uint32_t n_misc, epoch, k0, flags, decision, err_dirty, status;
+  uint32_t pad[7];
+};
+static_assert(sizeof(BlockVars) <= 64, "block vars");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cta(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ---- TMA bulk copy of the program code into shared memory (mbarrier completion)
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phase, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void group_sync(uint32_t id, uint32_t nthr) {
+  if (nthr == 32)
+    __syncwarp();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
+}
+
+// int32 ALU of the IR: two's-complement wrap, C division (x/0 and x%0 flagged)
+__device__ __forceinline__ int32_t alu(uint32_t op, int32_t x, int32_t y, bool& dz) {
+  switch (op) {
+    case SR_OP_MOV: return y;
+    case SR_OP_ADD: return (int32_t)((uint32_t)x + (uint32_t)y);
+    case SR_OP_SUB: return (int32_t)((uint32_t)x - (uint32_t)y);
+    case SR_OP_MUL: return (int32_t)((uint32_t)x * (uint32_t)y);
+    case SR_OP_DIV:
+      if (y == 0) { dz = true; return 0; }
+      return y == -1 ? (int32_t)(0u - (uint32_t)x) : x / y;   // -INT_MIN wraps to INT_MIN
+    case SR_OP_REM:
+      if (y == 0) { dz = true; return 0; }
+      return y == -1 ? 0 : x % y;
+    case SR_OP_AND: return x & y;
+    case SR_OP_OR: return x | y;
+    case SR_OP_XOR: return x ^ y;
+    case SR_OP_SHL: return (int32_t)((uint32_t)x << (y & 31));
+    case SR_OP_SHR: return x >> (y & 31);                        // arithmetic
+    case SR_OP_MIN: return min(x, y);
+    case SR_OP_MAX: return max(x, y);
+    case SR_OP_SLT: return x < y;
+    case SR_OP_SLE: return x <= y;
+    case SR_OP_SEQ: return x == y;
+    default: return x != y;                                      // SNE
+  }
+}
+
+// Wait until every other warp of the block has published a clock >= need.  With
+// `order` (store stage), also wait for lower warps whose store of this same round
+// (clock == need) touches an overlapping range of the same memory space.
+__device__ __forceinline__ bool wait_clocks(const uint32_t* clk, const int32_t* rlo, const int32_t* rhi,
+                                            const uint32_t* rsp, uint32_t nw, uint32_t w, uint32_t lane,
+                                            uint32_t need, bool order, int32_t lo, int32_t hi, uint32_t sp,
+                                            uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    bool ok = true;
+    if (lane < nw && lane != w) {
+      const uint32_t c = ld_acquire_cta(clk + lane);
+      ok = c >= need;
+      if (ok && order && lane < w && c == need) ok = !(rsp[lane] == sp && rlo[lane] <= hi && lo <= rhi[lane]);
+    }
+    if (__all_sync(FULL, ok)) {
+      __syncwarp();
+      return true;
+    }
+    if (it >= 32) __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void note_err(uint32_t* err, BlockVars* bv, uint32_t p, uint32_t w, uint32_t em,
+                                         uint32_t lane) {
+  if (lane == (uint32_t)(__ffs(em) - 1)) {
+    atomicAdd(&err[2 * p], (uint32_t)__popc(em));
+    atomicMin(&err[2 * p + 1], w * 32 + lane);
+    bv->err_dirty = 1;
+  }
+}
+
+// Append one record per lane with `me` to the block's access log (warp-aggregated:
+// one shared atomic per warp, consecutive 8-byte slots -> coalesced stores).
+__device__ __forceinline__ void log_access(BlockVars* bv, unsigned long long* region, uint32_t front_cap,
+                                           bool me, unsigned long long rec, uint32_t lane) {
+  const uint32_t m = __ballot_sync(FULL, me);
+  if (m == 0) return;
+  const uint32_t leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(&bv->cursor, (unsigned long long)__popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (me) {
+    const unsigned long long pos = base + __popc(m & lanemask_lt());
+    if (pos < front_cap)
+      region[pos] = rec;
+    else
+      atomicOr(&bv->flags, BF_OVERFLOW);
+  }
+}
+
+// Barrier/error records grow down from the end of the block's log region (16 B each).
+__device__ void push_misc(BlockVars* bv, unsigned long long* region, uint32_t log_cap, uint32_t kind,
+                          uint32_t epoch, uint32_t a, uint32_t b, uint32_t c) {
+  const uint32_t i = bv->n_misc;
+  const unsigned long long used = bv->cursor < log_cap ? bv->cursor : log_cap;
+  if (2ull * (i + 1) + used > log_cap) {
+    bv->flags |= BF_OVERFLOW;
+    return;
+  }
+  reinterpret_cast<uint4*>(region)[log_cap / 2 - 1 - i] = make_uint4(kind << 28 | epoch, a, b, c);
+  bv->n_misc = i + 1;
+}
+
+// Error records of the interval, ordered by (kind, pc); run by one whole warp.
+__device__ void flush_errors(BlockVars* bv, uint32_t* err, const uint2* ir, uint32_t ncode,
+                             unsigned long long* region, uint32_t log_cap, uint32_t epoch, uint32_t lane) {
+  for (uint32_t kind = SR_REP_ERR_OOB_SHARED; kind <= SR_REP_ERR_DIV0; ++kind) {
+    for (uint32_t base = 0; base < ncode; base += 32) {
+      const uint32_t pc = base + lane;
+      uint32_t cnt = 0, mt = 0;
+      bool hit = false;
+      if (pc < ncode) {
+        cnt = err[2 * pc];
+        if (cnt) {
+          const uint32_t op = ir[pc].x & 0x3Fu;
+          const uint32_t k2 = (op == SR_OP_LDS || op == SR_OP_STS || op == SR_OP_ATOMS) ? SR_REP_ERR_OOB_SHARED
+                              : (op == SR_OP_LDG || op == SR_OP_STG)                   ? SR_REP_ERR_OOB_GLOBAL
+                                                                                        : SR_REP_ERR_DIV0;
+          hit = (k2 == kind);
+          mt = err[2 * pc + 1];
+        }
+      }
+      uint32_t hm = __ballot_sync(FULL, hit);
+      while (hm) {
+        const uint32_t j = __ffs(hm) - 1;
+        hm &= hm - 1;
+        const uint32_t jc = __shfl_sync(FULL, cnt, j), jm = __shfl_sync(FULL, mt, j);
+        if (lane == 0) push_misc(bv, region, log_cap, kind, epoch, base + j, jm, jc);
+        __syncwarp();
+      }
+    }
+  }
+  for (uint32_t pc = lane; pc <= ncode; pc += 32) {
+    err[2 * pc] = 0;
+    err[2 * pc + 1] = kInf;
+  }
+  __syncwarp();
+  if (lane == 0) bv->err_dirty = 0;
+}
+
+// Run one simulated block on warps [0, nw) of a group (bar_id = its named barrier).
+__device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block, const uint2* __restrict__ ir,
+                          unsigned char* gsm, uint32_t w, uint32_t nw, uint32_t bar_id) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nthr = nw * 32;
+  const uint32_t tid = w * 32 + lane;
+  const uint32_t bdim = Ls->bdim, shw = Ls->shw, ncode = Ls->ncode, log_cap = Ls->log_cap;
+  const GroupLayout G = group_layout(nthr, shw, ncode);
+  uint32_t* regs = reinterpret_cast<uint32_t*>(gsm + G.regs);
+  int32_t* sh = reinterpret_cast<int32_t*>(gsm + G.sh);
+  uint32_t* clk = reinterpret_cast<uint32_t*>(gsm + G.clk);
+  int32_t* rlo = reinterpret_cast<int32_t*>(gsm + G.rlo);
+  int32_t* rhi = reinterpret_cast<int32_t*>(gsm + G.rhi);
+  uint32_t* rsp = reinterpret_cast<uint32_t*>(gsm + G.rsp);
+  uint32_t* park = reinterpret_cast<uint32_t*>(gsm + G.park);
+  uint32_t* err = reinterpret_cast<uint32_t*>(gsm + G.err);
+  BlockVars* bv = reinterpret_cast<BlockVars*>(gsm + G.bv);
+  int32_t* arena = A.arena + Ls->arena_off;
+  const uint32_t arena_words = (uint32_t)Ls->arena_words;
+  unsigned long long* region = A.log + Ls->log_base + (unsigned long long)block * log_cap;
+  const bool logging = A.check_races != 0;
+  const uint32_t budget = A.budget, spin = A.spin_limit;
+
+  // ---- block start: registers = params then zeros, shared memory zeroed
+  for (uint32_t r = 0; r < kRegRows; ++r)
+    regs[r * nthr + tid] = (r < Ls->nparams) ? (uint32_t)Ls->params[r] : 0u;
+  for (uint32_t i = tid; i < shw; i += nthr) sh[i] = 0;
+  for (uint32_t i = tid; i <= ncode; i += nthr) {
+    err[2 * i] = 0;
+    err[2 * i + 1] = kInf;
+  }
+  if (tid == 0) {
+    bv->cursor = 0;
+    bv->n_misc = 0; bv->epoch = 0; bv->k0 = 0; bv->flags = 0;
+    bv->decision = 0; bv->err_dirty = 0; bv->status = 0;
+  }
+  if (lane == 0) clk[w] = 0;
+  group_sync(bar_id, nthr);
+
+  uint32_t pc = Ls->entry, st = tid < bdim ? ST_RUN : ST_NONE, wpc = 0;
+  uint32_t k = 0, epoch = 0, front_cap = log_cap;
+  unsigned long long n_instr = 0, n_gacc = 0;
+
+  for (;;) {  // barrier intervals
+    bool limit = false, timeout = false;
+    for (;;) {  // rounds
+      const uint32_t runm = __ballot_sync(FULL, st == ST_RUN);
+      if (runm == 0) break;
+      if (k >= budget) { limit = true; break; }
+      const uint32_t p = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
+      const bool act = (st == ST_RUN) && (pc == p);
+      const uint32_t actm = __ballot_sync(FULL, act);
+      const uint2 ins = ir[p];
+      const uint32_t op = ins.x & 0x3Fu;
+      const uint32_t d = (ins.x >> 8) & 0xFFu, ra = (ins.x >> 16) & 0xFFu, rb = ins.x >> 24;
+      const int32_t imm = (int32_t)ins.y;
+      const int32_t va = (int32_t)regs[ra * nthr + tid];
+      const int32_t vb = (ins.x & SR_BIMM) ? imm : (int32_t)regs[rb * nthr + tid];
+      uint32_t npc = p + 1;
+      bool memop = false;
+      if (lane == 0) n_instr += __popc(actm);
+
+      if (op <= SR_OP_SNE) {
+        bool dz = false;
+        const int32_t r = alu(op, va, vb, dz);
+        if (act && d != kZeroReg) regs[d * nthr + tid] = (uint32_t)r;
+        if (op == SR_OP_DIV || op == SR_OP_REM) {
+          const uint32_t em = __ballot_sync(FULL, act && dz);
+          if (em) note_err(err, bv, p, w, em, lane);
+        }
+      } else {
+        switch (op) {
+          case SR_OP_S2R: {
+            const uint32_t v = imm == SR_SREG_TID    ? tid
+                               : imm == SR_SREG_BID  ? block
+                               : imm == SR_SREG_BDIM ? bdim
+                               : imm == SR_SREG_GDIM ? Ls->grid
+                                                     : 32u;
+            if (act && d != kZeroReg) regs[d * nthr + tid] = v;
+            break;
+          }
+          case SR_OP_LDS:
+          case SR_OP_LDG: {
+            memop = true;
+            const bool shared = op == SR_OP_LDS;
+            const int32_t addr = (int32_t)((uint32_t)va + (uint32_t)imm);
+            const bool inb = act && (uint32_t)addr < (shared ? shw : arena_words);
+            if (nw > 1 && !wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k, false, 0, 0, 0, spin)) {
+              timeout = true;
+              break;
+            }
+            int32_t v = 0;
+            if (inb) v = shared ? sh[addr] : arena[addr];
+            if (act && d != kZeroReg) regs[d * nthr + tid] = (uint32_t)v;
+            const uint32_t em = __ballot_sync(FULL, act && !inb);
+            if (em) note_err(err, bv, p, w, em, lane);
+            if (shared) {
+              if (logging) log_access(bv, region, front_cap, inb, make_record(epoch, addr, tid, K_R, p), lane);
+            } else if (lane == 0) {
+              n_gacc += __popc(actm);
+            }
+            break;
+          }
+          case SR_OP_STS:
+          case SR_OP_STG: {
+            memop = true;
+            const bool shared = op == SR_OP_STS;
+            const int32_t addr = (int32_t)((uint32_t)va + (uint32_t)imm);
+            const bool inb = act && (uint32_t)addr < (shared ? shw : arena_words);
+            if (nw > 1) {
+              const int32_t lo = __reduce_min_sync(FULL, inb ? addr : INT_MAX);
+              const int32_t hi = __reduce_max_sync(FULL, inb ? addr : INT_MIN);
+              if (lane == 0) {
+                rlo[w] = lo;
+                rhi[w] = hi;
+                rsp[w] = shared;
+                st_release_cta(&clk[w], 4u * k + 1u);
+              }
+              if (!wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k + 1u, true, lo, hi, shared, spin)) {
+                timeout = true;
+                break;
+              }
+            }
+            // several lanes of the warp on one word: the highest tid's store is the one kept
+            const uint32_t grp = __match_any_sync(FULL, inb ? (uint32_t)addr : (0x80000000u | lane));
+            if (inb && lane == 31u - __clz(grp)) {
+              if (shared)
+                sh[addr] = vb;
+              else
+                arena[addr] = vb;
+            }
+            const uint32_t em = __ballot_sync(FULL, act && !inb);
+            if (em) note_err(err, bv, p, w, em, lane);
+            if (shared) {
+              if (logging) log_access(bv, region, front_cap, inb, make_record(epoch, addr, tid, K_W, p), lane);
+            } else if (lane == 0) {
+              n_gacc += __popc(actm);
+            }
+            break;
+          }
+          case SR_OP_ATOMS: {
+            memop = true;
+            const int32_t addr = (int32_t)((uint32_t)va + (uint32_t)imm);
+            const bool inb = act && (uint32_t)addr < shw;
+            if (nw > 1) {
+              if (lane == 0) st_release_cta(&clk[w], 4u * k + 2u);
+              if (!wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k + 2u, false, 0, 0, 0, spin)) {
+                timeout = true;
+                break;
+              }
+            }
+            if (inb) atomicAdd(&sh[addr], vb);
+            const uint32_t em = __ballot_sync(FULL, act && !inb);
+            if (em) note_err(err, bv, p, w, em, lane);
+            if (logging) log_access(bv, region, front_cap, inb, make_record(epoch, addr, tid, K_A, p), lane);
+            break;
+          }
+          case SR_OP_BRA: npc = (uint32_t)imm; break;
+          case SR_OP_BRZ: npc = va == 0 ? (uint32_t)imm : p + 1; break;
+          case SR_OP_BRNZ: npc = va != 0 ? (uint32_t)imm : p + 1; break;
+          case SR_OP_BAR:
+            if (act) { st = ST_WAIT; wpc = p; }
+            break;
+          default:  // EXIT, and the EXIT sentinel after the last instruction
+            if (act) st = ST_EXIT;
+            break;
+        }
+      }
+      if (timeout) break;
+      if (act) pc = npc;
+      ++k;
+      // publish progress; after a memory instruction every lane's access must be
+      // ordered before the clock (warp barrier, then a release by lane 0)
+      if (memop) __syncwarp();
+      if (lane == 0) st_release_cta(&clk[w], 4u * k);
+    }
+
+    // ---- no runnable lane in this warp: publish its state and park
+    {
+      const uint32_t wm = __ballot_sync(FULL, st == ST_WAIT);
+      const uint32_t xm = __ballot_sync(FULL, st == ST_EXIT);
+      const uint32_t rm = __ballot_sync(FULL, st == ST_RUN);
+      const uint32_t pmn = __reduce_min_sync(FULL, st == ST_WAIT ? wpc : kInf);
+      const uint32_t pmx = __reduce_max_sync(FULL, st == ST_WAIT ? wpc : 0u);
+      const uint32_t rpc = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
+      if (lane == 0) {
+        uint32_t* P = park + w * 8;
+        P[0] = __popc(wm); P[1] = __popc(xm); P[2] = __popc(rm);
+        P[3] = pmn; P[4] = pmx; P[5] = rpc; P[6] = k;
+        P[7] = (limit ? 1u : 0u) | (timeout ? 2u : 0u);
+        st_release_cta(&clk[w], kInf);
+      }
+    }
+    group_sync(bar_id, nthr);
+
+    // ---- barrier resolution by warp 0 of the block
+    if (w == 0) {
+      const bool v = lane < nw;
+      const uint32_t* P = park + lane * 8;
+      const uint32_t nW = __reduce_add_sync(FULL, v ? P[0] : 0u);
+      const uint32_t nX = __reduce_add_sync(FULL, v ? P[1] : 0u);
+      const uint32_t nR = __reduce_add_sync(FULL, v ? P[2] : 0u);
+      const uint32_t pmn = __reduce_min_sync(FULL, v ? P[3] : kInf);
+      const uint32_t pmx = __reduce_max_sync(FULL, v ? P[4] : 0u);
+      const uint32_t rpc = __reduce_min_sync(FULL, v ? P[5] : kInf);
+      const uint32_t kmax = __reduce_max_sync(FULL, v ? P[6] : 0u);
+      const uint32_t fl = __reduce_or_sync(FULL, v ? P[7] : 0u);
+      const uint32_t ep = bv->epoch;
+      uint32_t dec, kind = 0, a = 0, b = 0, c = 0, stbits = 0;
+      if (fl & 2u) {
+        dec = DEC_STOP;
+        if (lane == 0) bv->flags |= BF_INTERNAL;
+      } else if (fl & 1u) {            // out of rounds
+        dec = DEC_STOP; kind = SR_REP_STEP_LIMIT; a = budget; b = nR; c = rpc; stbits = SR_ST_STEP_LIMIT;
+      } else if (nW == 0) {            // every thread exited
+        dec = DEC_DONE;
+      } else if (nX > 0) {             // some wait at a barrier that exited threads never reach
+        dec = DEC_STOP; kind = SR_REP_DEADLOCK; a = pmn; b = pmx; c = nW << 16 | nX; stbits = SR_ST_DEADLOCK;
+      } else {                         // all wait: release, flag differing barrier pcs
+        dec = DEC_RELEASE;
+        if (pmn != pmx) { kind = SR_REP_DIVERGENCE; a = pmn; b = pmx; c = nW << 16; }
+      }
+      if (lane == 0 && kind) push_misc(bv, region, log_cap, kind, ep, a, b, c);
+      __syncwarp();
+      if (bv->err_dirty) flush_errors(bv, err, ir, ncode, region, log_cap, ep, lane);
+      if (lane == 0) {
+        bv->decision = dec;
+        bv->status |= stbits;
+        if (dec == DEC_RELEASE) { bv->epoch = ep + 1; bv->k0 = kmax; }
+      }
+      if (dec == DEC_RELEASE && v) clk[lane] = 4u * kmax;
+    }
+    group_sync(bar_id, nthr);
+    if (bv->decision != DEC_RELEASE) break;
+    if (st == ST_WAIT) st = ST_RUN;
+    k = bv->k0;
+    epoch = bv->epoch;
+    front_cap = log_cap - 2u * bv->n_misc;
+  }
+
+  // ---- block finished
+  if (lane == 0) {
+    atomicAdd(&A.counters->thread_instrs, n_instr);
+    if (n_gacc) atomicAdd(&A.counters->global_accesses, n_gacc);
+  }
+  if (tid == 0) {
+    const uint32_t front = log_cap - 2u * bv->n_misc;
+    BlockRes r;
+    r.n_log = bv->cursor < front ? (uint32_t)bv->cursor : front;
+    r.n_race = 0;
+    r.n_misc = bv->n_misc;
+    r.flags = bv->flags;
+    A.blocks[Ls->block_base + block] = r;
+    if (r.n_log) atomicAdd(&A.counters->shared_accesses, (unsigned long long)r.n_log);
+    const uint32_t bits = bv->status | ((bv->flags & BF_OVERFLOW) ? (uint32_t)SR_ST_LOG_OVERFLOW : 0u) |
+                          ((bv->flags & BF_INTERNAL) ? (uint32_t)SR_ST_INTERNAL : 0u);
+    if (bits) atomicOr(&A.prog_status[Ls->prog], bits);
+    if (bits & (SR_ST_DEADLOCK | SR_ST_STEP_LIMIT | SR_ST_INTERNAL)) atomicMin(&A.prog_abort[Ls->prog], Ls->launch);
+  }
+}
+
+// One CTA per simulated block; one kernel launch per (program, launch).
+__global__ void __launch_bounds__(1024) k_interp_plain(RunArgs A, uint32_t li) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ LaunchDev Ls;
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t s_skip;
+  if (threadIdx.x == 0) {
+    Ls = A.launches[li];
+    // launches after a deadlock / step limit of the same program are skipped
+    s_skip = *reinterpret_cast<volatile uint32_t*>(&A.prog_abort[Ls.prog]) < Ls.launch;
+    if (!s_skip) {
+      mbar_init(&mbar);
+      bulk_load(smem, A.code + Ls.code_off, Ls.ir_bytes, &mbar);
+    }
+  }
+  __syncthreads();
+  if (s_skip) return;
+  // every thread must take the same branch before the block's named barriers
+  if (__syncthreads_or(!mbar_wait(&mbar, 0, A.spin_limit))) {
+    if (threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
+    return;
+  }
+  run_block(A, &Ls, blockIdx.x, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes, threadIdx.x >> 5,
+            blockDim.x >> 5, 1);
+}
+
+// Persistent: CTAs pop (launch, first block) items from a device queue; an item runs
+// `groups` simulated blocks side by side, each on its own warps and named barrier.
+// Items are ordered launch-wave by launch-wave, and an item of launch l waits (bounded)
+// until every block of launch l-1 of the same program has completed.
+__global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ LaunchDev Ls;
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t s_item, s_skip;
+  uint32_t phase = 0;
+  if (threadIdx.x == 0) mbar_init(&mbar);
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(A.queue_head, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= A.nitems) break;
+    const uint2 it = A.items[item];
+    if (threadIdx.x == 0) {
+      Ls = A.launches[it.x];
+      uint32_t skip = 0;
+      if (Ls.launch > 0) {
+        const uint32_t need = A.launches[it.x - 1].grid;
+        bool ok = false;
+        for (uint32_t s = 0; s < A.spin_limit; ++s) {
+          if (ld_acquire_gpu(&A.launch_done[it.x - 1]) >= need) { ok = true; break; }
+          __nanosleep(128);
+        }
+        if (!ok) {
+          skip = 1;
+          atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
+        }
+      }
+      if (!skip && *reinterpret_cast<volatile uint32_t*>(&A.prog_abort[Ls.prog]) < Ls.launch) skip = 1;
+      if (!skip) bulk_load(smem, A.code + Ls.code_off, Ls.ir_bytes, &mbar);
+      s_skip = skip;
+    }
+    __syncthreads();
+    const uint32_t nblk = min(Ls.groups, Ls.grid - it.y);
+    if (!s_skip) {
+      const bool ok = !__syncthreads_or(!mbar_wait(&mbar, phase, A.spin_limit));
+      phase ^= 1u;
+      const uint32_t nw = (Ls.bdim + 31) >> 5;
+      const uint32_t wid = threadIdx.x >> 5, g = wid / nw;
+      if (ok && g < nblk)
+        run_block(A, &Ls, it.y + g, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes + g * Ls.group_bytes,
+                  wid - g * nw, nw, 1 + g);
+      if (!ok && threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&A.launch_done[it.x], nblk);
+    }
+  }
+}
+
+}  // namespace
+
+uint32_t interp_plain_smem(const LaunchDev& L) {
+  const uint32_t nthr = ((L.bdim + 31) / 32) * 32;
+  return L.ir_bytes + group_layout(nthr, L.shw, L.ncode).total;
+}
+
+// dynamic shared memory may use what the kernel's static shared memory leaves of the opt-in limit
+template <typename K>
+static cudaError_t allow_dynamic_smem(K kernel, uint32_t smem_optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(smem_optin - (uint32_t)fa.sharedSizeBytes));
+}
+
+cudaError_t init_interp_attributes(uint32_t smem_optin) {
+  cudaError_t e = allow_dynamic_smem(k_interp_plain, smem_optin);
+  return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched, smem_optin) : e;
+}
+
+cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, cudaStream_t s) {
+  const uint32_t threads = ((L.bdim + 31) / 32) * 32;
+  k_interp_plain<<<L.grid, threads, interp_plain_smem(L), s>>>(a, li);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, cudaStream_t s) {
+  k_interp_batched<<<ctas, 1024, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sr

@@ -1,0 +1,726 @@
+// runtime.cpp - host side of libsimtcheck: the C ABI of include/simtcheck.h.
+//
+// load_programs  validates and packs the programs (code with an EXIT sentinel, register
+//                fields remapped so RZ and unused operands read the zero row), bounds
+//                every launch's per-block access log statically, groups launches into
+//                waves whose logs fit the log budget, and uploads everything.
+// run_and_check  per wave: interpreter (one launch per (program, launch) in plain mode,
+//                one persistent launch in batched mode), race check, report scan and
+//                emission.  Everything is enqueued on the caller's stream.
+// fetch_*        synchronise the stream and copy results to the host.
+#include <algorithm>
+#include <cstdarg>
+#include <new>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sr_internal.h"
+
+using sr::LaunchDev;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Wave {
+  uint32_t li0, li1;      // launch index range
+  uint32_t gb0, gb1;      // global block range
+  uint32_t item0, item1;  // batched work items
+  uint64_t log_records;
+};
+
+}  // namespace
+
+struct sr_ctx {
+  sr_opts opts{};
+  sr_allocator alloc{};
+  bool custom_alloc = false;
+  std::string err;
+  int device = 0;
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+
+struct sr_batch {
+  uint32_t nprogs = 0;
+  std::vector<LaunchDev> launches;
+  std::vector<uint64_t> arena_off, arena_words;
+  std::vector<uint2> items;
+  std::vector<Wave> waves;
+  uint32_t nblocks = 0;
+  uint32_t max_key_bits = 1;
+  uint32_t batched_smem = 0;
+  uint64_t total_code = 0, total_arena = 0, log_records = 0;
+  DevBuf code, launches_d, arena_init, arena_work, log, blocks, prog_status, prog_abort, counters, items_d,
+      queue_head, launch_done, scratch, work_head, err_flag, offsets, partials, out, total;
+  uint64_t out_cap = 0;
+  cudaStream_t stream = nullptr;
+  bool ran = false;
+  uint32_t check_ctas = 0;
+  // CUDA graph of run_and_check (batched mode with use_graph)
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  // profiling
+  std::vector<cudaEvent_t> events;
+  uint32_t nevents_used = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;   // failures of sr_create (no context yet)
+
+int fail(sr_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_create_error = buf;
+  return code;
+}
+#define CUDA_TRY(c, call)                                                                          \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail((c), SR_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+void* dev_alloc(sr_ctx* c, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (c->custom_alloc) return c->alloc.alloc(c->alloc.user, bytes, s);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void dev_free(sr_ctx* c, DevBuf& b, cudaStream_t s) {
+  if (!b.p) return;
+  if (c->custom_alloc)
+    c->alloc.release(c->alloc.user, b.p, b.bytes, s);
+  else
+    cudaFreeAsync(b.p, s);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+int alloc_buf(sr_ctx* c, DevBuf& b, size_t bytes, cudaStream_t s, const char* what) {
+  b.p = dev_alloc(c, bytes, s);
+  b.bytes = bytes ? bytes : 16;
+  if (!b.p) return fail(c, SR_E_NOMEM, "device allocation of %zu bytes for %s failed", bytes, what);
+  return SR_OK;
+}
+
+// which operand fields an opcode reads or writes
+bool op_writes_d(uint32_t b) {
+  return (b >= SR_OP_MOV && b <= SR_OP_SNE) || b == SR_OP_S2R || b == SR_OP_LDG || b == SR_OP_LDS;
+}
+bool op_reads_a(uint32_t b) {
+  return (b >= SR_OP_ADD && b <= SR_OP_SNE) || b == SR_OP_LDG || b == SR_OP_STG || b == SR_OP_LDS ||
+         b == SR_OP_STS || b == SR_OP_ATOMS || b == SR_OP_BRZ || b == SR_OP_BRNZ;
+}
+bool op_reads_b(uint32_t op) {
+  const uint32_t b = op & 0x7Fu;
+  return ((b >= SR_OP_MOV && b <= SR_OP_SNE) && !(op & SR_BIMM)) || b == SR_OP_STG || b == SR_OP_STS ||
+         b == SR_OP_ATOMS;
+}
+bool is_shared_access(uint32_t b) { return b == SR_OP_LDS || b == SR_OP_STS || b == SR_OP_ATOMS; }
+bool can_err(uint32_t b) {
+  return b == SR_OP_LDS || b == SR_OP_STS || b == SR_OP_ATOMS || b == SR_OP_LDG || b == SR_OP_STG ||
+         b == SR_OP_DIV || b == SR_OP_REM;
+}
+
+// Static bound for one kernel: the largest number of shared accesses and barriers a
+// single thread can execute, or "unbounded" if the control-flow graph from the entry
+// has a cycle.
+struct KernelBound {
+  bool cyclic = false;
+  uint32_t accesses = 0, barriers = 0, err_pcs = 0;
+};
+KernelBound bound_kernel(const sr_instr* code, uint32_t ncode, uint32_t entry) {
+  KernelBound kb;
+  // iterative DFS with colours; longest paths by memoised post-order
+  std::vector<uint8_t> colour(ncode + 1, 0);
+  std::vector<uint32_t> acc(ncode + 1, 0), bar(ncode + 1, 0);
+  std::vector<std::pair<uint32_t, uint32_t>> stack;   // (pc, next successor index)
+  auto succ = [&](uint32_t pc, uint32_t i, uint32_t& out) -> bool {
+    if (pc >= ncode) return false;
+    const uint32_t b = code[pc].op_d_a_b & 0x7Fu;
+    const uint32_t t = (uint32_t)code[pc].imm;
+    if (b == SR_OP_EXIT) return false;
+    if (b == SR_OP_BRA) { if (i == 0) { out = t; return true; } return false; }
+    if (b == SR_OP_BRZ || b == SR_OP_BRNZ) {
+      if (i == 0) { out = pc + 1; return true; }
+      if (i == 1) { out = t; return true; }
+      return false;
+    }
+    if (i == 0) { out = pc + 1; return true; }
+    return false;
+  };
+  stack.push_back({entry, 0});
+  colour[entry] = 1;
+  while (!stack.empty()) {
+    auto& top = stack.back();
+    uint32_t nxt;
+    if (succ(top.first, top.second, nxt)) {
+      top.second++;
+      if (colour[nxt] == 1) { kb.cyclic = true; return kb; }
+      if (colour[nxt] == 0) { colour[nxt] = 1; stack.push_back({nxt, 0}); }
+      continue;
+    }
+    const uint32_t pc = top.first;
+    uint32_t a = 0, br = 0, s;
+    for (uint32_t i = 0; succ(pc, i, s); ++i) { a = std::max(a, acc[s]); br = std::max(br, bar[s]); }
+    if (pc < ncode) {
+      const uint32_t b = code[pc].op_d_a_b & 0x7Fu;
+      a += is_shared_access(b);
+      br += b == SR_OP_BAR;
+      kb.err_pcs += can_err(b);
+    }
+    acc[pc] = a;
+    bar[pc] = br;
+    colour[pc] = 2;
+    stack.pop_back();
+  }
+  kb.accesses = acc[entry];
+  kb.barriers = bar[entry];
+  return kb;
+}
+
+int validate(const sr_program* p, char* msg, size_t len) {
+  auto bad = [&](const char* fmt, uint32_t x, uint32_t y) {
+    if (msg && len) snprintf(msg, len, fmt, x, y);
+    return SR_E_INVAL;
+  };
+  if (!p || !p->code || p->ncode == 0 || p->ncode > SR_MAX_CODE) return bad("code size %u outside 1..%u", p ? p->ncode : 0, SR_MAX_CODE);
+  if (!p->kernel_entry || p->nkernels == 0) return bad("no kernels (%u, %u)", 0, 0);
+  for (uint32_t k = 0; k < p->nkernels; ++k)
+    if (p->kernel_entry[k] >= p->ncode) return bad("kernel %u entry %u out of range", k, p->kernel_entry[k]);
+  for (uint32_t pc = 0; pc < p->ncode; ++pc) {
+    const uint32_t w = p->code[pc].op_d_a_b, op = w & 0xFFu, b = op & 0x7Fu;
+    const uint32_t d = (w >> 8) & 0xFFu, ra = (w >> 16) & 0xFFu, rb = (w >> 24) & 0xFFu;
+    const int32_t imm = p->code[pc].imm;
+    const bool alu = b >= SR_OP_MOV && b <= SR_OP_SNE;
+    if (b < SR_OP_MOV || b > SR_OP_EXIT || (op & 0x40u) || ((op & SR_BIMM) && !alu)) return bad("pc %u: bad opcode 0x%x", pc, op);
+    auto reg_ok = [](uint32_t r) { return r < 16 || r == SR_RZ; };
+    if ((op_writes_d(b) && !reg_ok(d)) || (op_reads_a(b) && !reg_ok(ra)) || (op_reads_b(op) && !reg_ok(rb)))
+      return bad("pc %u: bad register field (op %u)", pc, b);
+    if ((b == SR_OP_BRA || b == SR_OP_BRZ || b == SR_OP_BRNZ) && (imm < 0 || (uint32_t)imm > p->ncode))
+      return bad("pc %u: branch target %u out of range", pc, (uint32_t)imm);
+    if (b == SR_OP_S2R && (imm < 0 || imm > SR_SREG_WARPSIZE)) return bad("pc %u: bad special register %u", pc, (uint32_t)imm);
+  }
+  if (p->nlaunches && !p->launches) return bad("launch table missing (%u launches)", p->nlaunches, 0);
+  for (uint32_t l = 0; l < p->nlaunches; ++l) {
+    const sr_launch& L = p->launches[l];
+    if (L.kernel >= p->nkernels) return bad("launch %u: kernel %u out of range", l, L.kernel);
+    if (L.grid == 0 || L.grid > (1u << 30)) return bad("launch %u: grid %u", l, L.grid);
+    if (L.block_dim == 0 || L.block_dim > SR_MAX_BLOCK_DIM) return bad("launch %u: block_dim %u", l, L.block_dim);
+    if (L.shmem_words > SR_MAX_SHMEM_WORDS) return bad("launch %u: shmem_words %u", l, L.shmem_words);
+    if (L.nparams > 4) return bad("launch %u: nparams %u", l, L.nparams);
+  }
+  if (p->global_words >= (1ull << 31)) return bad("global arena too large (%u)", (uint32_t)(p->global_words >> 20), 0);
+  if (p->global_words && !p->global_init) return bad("global_init missing (%u words)", (uint32_t)p->global_words, 0);
+  return SR_OK;
+}
+
+// pack one instruction: RZ and unused register fields point at the zero row (16)
+uint2 pack(const sr_instr& in) {
+  const uint32_t w = in.op_d_a_b, op = w & 0xFFu, b = op & 0x7Fu;
+  uint32_t d = (w >> 8) & 0xFFu, ra = (w >> 16) & 0xFFu, rb = (w >> 24) & 0xFFu;
+  auto map = [](uint32_t r) { return r == SR_RZ ? sr::kZeroReg : r; };
+  d = op_writes_d(b) ? map(d) : sr::kZeroReg;
+  ra = op_reads_a(b) ? map(ra) : sr::kZeroReg;
+  rb = op_reads_b(op) ? map(rb) : sr::kZeroReg;
+  return make_uint2(op | d << 8 | ra << 16 | rb << 24, (uint32_t)in.imm);
+}
+
+uint32_t key_bits_for(uint32_t shw) {
+  uint32_t b = 1;
+  while ((1u << b) < shw) ++b;
+  return b;
+}
+
+void free_batch_buffers(sr_ctx* c, sr_batch* b, cudaStream_t s) {
+  DevBuf* all[] = {&b->code, &b->launches_d, &b->arena_init, &b->arena_work, &b->log, &b->blocks,
+                   &b->prog_status, &b->prog_abort, &b->counters, &b->items_d, &b->queue_head,
+                   &b->launch_done, &b->scratch, &b->work_head, &b->err_flag, &b->offsets, &b->partials,
+                   &b->out, &b->total};
+  for (DevBuf* d : all) dev_free(c, *d, s);
+}
+
+cudaEvent_t next_event(sr_batch* b) {
+  if (b->nevents_used == b->events.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    b->events.push_back(e);
+  }
+  return b->events[b->nevents_used++];
+}
+
+// Enqueue the whole pipeline for one run on stream s.
+int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
+  const sr_opts& o = c->opts;
+  b->nevents_used = 0;
+  auto mark = [&]() -> cudaEvent_t {
+    if (!profile) return nullptr;
+    cudaEvent_t e = next_event(b);
+    if (e) cudaEventRecord(e, s);
+    return e;
+  };
+  mark();
+  CUDA_TRY(c, cudaMemcpyAsync(b->arena_work.p, b->arena_init.p, b->total_arena * 4, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(c, cudaMemsetAsync(b->blocks.p, 0, (size_t)b->nblocks * sizeof(sr::BlockRes), s));
+  CUDA_TRY(c, cudaMemsetAsync(b->prog_status.p, 0, (size_t)b->nprogs * 4, s));
+  CUDA_TRY(c, cudaMemsetAsync(b->prog_abort.p, 0xFF, (size_t)b->nprogs * 4, s));
+  CUDA_TRY(c, cudaMemsetAsync(b->counters.p, 0, sizeof(sr::Counters), s));
+  CUDA_TRY(c, cudaMemsetAsync(b->launch_done.p, 0, b->launches.size() * 4, s));
+  CUDA_TRY(c, cudaMemsetAsync(b->total.p, 0, 8, s));
+  CUDA_TRY(c, cudaMemsetAsync(b->err_flag.p, 0, 4, s));
+  mark();
+
+  sr::RunArgs ra{};
+  ra.launches = (const LaunchDev*)b->launches_d.p;
+  ra.nlaunches = (uint32_t)b->launches.size();
+  ra.budget = o.round_budget;
+  ra.check_races = o.check_races;
+  ra.spin_limit = o.spin_limit;
+  ra.code = (const uint2*)b->code.p;
+  ra.arena = (int32_t*)b->arena_work.p;
+  ra.log = (unsigned long long*)b->log.p;
+  ra.blocks = (sr::BlockRes*)b->blocks.p;
+  ra.prog_status = (uint32_t*)b->prog_status.p;
+  ra.prog_abort = (uint32_t*)b->prog_abort.p;
+  ra.counters = (sr::Counters*)b->counters.p;
+  ra.items = (const uint2*)b->items_d.p;
+  ra.launch_done = (uint32_t*)b->launch_done.p;
+
+  for (size_t wi = 0; wi < b->waves.size(); ++wi) {
+    const Wave& w = b->waves[wi];
+    if (o.mode == SR_MODE_BATCHED) {
+      ra.items = (const uint2*)b->items_d.p + w.item0;
+      ra.nitems = w.item1 - w.item0;
+      ra.queue_head = (uint32_t*)b->queue_head.p + wi;
+      CUDA_TRY(c, cudaMemsetAsync(ra.queue_head, 0, 4, s));
+      const uint32_t ctas = std::min<uint32_t>(ra.nitems, (uint32_t)c->sms * std::max(1u, o.ctas_per_sm));
+      if (ctas) CUDA_TRY(c, sr::launch_interp_batched(ra, ctas, b->batched_smem, s));
+    } else {
+      for (uint32_t li = w.li0; li < w.li1; ++li) CUDA_TRY(c, sr::launch_interp_plain(ra, li, b->launches[li], s));
+    }
+    mark();
+    if (o.check_races) {
+      sr::CheckArgs ca{};
+      ca.launches = ra.launches;
+      ca.nlaunches = ra.nlaunches;
+      ca.gb0 = w.gb0;
+      ca.gb1 = w.gb1;
+      ca.log = ra.log;
+      ca.blocks = ra.blocks;
+      ca.scratch = (uint4*)b->scratch.p;
+      ca.work_head = (uint32_t*)b->work_head.p + wi;
+      ca.error_flag = (uint32_t*)b->err_flag.p;
+      ca.spin_limit = o.spin_limit;
+      ca.max_key_bits = b->max_key_bits;
+      CUDA_TRY(c, cudaMemsetAsync(ca.work_head, 0, 4, s));
+      const uint32_t ctas = std::min<uint32_t>(b->check_ctas, w.gb1 - w.gb0);
+      if (ctas) CUDA_TRY(c, sr::launch_check(ca, ctas, s));
+    }
+    mark();
+    sr::CompactArgs ka{};
+    ka.launches = ra.launches;
+    ka.nlaunches = ra.nlaunches;
+    ka.gb0 = w.gb0;
+    ka.gb1 = w.gb1;
+    ka.total = (unsigned long long*)b->total.p;
+    ka.log = ra.log;
+    ka.blocks = ra.blocks;
+    ka.offsets = (unsigned long long*)b->offsets.p;
+    ka.partials = (unsigned long long*)b->partials.p;
+    ka.out = (sr_report*)b->out.p;
+    ka.out_cap = b->out_cap;
+    ka.counters = ra.counters;
+    CUDA_TRY(c, sr::launch_compact_scan(ka, s));
+    CUDA_TRY(c, sr::launch_compact_emit(ka, s));
+    mark();
+  }
+  return SR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sr_create(sr_ctx** out, const sr_opts* opts) {
+  if (!out) return fail(nullptr, SR_E_INVAL, "out is NULL");
+  *out = nullptr;
+  sr_ctx* c = new (std::nothrow) sr_ctx();
+  if (!c) return fail(nullptr, SR_E_NOMEM, "host allocation failed");
+  if (opts)
+    c->opts = *opts;
+  else
+    c->opts.check_races = 1;
+  sr_opts& o = c->opts;
+  if (o.round_budget == 0) o.round_budget = 1u << 24;
+  if (o.loop_log_records == 0) o.loop_log_records = 65536;
+  if (o.check_ctas_per_sm == 0) o.check_ctas_per_sm = 1;
+  if (o.ctas_per_sm == 0) o.ctas_per_sm = 1;
+  if (o.spin_limit == 0) o.spin_limit = 1u << 26;
+  if (o.round_budget > sr::kMaxBudget || o.mode > SR_MODE_BATCHED) {
+    delete c;
+    return fail(nullptr, SR_E_INVAL, "round_budget above 2^26 or unknown mode");
+  }
+  if (o.allocator && o.allocator->alloc && o.allocator->release) {
+    c->alloc = *o.allocator;
+    c->custom_alloc = true;
+  }
+  o.allocator = nullptr;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  c->smem_optin = (size_t)optin;
+  if (e == cudaSuccess) e = sr::init_kernel_attributes((uint32_t)optin);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(nullptr, SR_E_CUDA, "device setup failed: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return SR_OK;
+}
+
+void sr_destroy(sr_ctx* c) { delete c; }
+
+const char* sr_last_error(sr_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int sr_validate_program(const sr_program* prog, char* msg, size_t msg_len) {
+  if (msg && msg_len) msg[0] = 0;
+  return validate(prog, msg, msg_len);
+}
+
+int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, sr_batch** out) {
+  if (!c || !out || (n && !progs)) return fail(c, SR_E_INVAL, "null argument");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  const sr_opts& o = c->opts;
+  for (uint32_t i = 0; i < n; ++i) {
+    char msg[256];
+    if (validate(&progs[i], msg, sizeof msg) != SR_OK) return fail(c, SR_E_INVAL, "program %u: %s", i, msg);
+  }
+  sr_batch* b = new (std::nothrow) sr_batch();
+  if (!b) return fail(c, SR_E_NOMEM, "host allocation failed");
+  b->nprogs = n;
+  b->stream = s;
+
+  // ---- pack code and arenas, bound the logs
+  std::vector<uint2> code;
+  std::vector<uint32_t> code_off(n);
+  b->arena_off.resize(n);
+  b->arena_words.resize(n);
+  uint64_t arena_total = 0;
+  uint64_t nblocks = 0;
+  const uint32_t smem_budget = (uint32_t)std::min<size_t>(c->smem_optin ? c->smem_optin : 227 * 1024, 227 * 1024) /
+                                   std::max(1u, o.ctas_per_sm) -
+                               1024;
+  for (uint32_t i = 0; i < n; ++i) {
+    const sr_program& P = progs[i];
+    code_off[i] = (uint32_t)code.size();
+    for (uint32_t pc = 0; pc < P.ncode; ++pc) code.push_back(pack(P.code[pc]));
+    code.push_back(make_uint2(SR_OP_EXIT | sr::kZeroReg << 8 | sr::kZeroReg << 16 | sr::kZeroReg << 24, 0));
+    if (code.size() & 1) code.push_back(make_uint2(SR_OP_EXIT, 0));
+    b->arena_off[i] = arena_total;
+    b->arena_words[i] = P.global_words;
+    arena_total += (P.global_words + 3) & ~3ull;
+    std::vector<KernelBound> kb(P.nkernels);
+    for (uint32_t k = 0; k < P.nkernels; ++k) kb[k] = bound_kernel(P.code, P.ncode, P.kernel_entry[k]);
+    for (uint32_t l = 0; l < P.nlaunches; ++l) {
+      const sr_launch& L = P.launches[l];
+      LaunchDev d{};
+      d.prog = i;
+      d.launch = l;
+      d.entry = P.kernel_entry[L.kernel];
+      d.ncode = P.ncode;
+      d.code_off = code_off[i];
+      d.grid = L.grid;
+      d.bdim = L.block_dim;
+      d.shw = L.shmem_words;
+      d.nparams = L.nparams;
+      for (uint32_t q = 0; q < 4; ++q) d.params[q] = q < L.nparams ? L.params[q] : 0;
+      d.block_base = (uint32_t)nblocks;
+      d.key_bits = key_bits_for(std::max(1u, L.shmem_words));
+      const KernelBound& k = kb[L.kernel];
+      uint64_t recs, misc;
+      if (k.cyclic) {
+        recs = o.loop_log_records;
+        misc = std::max<uint64_t>(256, 4ull * (1 + k.err_pcs));
+      } else {
+        recs = (uint64_t)k.accesses * L.block_dim;
+        misc = (uint64_t)(k.barriers + 1) * (1 + k.err_pcs) + 1;
+      }
+      if (!o.check_races) recs = 0;
+      uint64_t cap = recs + 2 * misc;
+      cap = (cap + 1) & ~1ull;
+      if (cap >= (1ull << 31)) {
+        delete b;
+        return fail(c, SR_E_INVAL, "program %u launch %u: access log bound too large", i, l);
+      }
+      d.log_cap = (uint32_t)cap;
+      d.arena_off = b->arena_off[i];
+      d.arena_words = P.global_words;
+      d.ir_bytes = sr::ir_smem_bytes(P.ncode);
+      const uint32_t nw = (L.block_dim + 31) / 32;
+      d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode).total;
+      if (d.ir_bytes + d.group_bytes > smem_budget) {
+        delete b;
+        return fail(c, SR_E_INVAL, "program %u launch %u: %u bytes of shared memory needed, %u available", i, l,
+                    d.ir_bytes + d.group_bytes, smem_budget);
+      }
+      uint32_t g = std::min<uint32_t>(32 / nw, (smem_budget - d.ir_bytes) / d.group_bytes);
+      if (nw >= 2) g = std::min<uint32_t>(g, 15);
+      d.groups = std::max<uint32_t>(1, std::min<uint32_t>(g, L.grid));
+      b->max_key_bits = std::max(b->max_key_bits, d.key_bits);
+      nblocks += L.grid;
+      if (nblocks >= (1ull << 31)) {
+        delete b;
+        return fail(c, SR_E_INVAL, "too many simulated blocks in one batch");
+      }
+      b->launches.push_back(d);
+    }
+  }
+  b->nblocks = (uint32_t)nblocks;
+  b->total_code = code.size();
+  b->total_arena = arena_total;
+
+  // ---- waves: consecutive launches whose logs fit the budget together
+  size_t free_b = 0, tot_b = 0;
+  cudaMemGetInfo(&free_b, &tot_b);
+  const uint64_t budget_records =
+      std::max<uint64_t>(1, (o.log_budget_mb ? (uint64_t)o.log_budget_mb << 20
+                                             : std::min<uint64_t>(96ull << 30, (uint64_t)free_b / 2)) / 8);
+  uint64_t wave_max = 0;
+  {
+    Wave cur{0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t li = 0; li < b->launches.size(); ++li) {
+      LaunchDev& d = b->launches[li];
+      const uint64_t need = (uint64_t)d.grid * d.log_cap;
+      if (cur.li1 > cur.li0 && cur.log_records + need > budget_records) {
+        b->waves.push_back(cur);
+        wave_max = std::max(wave_max, cur.log_records);
+        cur = Wave{li, li, d.block_base, d.block_base, 0, 0, 0};
+      }
+      d.log_base = cur.log_records;
+      cur.log_records += need;
+      cur.li1 = li + 1;
+      cur.gb1 = d.block_base + d.grid;
+    }
+    if (cur.li1 > cur.li0) {
+      b->waves.push_back(cur);
+      wave_max = std::max(wave_max, cur.log_records);
+    }
+  }
+  b->log_records = wave_max;
+
+  // ---- batched work items: per wave, launch-index order, blocks in chunks of `groups`
+  b->batched_smem = 0;
+  for (Wave& w : b->waves) {
+    w.item0 = (uint32_t)b->items.size();
+    uint32_t maxl = 0;
+    for (uint32_t li = w.li0; li < w.li1; ++li) maxl = std::max(maxl, b->launches[li].launch);
+    for (uint32_t lv = 0; lv <= maxl; ++lv)
+      for (uint32_t li = w.li0; li < w.li1; ++li) {
+        const LaunchDev& d = b->launches[li];
+        if (d.launch != lv) continue;
+        for (uint32_t blk = 0; blk < d.grid; blk += d.groups) b->items.push_back(make_uint2(li, blk));
+        b->batched_smem = std::max(b->batched_smem, d.ir_bytes + d.groups * d.group_bytes);
+      }
+    w.item1 = (uint32_t)b->items.size();
+  }
+  b->check_ctas = (uint32_t)c->sms * o.check_ctas_per_sm;
+
+  // ---- device buffers
+  int rc = SR_OK;
+  const size_t nl = b->launches.size();
+  const uint32_t nwaves = (uint32_t)b->waves.size();
+  b->out_cap = o.report_cap ? o.report_cap : (1u << 20);
+  struct A { DevBuf* buf; size_t bytes; const char* what; } allocs[] = {
+      {&b->code, b->total_code * 8, "code"},
+      {&b->launches_d, std::max<size_t>(1, nl) * sizeof(LaunchDev), "launch table"},
+      {&b->arena_init, b->total_arena * 4, "initial arenas"},
+      {&b->arena_work, b->total_arena * 4, "working arenas"},
+      {&b->log, b->log_records * 8, "access log"},
+      {&b->blocks, (size_t)b->nblocks * sizeof(sr::BlockRes), "block results"},
+      {&b->prog_status, (size_t)n * 4, "status"},
+      {&b->prog_abort, (size_t)n * 4, "abort marks"},
+      {&b->counters, sizeof(sr::Counters), "counters"},
+      {&b->items_d, std::max<size_t>(1, b->items.size()) * 8, "work items"},
+      {&b->queue_head, (size_t)nwaves * 4, "queue heads"},
+      {&b->launch_done, std::max<size_t>(1, nl) * 4, "launch completion"},
+      {&b->scratch, (size_t)b->check_ctas * sr::kScratchWords * 16, "checker scratch"},
+      {&b->work_head, (size_t)nwaves * 4, "checker queue"},
+      {&b->err_flag, 4, "error flag"},
+      {&b->offsets, ((size_t)b->nblocks + 1) * 8, "report offsets"},
+      {&b->partials, sr::compact_partials_count(b->nblocks) * 8, "scan partials"},
+      {&b->out, b->out_cap * sizeof(sr_report), "reports"},
+      {&b->total, 8, "report total"},
+  };
+  for (auto& a : allocs) {
+    rc = alloc_buf(c, *a.buf, a.bytes, s, a.what);
+    if (rc) {
+      free_batch_buffers(c, b, s);
+      delete b;
+      return rc;
+    }
+  }
+  auto up = [&](DevBuf& d, const void* src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(d.p, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  cudaError_t e = up(b->code, code.data(), code.size() * 8);
+  if (e == cudaSuccess) e = up(b->launches_d, b->launches.data(), nl * sizeof(LaunchDev));
+  if (e == cudaSuccess) e = up(b->items_d, b->items.data(), b->items.size() * 8);
+  for (uint32_t i = 0; i < n && e == cudaSuccess; ++i)
+    if (progs[i].global_words)
+      e = cudaMemcpyAsync((int32_t*)b->arena_init.p + b->arena_off[i], progs[i].global_init,
+                          progs[i].global_words * 4, cudaMemcpyHostToDevice, s);
+  // host buffers are caller-owned: the copies must finish before we return
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_batch_buffers(c, b, s);
+    delete b;
+    return fail(c, SR_E_CUDA, "upload failed: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return SR_OK;
+}
+
+int run_and_check(sr_ctx* c, sr_batch* b, void* stream) {
+  if (!c || !b) return fail(c, SR_E_INVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  b->stream = s;
+  b->ran = true;
+  const bool profile = c->opts.profile != 0;
+  if (c->opts.use_graph && c->opts.mode == SR_MODE_BATCHED && !profile) {
+    if (!b->graph || b->graph_stream != s) {
+      if (b->graph) cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+      cudaStream_t cap;
+      CUDA_TRY(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      CUDA_TRY(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      int rc = enqueue_run(c, b, cap, false);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cap, &g);
+      cudaStreamDestroy(cap);
+      if (rc) return rc;
+      if (e != cudaSuccess) return fail(c, SR_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(c, SR_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+      b->graph_stream = s;
+    }
+    CUDA_TRY(c, cudaGraphLaunch(b->graph, s));
+    return SR_OK;
+  }
+  return enqueue_run(c, b, s, profile);
+}
+
+int fetch_reports(sr_ctx* c, sr_batch* b, sr_report* dst, uint64_t cap, uint64_t* n_total) {
+  if (!c || !b) return fail(c, SR_E_INVAL, "null argument");
+  if (!b->ran) return fail(c, SR_E_INVAL, "run_and_check has not been called");
+  cudaStream_t s = b->stream;
+  unsigned long long total = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&total, b->total.p, 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (total > b->out_cap) {
+    // the report buffer was too small: grow it and run again (runs are deterministic)
+    dev_free(c, b->out, s);
+    b->out_cap = total + total / 8 + 1024;
+    int rc = alloc_buf(c, b->out, b->out_cap * sizeof(sr_report), s, "reports");
+    if (rc) return rc;
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    rc = run_and_check(c, b, s);
+    if (rc) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(&total, b->total.p, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+  }
+  uint32_t err = 0;
+  CUDA_TRY(c, cudaMemcpy(&err, b->err_flag.p, 4, cudaMemcpyDeviceToHost));
+  if (n_total) *n_total = total;
+  if (err) return fail(c, SR_E_TIMEOUT, "the race checker's staging wait gave up");
+  if (!dst) return SR_OK;
+  if (cap < total) return fail(c, SR_E_RANGE, "report buffer holds %llu, %llu needed", (unsigned long long)cap, total);
+  if (total) CUDA_TRY(c, cudaMemcpyAsync(dst, b->out.p, total * sizeof(sr_report), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
+  return SR_OK;
+}
+
+int fetch_memory(sr_ctx* c, sr_batch* b, uint32_t prog, int32_t* dst, uint64_t cap_words, uint64_t* n_words) {
+  if (!c || !b) return fail(c, SR_E_INVAL, "null argument");
+  if (prog >= b->nprogs) return fail(c, SR_E_INVAL, "program %u out of range", prog);
+  const uint64_t nw = b->arena_words[prog];
+  if (n_words) *n_words = nw;
+  if (!dst) return SR_OK;
+  if (cap_words < nw) return fail(c, SR_E_RANGE, "arena has %llu words", (unsigned long long)nw);
+  const DevBuf& src = b->ran ? b->arena_work : b->arena_init;
+  if (nw)
+    CUDA_TRY(c, cudaMemcpyAsync(dst, (int32_t*)src.p + b->arena_off[prog], nw * 4, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(b->stream));
+  return SR_OK;
+}
+
+int sr_batch_status(sr_ctx* c, sr_batch* b, uint32_t prog, uint32_t* status) {
+  if (!c || !b || !status) return fail(c, SR_E_INVAL, "null argument");
+  if (prog >= b->nprogs) return fail(c, SR_E_INVAL, "program %u out of range", prog);
+  CUDA_TRY(c, cudaMemcpyAsync(status, (uint32_t*)b->prog_status.p + prog, 4, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(b->stream));
+  return SR_OK;
+}
+
+int sr_batch_stats(sr_ctx* c, sr_batch* b, sr_stats* out) {
+  if (!c || !b || !out) return fail(c, SR_E_INVAL, "null argument");
+  memset(out, 0, sizeof(*out));
+  sr::Counters k{};
+  CUDA_TRY(c, cudaMemcpyAsync(&k, b->counters.p, sizeof k, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(b->stream));
+  out->thread_instrs = k.thread_instrs;
+  out->shared_accesses = k.shared_accesses;
+  out->global_accesses = k.global_accesses;
+  out->reports = k.total_reports;
+  out->log_bytes = b->log_records * 8;
+  out->blocks = b->nblocks;
+  if (c->opts.profile && b->nevents_used >= 2) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, b->events[0], b->events[1]);
+    out->ms_reset = ms;
+    // per wave: interp, check, compact marks follow
+    for (uint32_t i = 1; i + 3 < b->nevents_used; i += 3) {   // per wave: interp, check, compact
+      float t;
+      cudaEventElapsedTime(&t, b->events[i], b->events[i + 1]);
+      out->ms_interp += t;
+      cudaEventElapsedTime(&t, b->events[i + 1], b->events[i + 2]);
+      out->ms_check += t;
+      cudaEventElapsedTime(&t, b->events[i + 2], b->events[i + 3]);
+      out->ms_compact += t;
+    }
+  }
+  return SR_OK;
+}
+
+void sr_free_batch(sr_ctx* c, sr_batch* b) {
+  if (!c || !b) return;
+  cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  free_batch_buffers(c, b, b->stream);
+  cudaStreamSynchronize(b->stream);
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// sr_internal.h - device-side data layout shared by the kernels and the host runtime of
+// libsimtcheck.  Nothing here is part of the public C ABI (include/simtcheck.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "simtcheck.h"
+
+namespace sr {
+
+constexpr uint32_t kRegRows = 17;     // r0..r15 + one zero row; packed RZ fields point at row 16
+constexpr uint32_t kZeroReg = 16;
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr uint32_t kMaxBudget = 1u << 26;  // epochs and rounds stay below 2^26
+
+// thread status of a simulated thread
+enum : uint32_t { ST_RUN = 0, ST_WAIT = 1, ST_EXIT = 2, ST_NONE = 3 };
+// access kinds inside a log record
+enum : uint32_t { K_R = 0, K_W = 1, K_A = 2 };
+// per-block flags
+enum : uint32_t { BF_OVERFLOW = 1, BF_INTERNAL = 2 };
+
+// Access-log record (8 bytes):
+//   bits 63..38 epoch (26) | 37..24 word address (14) | 23..14 tid (10) | 13..12 kind | 11..0 pc
+// The high 40 bits (epoch, address) are the sort key of the race check.
+__host__ __device__ constexpr uint64_t make_record(uint32_t epoch, uint32_t addr, uint32_t tid,
+                                                   uint32_t kind, uint32_t pc) {
+  return (uint64_t)epoch << 38 | (uint64_t)addr << 24 | (uint64_t)(tid << 14 | kind << 12 | pc);
+}
+__host__ __device__ constexpr uint32_t rec_epoch(uint64_t r) { return (uint32_t)(r >> 38); }
+__host__ __device__ constexpr uint32_t rec_addr(uint64_t r) { return (uint32_t)(r >> 24) & 0x3FFFu; }
+__host__ __device__ constexpr uint32_t rec_tid(uint64_t r) { return (uint32_t)(r >> 14) & 0x3FFu; }
+__host__ __device__ constexpr uint32_t rec_kind(uint64_t r) { return (uint32_t)(r >> 12) & 3u; }
+__host__ __device__ constexpr uint32_t rec_pc(uint64_t r) { return (uint32_t)r & 0xFFFu; }
+
+// One (program, launch) pair, in canonical order.
+struct LaunchDev {
+  uint32_t prog, launch, entry, ncode;   // ncode without the EXIT sentinel
+  uint32_t code_off, grid, bdim, shw;    // code_off in instructions (even)
+  int32_t params[4];
+  uint32_t nparams, block_base, log_cap, key_bits;   // log_cap records per block (even)
+  uint64_t log_base;                     // record offset of block 0's region
+  uint64_t arena_off, arena_words;       // word offset of the program's working arena
+  uint32_t groups, group_bytes;          // batched mode: blocks per CTA, smem per block
+  uint32_t ir_bytes, pad;                // smem bytes of the staged code
+};
+
+// Per simulated block, written by the interpreter (n_log, n_misc, flags) and the checker (n_race).
+struct BlockRes { uint32_t n_log, n_race, n_misc, flags; };
+
+struct Counters {
+  unsigned long long thread_instrs, global_accesses, total_reports, shared_accesses;
+};
+
+struct RunArgs {
+  const LaunchDev* launches;
+  uint32_t nlaunches;
+  uint32_t budget, check_races, spin_limit;
+  const uint2* code;            // packed instructions of all programs
+  int32_t* arena;               // working arenas of all programs
+  unsigned long long* log;      // access-log pool
+  BlockRes* blocks;
+  uint32_t* prog_status;        // SR_ST_* bits
+  uint32_t* prog_abort;         // lowest launch index that stopped the program (or ~0)
+  Counters* counters;
+  // batched mode
+  const uint2* items;           // (launch index, first block)
+  uint32_t nitems;
+  uint32_t* queue_head;
+  uint32_t* launch_done;        // completed blocks per launch
+};
+
+// Shared-memory footprint of one simulated block in the interpreter.
+struct GroupLayout {
+  uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, total;
+};
+__host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+__host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode) {
+  GroupLayout g;
+  uint32_t o = 0;
+  g.regs = o; o += align16(kRegRows * nthr * 4u);
+  g.sh = o;   o += align16(shw * 4u);
+  g.clk = o;  o += 32 * 4;
+  g.rlo = o;  o += 32 * 4;
+  g.rhi = o;  o += 32 * 4;
+  g.rsp = o;  o += 32 * 4;
+  g.park = o; o += 32 * 8 * 4;
+  g.err = o;  o += align16(2u * (ncode + 1) * 4u);
+  g.bv = o;   o += 64;
+  g.total = o;
+  return g;
+}
+__host__ __device__ inline uint32_t ir_smem_bytes(uint32_t ncode) {
+  return align16(((ncode + 2u) & ~1u) * 8u);   // ncode + EXIT sentinel, even count
+}
+
+// kernel launchers (defined in the .cu files); attributes are set once per process
+cudaError_t init_kernel_attributes(uint32_t smem_optin);
+cudaError_t init_interp_attributes(uint32_t smem_optin);
+cudaError_t init_check_attributes(uint32_t smem_optin);
+cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, cudaStream_t s);
+cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, cudaStream_t s);
+uint32_t interp_plain_smem(const LaunchDev& L);
+
+struct CheckArgs {
+  const LaunchDev* launches;
+  uint32_t nlaunches;
+  uint32_t gb0, gb1;            // block range of the wave
+  unsigned long long* log;
+  BlockRes* blocks;
+  uint4* scratch;               // per checker CTA: 1 << 14 summaries (large intervals)
+  uint32_t* work_head;
+  uint32_t* error_flag;
+  uint32_t spin_limit;
+  uint32_t max_key_bits;        // largest address width over the launches (<= 14)
+};
+cudaError_t launch_check(const CheckArgs& a, uint32_t ctas, cudaStream_t s);
+uint32_t check_smem_bytes_bits(uint32_t max_bits);
+constexpr uint32_t kCheckThreads = 512;
+constexpr uint32_t kCheckTile = 4096;          // records per staged tile
+constexpr uint32_t kScratchWords = 1u << 14;   // summaries per CTA in the large-interval path
+
+struct CompactArgs {
+  const LaunchDev* launches;
+  uint32_t nlaunches;
+  uint32_t gb0, gb1;            // block range of the wave
+  unsigned long long* total;    // running report count over waves
+  const unsigned long long* log;
+  const BlockRes* blocks;
+  unsigned long long* offsets;  // nblocks + 1
+  unsigned long long* partials; // scan scratch
+  sr_report* out;
+  unsigned long long out_cap;
+  Counters* counters;
+};
+cudaError_t launch_compact_scan(const CompactArgs& a, cudaStream_t s);
+cudaError_t launch_compact_emit(const CompactArgs& a, cudaStream_t s);
+uint64_t compact_partials_count(uint32_t nblocks);
+
+}  // namespace sr

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work: final global arenas, the sorted report set and the program status must
+match bit for bit.  Sizes here span several tiles, ragged block sizes and every edge
+case of the method; the full-size workloads are checked on sampled blocks and through
+closed forms that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1211_6193_gb300.workloads import families, fig1, ir, stencil2d, tiny
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["plain", "batched"]
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1211_6193_gb300 import binding, build
+    build.build()
+    binding.load_library()
+    return binding
+
+
+def assert_parity(B, progs, mode="plain", oracle_kw=None, **opts):
+    want = oracle.run(progs, **(oracle_kw or {}))
+    got = B.check(progs, mode=mode, **opts)
+    gt, wt = got.report_tuples(), want.report_tuples()
+    if gt != wt:
+        gs, ws = set(gt), set(wt)
+        raise AssertionError(f"{mode}: reports differ: {len(gt)} vs {len(wt)}; "
+                             f"extra {sorted(gs - ws)[:5]} missing {sorted(ws - gs)[:5]}")
+    for i in range(len(progs)):
+        if not np.array_equal(got.arenas[i], want.arenas[i]):
+            bad = np.nonzero(got.arenas[i] != want.arenas[i])[0]
+            raise AssertionError(f"{mode}: program {i} ({progs[i].name}) arena differs at {bad[:8]} "
+                                 f"got {got.arenas[i][bad[:8]]} want {want.arenas[i][bad[:8]]}")
+    assert list(got.status & 3) == list(want.status), (got.status, want.status)
+    assert not np.any(got.status & (B.ST_LOG_OVERFLOW | B.ST_INTERNAL)), got.status
+    return got, want
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_fig1_and_variants(B, mode):
+    progs = [fig1.program(), fig1.program(race=True), fig1.program(deadlock=True)]
+    got, _ = assert_parity(B, progs, mode)
+    assert got.arenas[0][fig1.OUT_OFF] == 767
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_tiny_interleaving_programs(B, mode):
+    progs = tiny.tiny_batch(77, 60, nthreads=3, nsteps=6, nwords=3)
+    progs += tiny.tiny_batch(78, 30, nthreads=40, nsteps=6, nwords=5)     # two warps
+    assert_parity(B, progs, mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_family_batch_with_planted_bugs(B, mode):
+    progs = families.batch(n_programs=48, seed=3, max_grid=6, bug_rate=0.5)
+    assert_parity(B, progs, mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_plain_reduction_scaled(B, mode):
+    p = families.reduction_plain(n_blocks=40, bdim=1024, seed=1, omit_level=3)
+    got, _ = assert_parity(B, [p], mode)
+    assert len(got.reports) == 40 * 32
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_stencil2d_scaled(B, mode):
+    p = stencil2d.program(log2w=7, steps=4, buggy_launch=2, seed=4)
+    got, _ = assert_parity(B, [p], mode)
+    assert len(got.reports) == 16 * 1024
+
+
+def _lockstep_programs():
+    out = []
+    a = ir.Asm()      # same-round load vs store, atomics after stores, min-pc order
+    a.s2r(ir.r2, ir.TID).shr(ir.r3, ir.r2, 5).mov(ir.r4, 5).brnz(ir.r3, "w1")
+    a.sts(ir.RZ, ir.r4).sts(ir.RZ, ir.r4, 1).bra("join")
+    a.label("w1").lds(ir.r5, ir.RZ).mov(ir.r6, 1).atoms(ir.RZ, ir.r6, 1).lds(ir.r7, ir.RZ)
+    a.stg(ir.r2, ir.r5).stg(ir.r2, ir.r7, 64)
+    a.label("join").sts(ir.RZ, ir.r2, 2)
+    a.slt(ir.r8, ir.r2, 16).brnz(ir.r8, "hi").mov(ir.r9, 0).mov(ir.r9, 0).mov(ir.r9, 0)
+    a.lds(ir.r9, ir.RZ, 3).stg(ir.r2, ir.r9, 128).bra("end")
+    a.label("hi").mov(ir.r9, 7).sts(ir.RZ, ir.r9, 3)
+    a.label("end").bar()
+    a.brnz(ir.r2, "out").lds(ir.r10, ir.RZ).stg(ir.RZ, ir.r10, 192).lds(ir.r10, ir.RZ, 1)
+    a.stg(ir.RZ, ir.r10, 193).lds(ir.r10, ir.RZ, 2).stg(ir.RZ, ir.r10, 194).lds(ir.r10, ir.RZ, 3)
+    a.stg(ir.RZ, ir.r10, 195).label("out").exit()
+    out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 3, 64, 4, ())], np.full(196, -1, np.int32)))
+    a = ir.Asm()      # many warps storing to one word in one round: highest tid wins
+    a.s2r(ir.r2, ir.TID).sts(ir.RZ, ir.r2).sts(ir.r2, ir.r2, 1).bar().brnz(ir.r2, "x")
+    a.lds(ir.r3, ir.RZ).stg(ir.RZ, ir.r3).label("x").exit()
+    for bdim in (64, 1000, 1024):
+        out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 2, bdim, 1025, ())], np.zeros(1, np.int32)))
+    a = ir.Asm()      # stores and atomic adds to the same word in one round
+    a.s2r(ir.r2, ir.TID).shr(ir.r3, ir.r2, 5).mov(ir.r4, 10).mov(ir.r5, 1).brnz(ir.r3, "w1")
+    a.sts(ir.RZ, ir.r4).bra("j")
+    a.label("w1").atoms(ir.RZ, ir.r5).label("j").bar()
+    a.brnz(ir.r2, "x").lds(ir.r6, ir.RZ).stg(ir.RZ, ir.r6).label("x").exit()
+    out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 1, 256, 1, ())], np.zeros(1, np.int32)))
+    return out
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_round_semantics_programs(B, mode):
+    assert_parity(B, _lockstep_programs(), mode)
+
+
+def _edge_programs():
+    out = []
+    p = fig1.program()
+    out.append(ir.Program(p.code, [0], [], np.arange(5, dtype=np.int32), name="no_launch"))
+    a = ir.Asm()      # errors: x/0, x%0, shared and global out of bounds
+    a.s2r(ir.r2, ir.TID).mov(ir.r4, 5).div(ir.r6, ir.r4, ir.RZ).rem(ir.r7, ir.r4, 0).add(ir.r8, ir.r2, -3)
+    a.lds(ir.r9, ir.r8).ldg(ir.r10, ir.r2, 100).sts(ir.r2, ir.r2, -3).bar().atoms(ir.r2, ir.r4, -4)
+    a.add(ir.r11, ir.r6, ir.r7).add(ir.r11, ir.r11, ir.r9).add(ir.r11, ir.r11, ir.r10).stg(ir.r2, ir.r11)
+    a.stg(ir.r2, ir.r2, 1).exit()
+    out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 2, 40, 4, (0,))], np.full(40, 77, np.int32)))
+    a = ir.Asm()      # no shared memory at all, 1-thread blocks, ragged block sizes
+    a.s2r(ir.r2, ir.TID).s2r(ir.r3, ir.BID).s2r(ir.r4, ir.BDIM).mul(ir.r5, ir.r3, ir.r4).add(ir.r5, ir.r5, ir.r2)
+    a.mul(ir.r6, ir.r5, 3).add(ir.r6, ir.r6, 1).stg(ir.r5, ir.r6).exit()
+    for g, b in ((1, 1), (7, 33), (3, 1000), (2, 1024)):
+        out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, g, b, 0, ())], np.zeros(g * b, np.int32)))
+    a = ir.Asm()      # the largest shared array: every thread sweeps 12 words of 12288
+    a.s2r(ir.r2, ir.TID)
+    for j in range(12):
+        a.sts(ir.r2, ir.r2, 1024 * j)
+    a.bar()
+    for j in range(12):
+        a.lds(ir.r3, ir.r2, 1024 * j).add(ir.r4, ir.r4, ir.r3)
+    a.stg(ir.r2, ir.r4).exit()
+    out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 2, 1024, 12288, ())], np.zeros(1024, np.int32)))
+    a = ir.Asm()      # endless loop stopped by the round budget; the next launch is skipped
+    a.s2r(ir.r2, ir.TID).label("top").add(ir.r3, ir.r3, 1).sts(ir.r2, ir.r3).bra("top")
+    out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 2, 70, 70, ()), ir.Launch(0, 1, 32, 32, ())],
+                          np.zeros(1, np.int32), name="budget"))
+    # a 4096-instruction program (filler) with a reduction tail
+    spec = families.FamilySpec("reduction", 3, 96, 96, 4096 - 64, None, 0)
+    out.append(families.build_family(spec, seed=4))
+    return out
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_edge_cases(B, mode):
+    progs = _edge_programs()
+    assert max(p.ncode for p in progs) <= ir.MAX_CODE
+    assert_parity(B, progs, mode, oracle_kw={"round_budget": 3000}, round_budget=3000,
+                  loop_log_records=1 << 18)
+
+
+def test_race_check_disabled_keeps_memory_and_barrier_reports(B):
+    progs = families.batch(n_programs=24, seed=8, max_grid=4, bug_rate=0.6)
+    want = oracle.run(progs, check_races=False)
+    got = B.check(progs, mode="batched", check_races=False)
+    assert got.report_tuples() == want.report_tuples()
+    assert all(np.array_equal(a, b) for a, b in zip(got.arenas, want.arenas))
+    assert not any(r[0] == oracle.RACE for r in got.report_tuples())
+
+
+def test_waves_and_graph_and_repeat(B):
+    progs = families.batch(n_programs=40, seed=12, max_grid=12, bug_rate=0.4)
+    want = oracle.run(progs)
+    with B.Context(mode="batched", use_graph=True, log_budget_mb=1, report_cap=16) as ctx:
+        with ctx.load_programs(progs) as b:
+            for _ in range(3):                    # graph replays give identical results
+                b.run_and_check()
+                assert [tuple(int(x) for x in r) for r in b.fetch_reports()] == want.report_tuples()
+                for i in range(len(progs)):
+                    assert np.array_equal(b.fetch_memory(i), want.arenas[i])
+
+
+def test_log_overflow_is_reported_not_silent(B):
+    a = ir.Asm()
+    a.s2r(ir.r2, ir.TID).mov(ir.r3, 50).label("l").sts(ir.r2, ir.r3).sub(ir.r3, ir.r3, 1).brnz(ir.r3, "l").exit()
+    p = ir.Program(a.assemble(), [0], [ir.Launch(0, 1, 64, 64, ())], np.zeros(1, np.int32))
+    got = B.check([p], loop_log_records=64)
+    assert got.status[0] & B.ST_LOG_OVERFLOW
+
+
+def test_full_size_plain_reduction(B):
+    """The 2^24-element workload (16384 blocks x 1024 threads): block sums in closed form,
+    the 32 races per block in closed form, and the first blocks against the oracle."""
+    p = families.reduction_plain()
+    got = B.check([p], mode="plain")
+    n = 16384 * 1024
+    sums = p.global_init[:n].astype(np.int64).reshape(16384, 1024).sum(axis=1).astype(np.int32)
+    assert np.array_equal(got.arenas[0][n:], sums)
+    assert got.status[0] == 0
+    rep = got.reports
+    assert len(rep) == 16384 * 32
+    assert np.all(rep["kind"] == oracle.RACE) and np.all(rep["epoch"] == 4)
+    j = np.tile(np.arange(32, dtype=np.uint32), 16384)
+    assert np.array_equal(rep["block"], np.repeat(np.arange(16384, dtype=np.uint32), 32))
+    assert np.array_equal(rep["a"], 32 + j) and np.array_equal(rep["b"], (j << 16) | (32 + j))
+    want = oracle.run([p], max_blocks=8)
+    assert got.report_tuples()[:8 * 32] == want.report_tuples()
+    assert got.stats.shared_accesses == 16384 * 4094
