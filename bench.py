@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-blocks", type=int, default=16384)
+    ap.add_argument("--interp-variant", type=int, default=0, choices=[0, 1, 2],
+                    help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
     ap.add_argument("--blocks", type=int, default=16384,
                     help="blocks of the reduction (default: the full 2^24-element workload; smaller only "
                          "for profiling captures)")
@@ -164,7 +166,7 @@ def run_native(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    ctx = binding.Context(mode=args.mode, profile=True)
+    ctx = binding.Context(mode=args.mode, profile=True, interp_variant=args.interp_variant)
     batch = ctx.load_programs([prog])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 129 MB L2
     for _ in range(max(3, args.warmup)):
@@ -233,7 +235,7 @@ def run_native(args):
     h2d = prog.global_init.nbytes + prog.code.nbytes
     d2h = out_arena.nbytes + n_reports * 32
     e2e_times = []
-    ctx_e2e = binding.Context(mode=args.mode, report_cap=max(16, n_reports))
+    ctx_e2e = binding.Context(mode=args.mode, report_cap=max(16, n_reports), interp_variant=args.interp_variant)
     for i in range(1 + min(args.steps, 5)):
         barrier()
         t0 = time.perf_counter()

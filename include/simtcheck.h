@@ -144,7 +144,8 @@ typedef struct {
   uint32_t mode;             /* SR_MODE_* */
   uint32_t ctas_per_sm;      /* batched interpreter CTAs per SM; 0 = 1 */
   uint32_t loop_log_records; /* log region (records per block) for kernels with loops; 0 = 65536 */
-  uint32_t check_ctas_per_sm;/* checker CTAs per SM; 0 = 2 */
+  uint32_t interp_variant;   /* plain-mode interpreter: 1 = one 1024-thread CTA per SM budget,
+                                2 = registers capped for two per SM, 0 = pick by occupancy */
   uint32_t use_graph;        /* batched mode: capture run_and_check once, replay as a CUDA graph */
   uint32_t profile;          /* record CUDA events between stages (sr_batch_stats) */
   uint32_t spin_limit;       /* device wait iterations before SR_ST_INTERNAL; 0 = 1 << 26 */

@@ -60,7 +60,7 @@ class sr_allocator(C.Structure):
 class sr_opts(C.Structure):
     _fields_ = [("check_races", C.c_uint32), ("round_budget", C.c_uint32), ("mode", C.c_uint32),
                 ("ctas_per_sm", C.c_uint32), ("loop_log_records", C.c_uint32),
-                ("check_ctas_per_sm", C.c_uint32), ("use_graph", C.c_uint32), ("profile", C.c_uint32),
+                ("interp_variant", C.c_uint32), ("use_graph", C.c_uint32), ("profile", C.c_uint32),
                 ("spin_limit", C.c_uint32), ("log_budget_mb", C.c_uint32), ("report_cap", C.c_uint32),
                 ("allocator", C.POINTER(sr_allocator))]
 
@@ -189,7 +189,7 @@ class Context:
     """An ``sr_ctx``: options + device; creates batches with the same-named entry points."""
 
     def __init__(self, check_races: bool = True, round_budget: int = 0, mode: str = "plain", ctas_per_sm: int = 0,
-                 loop_log_records: int = 0, check_ctas_per_sm: int = 0, use_graph: bool = False,
+                 loop_log_records: int = 0, interp_variant: int = 0, use_graph: bool = False,
                  profile: bool = False, spin_limit: int = 0, log_budget_mb: int = 0, report_cap: int = 0,
                  torch_allocator: bool = True):
         self.lib = load_library()
@@ -197,7 +197,7 @@ class Context:
         o = sr_opts()
         o.check_races, o.round_budget = int(check_races), round_budget
         o.mode = {"plain": MODE_PLAIN, "batched": MODE_BATCHED}[mode]
-        o.ctas_per_sm, o.loop_log_records, o.check_ctas_per_sm = ctas_per_sm, loop_log_records, check_ctas_per_sm
+        o.ctas_per_sm, o.loop_log_records, o.interp_variant = ctas_per_sm, loop_log_records, interp_variant
         o.use_graph, o.profile, o.spin_limit = int(use_graph), int(profile), spin_limit
         o.log_budget_mb, o.report_cap = log_budget_mb, report_cap
         if self.allocator is not None:

@@ -25,6 +25,7 @@ namespace {
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr uint32_t NT = kCheckThreads;
 constexpr uint32_t T = kCheckTile;
+constexpr uint32_t NB = kCheckBins;
 constexpr uint32_t NONE = 0xFFFFu;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -118,152 +119,199 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phas
   return false;
 }
 
-// ---------------------------------------------------------------- CTA scan
-// In-place exclusive scan of a[0..len) (shared memory) by all NT threads; returns the total.
-__device__ uint32_t cta_exclusive_scan(uint32_t* a, uint32_t len, uint32_t* wtot) {
-  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t per = (len + NT - 1) / NT;
-  const uint32_t b0 = min(len, tid * per), b1 = min(len, b0 + per);
-  uint32_t sum = 0;
-  for (uint32_t i = b0; i < b1; ++i) sum += a[i];
-  uint32_t inc = sum;
+// ---------------------------------------------------------------- CTA scans
+// Exclusive scan of one value per thread over the CTA; returns the prefix, total in *tot.
+__device__ uint32_t cta_scan_value(uint32_t v, uint32_t* wtot, uint32_t* tot) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t v = __shfl_up_sync(FULL, inc, o);
-    if (lane >= (uint32_t)o) inc += v;
+    const uint32_t y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= (uint32_t)o) inc += y;
   }
   if (lane == 31) wtot[wid] = inc;
   __syncthreads();
   if (wid == 0) {
-    const uint32_t v = lane < NT / 32 ? wtot[lane] : 0u;
-    uint32_t x = v;
+    const uint32_t x0 = lane < NT / 32 ? wtot[lane] : 0u;
+    uint32_t x = x0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(FULL, x, o);
       if (lane >= (uint32_t)o) x += y;
     }
-    if (lane < NT / 32) wtot[lane] = x - v;     // exclusive warp offsets
-    if (lane == 31) wtot[32] = x;               // total
+    if (lane < NT / 32) wtot[lane] = x - x0;
+    if (lane == 31) wtot[32] = x;
   }
   __syncthreads();
-  uint32_t run = wtot[wid] + inc - sum;
+  const uint32_t r = wtot[wid] + inc - v;
+  *tot = wtot[32];
+  __syncthreads();
+  return r;
+}
+
+// In-place exclusive scan of a[0..len) (shared memory); returns the total.
+__device__ uint32_t cta_exclusive_scan(uint32_t* a, uint32_t len, uint32_t* wtot) {
+  const uint32_t per = (len + NT - 1) / NT;
+  const uint32_t b0 = min(len, threadIdx.x * per), b1 = min(len, b0 + per);
+  uint32_t sum = 0;
+  for (uint32_t i = b0; i < b1; ++i) sum += a[i];
+  uint32_t total;
+  uint32_t run = cta_scan_value(sum, wtot, &total);
   for (uint32_t i = b0; i < b1; ++i) {
     const uint32_t v = a[i];
     a[i] = run;
     run += v;
   }
-  const uint32_t total = wtot[32];
   __syncthreads();
   return total;
 }
 
+constexpr uint32_t MAXSEG = 256;   // barrier intervals handled per staged tile
+
 struct Smem {
-  unsigned long long* tile;     // T + 2 staged records
+  unsigned long long* tile[2];  // T + 2 staged records each (double buffer)
   unsigned long long* sorted;   // T
-  uint32_t* bins;               // 1 << max key bits
-  uint32_t* flags;              // T (or bins) entries for the scans
-  uint32_t* touched;            // bitmap over addresses (large-interval path)
-  uint32_t* wtot;               // 33 scan words
-  uint32_t* misc;               // small broadcast words
+  uint32_t* sbin;               // T: bin of sorted[i]
+  uint32_t* bins;               // NB
+  uint32_t* flags;              // 2T
+  uint32_t* seg_start;          // MAXSEG + 1 (record index of each interval of the tile)
+  uint32_t* seg_lo;             // MAXSEG: lowest address of the interval
+  uint32_t* seg_hi;             // MAXSEG
+  uint32_t* seg_off;            // MAXSEG: first bin of the interval
+  uint32_t* touched;            // NB / 32 + 1 bitmap (large intervals)
+  uint32_t* wtot;               // 36 scan words
+  uint32_t* misc;               // broadcast words
 };
 
-// Sort the m records rec[0..m) by address into S.sorted; afterwards S.bins[x] is the end
-// (exclusive) of address x's run.
-__device__ void counting_sort(const Smem& S, const unsigned long long* rec, uint32_t m, uint32_t nb) {
+// Counting sort of records rec[0..m) (intervals s0..s0+nseg-1 of the tile, starting at
+// record seg_start[s0]) by (interval, address): each interval owns the bins of its own
+// address range, so the sorted order is exactly (epoch, address).  Returns the number
+// of intervals that fit the bin budget (at least one).  Afterwards sorted/sbin hold the
+// records and their bins, bins[b] is the end of bin b's run.
+__device__ uint32_t sort_intervals(const Smem& S, const unsigned long long* tile, uint32_t s0, uint32_t nseg,
+                                   uint32_t& m_out) {
   const uint32_t tid = threadIdx.x;
-  for (uint32_t i = tid; i < nb; i += NT) S.bins[i] = 0;
+  const uint32_t base = S.seg_start[s0], end = S.seg_start[s0 + nseg];
+  for (uint32_t i = tid; i < nseg; i += NT) { S.seg_lo[s0 + i] = 0xFFFFFFFFu; S.seg_hi[s0 + i] = 0; }
   __syncthreads();
-  for (uint32_t i = tid; i < m; i += NT) atomicAdd(&S.bins[rec_addr(rec[i])], 1u);
+  // per-interval address range: a warp whose 32 records share one interval reduces them
+  // first (one atomic pair per warp instead of per record)
+  for (uint32_t i0 = base + (tid & ~31u); i0 < end; i0 += NT) {
+    const uint32_t i = i0 + (tid & 31u);
+    const bool valid = i < end;
+    uint32_t sg = 0, a = 0;
+    if (valid) {
+      uint32_t lo = s0, hi = s0 + nseg - 1;     // interval of record i
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (S.seg_start[mid] <= i) lo = mid; else hi = mid - 1;
+      }
+      sg = lo;
+      a = rec_addr(tile[i]);
+    }
+    const uint32_t sg0 = __shfl_sync(FULL, sg, 0);
+    if (__all_sync(FULL, !valid || sg == sg0)) {
+      const uint32_t mn = __reduce_min_sync(FULL, valid ? a : 0xFFFFFFFFu);
+      const uint32_t mx = __reduce_max_sync(FULL, valid ? a : 0u);
+      if ((tid & 31u) == 0) {
+        atomicMin(&S.seg_lo[sg0], mn);
+        atomicMax(&S.seg_hi[sg0], mx);
+      }
+    } else if (valid) {
+      atomicMin(&S.seg_lo[sg], a);
+      atomicMax(&S.seg_hi[sg], a);
+    }
+  }
+  __syncthreads();
+  // bin offsets: a prefix of the intervals whose ranges fit NB bins together (one warp);
+  // a single range never exceeds NB, so at least one interval is always kept
+  if (tid < 32) {
+    uint32_t run = 0, kept = 0;
+    for (uint32_t c = 0; c < nseg; c += 32) {
+      const uint32_t i = c + tid;
+      const uint32_t r = i < nseg ? S.seg_hi[s0 + i] - S.seg_lo[s0 + i] + 1 : 0u;
+      uint32_t inc = r;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (tid >= (uint32_t)o) inc += y;
+      }
+      const bool fits = i < nseg && run + inc <= NB;   // a prefix of the lanes (inc grows)
+      const uint32_t nf = __popc(__ballot_sync(FULL, fits));
+      if (fits) S.seg_off[s0 + i] = run + inc - r;
+      if (nf) run += __shfl_sync(FULL, inc, nf - 1);
+      kept += nf;
+      if (nf < 32) break;
+    }
+    if (tid == 0) { S.misc[0] = kept; S.misc[1] = run; }
+  }
+  __syncthreads();
+  const uint32_t kept = S.misc[0], nb = S.misc[1];
+  const uint32_t mend = S.seg_start[s0 + kept];
+  const uint32_t m = mend - base;
+  for (uint32_t b = tid; b < nb; b += NT) S.bins[b] = 0;
+  __syncthreads();
+  for (uint32_t i = base + tid; i < mend; i += NT) {
+    uint32_t lo = s0, hi = s0 + kept - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (S.seg_start[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t b = S.seg_off[lo] + rec_addr(tile[i]) - S.seg_lo[lo];
+    S.flags[T + (i - base)] = b;
+    atomicAdd(&S.bins[b], 1u);
+  }
   __syncthreads();
   cta_exclusive_scan(S.bins, nb, S.wtot);
   for (uint32_t i = tid; i < m; i += NT) {
-    const unsigned long long r = rec[i];
-    S.sorted[atomicAdd(&S.bins[rec_addr(r)], 1u)] = r;
+    const uint32_t b = S.flags[T + i];
+    const uint32_t pos = atomicAdd(&S.bins[b], 1u);
+    S.sorted[pos] = tile[base + i];
+    S.sbin[pos] = b;
   }
   __syncthreads();
+  m_out = m;
+  return kept;
 }
 
-// One complete barrier interval held in shared memory: emit its race entries in
-// address order at out[*race_out ...].
-__device__ void check_interval(const Smem& S, const unsigned long long* rec, uint32_t m, uint32_t epoch,
-                               uint32_t nb, uint4* out, uint32_t& race_out) {
-  const uint32_t tid = threadIdx.x, lane = tid & 31;
-  if (m <= 32) {
-    // warp path: group equal addresses with __match_any_sync
-    if (tid < 32) {
-      const bool valid = lane < m;
-      const unsigned long long r = valid ? rec[lane] : 0ull;
-      const uint32_t addr = valid ? rec_addr(r) : 0u;
-      const uint32_t grp = __match_any_sync(FULL, valid ? addr : (0x80000000u | lane));
-      const bool leader = valid && lane == (uint32_t)(__ffs(grp) - 1);
-      bool racy = false;
-      uint32_t b = 0, c = 0;
-      if (leader) {
-        Summ s = summ_empty();
-        for (uint32_t g = grp; g; g &= g - 1) summ_add(s, rec[__ffs(g) - 1]);
-        racy = summ_race(s, b, c);
-      }
-      const uint32_t rm = __ballot_sync(FULL, racy);
-      uint32_t rank = 0;
-      for (uint32_t g = rm; g; g &= g - 1) {
-        const uint32_t aj = __shfl_sync(FULL, addr, __ffs(g) - 1);
-        rank += aj < addr;
-      }
-      if (racy) out[race_out + rank] = make_uint4(epoch, addr, b, c);
-      race_out += __popc(rm);
-      if (tid == 0) S.misc[0] = race_out;
-    }
-    __syncthreads();
-    race_out = S.misc[0];
-    __syncthreads();
-    return;
-  }
-  counting_sort(S, rec, m, nb);
-  // run heads: summary of [i, end of run) -> racy flag
+__device__ __forceinline__ Summ run_summary(const Smem& S, uint32_t i, uint32_t end) {
+  Summ s = summ_empty();
+  for (uint32_t j = i; j < end; ++j) summ_add(s, S.sorted[j]);
+  return s;
+}
+
+// Race entries of sorted intervals, in (epoch, address) order, at out[race_out ...].
+__device__ void emit_races(const Smem& S, uint32_t m, uint4* out, uint32_t& race_out) {
+  const uint32_t tid = threadIdx.x;
   for (uint32_t i = tid; i < m; i += NT) {
-    const unsigned long long r = S.sorted[i];
-    const uint32_t a = rec_addr(r);
     uint32_t f = 0;
-    if (i == 0 || rec_addr(S.sorted[i - 1]) != a) {
-      Summ s = summ_empty();
-      const uint32_t end = S.bins[a];
-      for (uint32_t j = i; j < end; ++j) summ_add(s, S.sorted[j]);
+    if (i == 0 || S.sbin[i] != S.sbin[i - 1]) {
       uint32_t b, c;
-      f = summ_race(s, b, c);
+      f = summ_race(run_summary(S, i, S.bins[S.sbin[i]]), b, c);
     }
     S.flags[i] = f;
+    S.flags[T + i] = f;
   }
-  __syncthreads();
-  // keep the flags: the scan below turns them into output positions
-  for (uint32_t i = tid; i < m; i += NT) S.flags[T + i] = S.flags[i];
   __syncthreads();
   const uint32_t total = cta_exclusive_scan(S.flags, m, S.wtot);
   for (uint32_t i = tid; i < m; i += NT) {
     if (!S.flags[T + i]) continue;
-    const uint32_t a = rec_addr(S.sorted[i]);
-    Summ s = summ_empty();
-    const uint32_t end = S.bins[a];
-    for (uint32_t j = i; j < end; ++j) summ_add(s, S.sorted[j]);
+    const unsigned long long r = S.sorted[i];
     uint32_t b = 0, c = 0;
-    summ_race(s, b, c);
-    out[race_out + S.flags[i]] = make_uint4(epoch, a, b, c);
+    summ_race(run_summary(S, i, S.bins[S.sbin[i]]), b, c);
+    out[race_out + S.flags[i]] = make_uint4(rec_epoch(r), rec_addr(r), b, c);
   }
   race_out += total;
   __syncthreads();
 }
 
-// Part of an interval that does not fit one tile: fold its run summaries into the
-// per-CTA table (each address once per chunk, so no atomics on the table itself).
-__device__ void fold_chunk(const Smem& S, const unsigned long long* rec, uint32_t m, uint32_t nb, uint4* table) {
+// A chunk of an interval larger than a tile: fold run summaries into the per-CTA table.
+__device__ void fold_sorted(const Smem& S, uint32_t m, uint4* table) {
   const uint32_t tid = threadIdx.x;
-  counting_sort(S, rec, m, nb);
   for (uint32_t i = tid; i < m; i += NT) {
-    const unsigned long long r = S.sorted[i];
-    const uint32_t a = rec_addr(r);
-    if (i != 0 && rec_addr(S.sorted[i - 1]) == a) continue;
-    Summ s = summ_empty();
-    const uint32_t end = S.bins[a];
-    for (uint32_t j = i; j < end; ++j) summ_add(s, S.sorted[j]);
+    if (i != 0 && S.sbin[i] == S.sbin[i - 1]) continue;
+    Summ s = run_summary(S, i, S.bins[S.sbin[i]]);
+    const uint32_t a = rec_addr(S.sorted[i]);
     const uint32_t bit = 1u << (a & 31);
     if (atomicOr(&S.touched[a >> 5], bit) & bit) {
       const uint4 o = table[a];
@@ -276,137 +324,187 @@ __device__ void fold_chunk(const Smem& S, const unsigned long long* rec, uint32_
 }
 
 // End of a large interval: races of every touched address, in address order.
-__device__ void finish_large(const Smem& S, uint32_t epoch, uint32_t nb, uint4* table, uint4* out,
-                             uint32_t& race_out) {
+__device__ void finish_large(const Smem& S, uint32_t epoch, uint4* table, uint4* out, uint32_t& race_out) {
   const uint32_t tid = threadIdx.x;
-  for (uint32_t a = tid; a < nb; a += NT) {
+  for (uint32_t a = tid; a < NB; a += NT) {
     uint32_t f = 0;
     if (S.touched[a >> 5] & (1u << (a & 31))) {
       const uint4 o = table[a];
       uint32_t b, c;
       f = summ_race(Summ{o.x, o.y, o.z, o.w}, b, c);
     }
-    S.flags[a] = f;
+    S.bins[a] = f;
   }
   __syncthreads();
-  const uint32_t total = cta_exclusive_scan(S.flags, nb, S.wtot);
-  for (uint32_t a = tid; a < nb; a += NT) {          // racy flags re-derived from the table
+  const uint32_t total = cta_exclusive_scan(S.bins, NB, S.wtot);
+  for (uint32_t a = tid; a < NB; a += NT) {          // racy flags re-derived from the table
     if (!(S.touched[a >> 5] & (1u << (a & 31)))) continue;
     const uint4 o = table[a];
     uint32_t b = 0, c = 0;
-    if (summ_race(Summ{o.x, o.y, o.z, o.w}, b, c)) out[race_out + S.flags[a]] = make_uint4(epoch, a, b, c);
+    if (summ_race(Summ{o.x, o.y, o.z, o.w}, b, c)) out[race_out + S.bins[a]] = make_uint4(epoch, a, b, c);
   }
   __syncthreads();
   race_out += total;
-  for (uint32_t i = tid; i < nb / 32 + 1; i += NT) S.touched[i] = 0;
+  for (uint32_t i = tid; i < NB / 32 + 1; i += NT) S.touched[i] = 0;
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) k_check(CheckArgs A, uint32_t max_bits) {
+// Interval starts of tile[0..cnt) (records are in interval order): at most MAXSEG are
+// kept; returns their number and sets cnt_eff to the end of the last kept interval.
+__device__ uint32_t find_intervals(const Smem& S, const unsigned long long* tile, uint32_t cnt, uint32_t& cnt_eff) {
+  constexpr uint32_t PER = (T + NT - 1) / NT;
+  const uint32_t i0 = threadIdx.x * PER;
+  uint32_t f = 0, c = 0;
+  for (uint32_t j = 0; j < PER; ++j) {
+    const uint32_t i = i0 + j;
+    const bool st = i < cnt && (i == 0 || rec_epoch(tile[i]) != rec_epoch(tile[i - 1]));
+    f |= (uint32_t)st << j;
+    c += st;
+  }
+  uint32_t total;
+  uint32_t o = cta_scan_value(c, S.wtot, &total);
+  for (uint32_t j = 0; j < PER; ++j)
+    if (f >> j & 1u) {
+      if (o <= MAXSEG) S.seg_start[o] = i0 + j;
+      ++o;
+    }
+  __syncthreads();
+  const uint32_t nseg = min(total, MAXSEG);
+  if (total <= MAXSEG && threadIdx.x == 0) S.seg_start[nseg] = cnt;
+  __syncthreads();
+  cnt_eff = S.seg_start[nseg];
+  return nseg;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_check(CheckArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long mbar;
-  __shared__ uint32_t s_gb, s_li;
-  const uint32_t maxnb = 1u << max_bits;
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ uint32_t s_next;
   Smem S;
   unsigned char* p = smem;
-  S.tile = reinterpret_cast<unsigned long long*>(p); p += (T + 2) * 8;
+  S.tile[0] = reinterpret_cast<unsigned long long*>(p); p += (T + 2) * 8;
+  S.tile[1] = reinterpret_cast<unsigned long long*>(p); p += (T + 2) * 8;
   S.sorted = reinterpret_cast<unsigned long long*>(p); p += T * 8;
-  S.bins = reinterpret_cast<uint32_t*>(p); p += maxnb * 4;
-  S.flags = reinterpret_cast<uint32_t*>(p); p += max(2 * T, maxnb) * 4;
-  S.touched = reinterpret_cast<uint32_t*>(p); p += (maxnb / 32 + 1) * 4;
+  S.sbin = reinterpret_cast<uint32_t*>(p); p += T * 4;
+  S.bins = reinterpret_cast<uint32_t*>(p); p += NB * 4;
+  S.flags = reinterpret_cast<uint32_t*>(p); p += 2 * T * 4;
+  S.seg_start = reinterpret_cast<uint32_t*>(p); p += (MAXSEG + 4) * 4;
+  S.seg_lo = reinterpret_cast<uint32_t*>(p); p += MAXSEG * 4;
+  S.seg_hi = reinterpret_cast<uint32_t*>(p); p += MAXSEG * 4;
+  S.seg_off = reinterpret_cast<uint32_t*>(p); p += MAXSEG * 4;
+  S.touched = reinterpret_cast<uint32_t*>(p); p += (NB / 32 + 1) * 4;
   S.wtot = reinterpret_cast<uint32_t*>(p); p += 36 * 4;
   S.misc = reinterpret_cast<uint32_t*>(p);
   uint4* table = A.scratch + (size_t)blockIdx.x * kScratchWords;
   const uint32_t tid = threadIdx.x;
-  uint32_t phase = 0;
-  if (tid == 0) mbar_init(&mbar);
-  for (uint32_t i = tid; i < maxnb / 32 + 1; i += NT) S.touched[i] = 0;
-  __syncthreads();
+  uint32_t phases = 0;                           // bit b: mbarrier parity of buffer b
+  if (tid == 0) { mbar_init(&mbar[0]); mbar_init(&mbar[1]); }
+  for (uint32_t i = tid; i < NB / 32 + 1; i += NT) S.touched[i] = 0;
 
-  for (;;) {
-    __syncthreads();                                 // every thread is done with s_gb / s_li
+  // next block with a non-empty log, and the start of its staging into buffer `buf`
+  auto claim = [&](uint32_t buf) {
     if (tid == 0) {
-      const uint32_t gb = A.gb0 + atomicAdd(A.work_head, 1u);
-      s_gb = gb;
+      uint32_t gb;
+      for (;;) {
+        gb = A.gb0 + atomicAdd(A.work_head, 1u);
+        if (gb >= A.gb1 || A.blocks[gb].n_log) break;
+      }
       if (gb < A.gb1) {
-        uint32_t lo = 0, hi = A.nlaunches - 1;     // last launch with block_base <= gb
+        uint32_t lo = 0, hi = A.nlaunches - 1;
         while (lo < hi) {
           const uint32_t mid = (lo + hi + 1) >> 1;
           if (A.launches[mid].block_base <= gb) lo = mid; else hi = mid - 1;
         }
-        s_li = lo;
+        const LaunchDev* L = A.launches + lo;
+        const unsigned long long* region = A.log + L->log_base + (unsigned long long)(gb - L->block_base) * L->log_cap;
+        const uint32_t n = A.blocks[gb].n_log, cnt = min(T, n);
+        bulk_load(S.tile[buf], region, ((cnt + 1u) & ~1u) * 8u, &mbar[buf]);
+        S.misc[8] = lo;
       }
+      s_next = gb;
     }
     __syncthreads();
-    const uint32_t gb = s_gb;
-    if (gb >= A.gb1) break;
-    const uint32_t n = A.blocks[gb].n_log;
-    if (n == 0) continue;
-    const LaunchDev* L = A.launches + s_li;
-    const uint32_t nb = 1u << L->key_bits;
+    return s_next;
+  };
+
+  uint32_t cur = 0;
+  uint32_t gb = claim(cur);
+  while (gb < A.gb1) {
+    const LaunchDev* L = A.launches + S.misc[8];
     unsigned long long* region = A.log + L->log_base + (unsigned long long)(gb - L->block_base) * L->log_cap;
     uint4* out = reinterpret_cast<uint4*>(region);
-    uint32_t race_out = 0, pos = 0;
-    bool large = false;
-    uint32_t large_epoch = 0;
-    bool failed = false;
-    while (pos < n && !failed) {
+    const uint32_t n = A.blocks[gb].n_log;
+    uint32_t pos = 0, race_out = 0, large_epoch = 0, next_gb = A.gb1;
+    bool large = false, failed = false, prefetched = false;
+    while (pos < n) {
+      const bool ok = mbar_wait(&mbar[cur], (phases >> cur) & 1u, A.spin_limit);
+      phases ^= 1u << cur;
+      if (__syncthreads_or(!ok)) { failed = true; break; }
       const uint32_t off = pos & 1u, cnt = min(T, n - pos);
-      const uint32_t nload = (cnt + off + 1u) & ~1u;
-      if (tid == 0) bulk_load(S.tile, region + (pos - off), nload * 8u, &mbar);
-      const bool ok = mbar_wait(&mbar, phase, A.spin_limit);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {                   // agree on a (bounded) wait that gave up
-        failed = true;
-        break;
+      const unsigned long long* tile = S.tile[cur] + off;
+      const bool last_tile = pos + cnt == n;
+      if (last_tile && !prefetched) {            // stage the next block while this one is checked
+        next_gb = claim(cur ^ 1u);
+        prefetched = true;
       }
-      const unsigned long long* rec = S.tile + off;
-      uint32_t s = 0;
-      while (s < cnt) {
-        const uint32_t e = rec_epoch(rec[s]);
-        uint32_t lo = s, hi = cnt;                   // first index with a later epoch
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (rec_epoch(rec[mid]) <= e) lo = mid + 1; else hi = mid;
+      uint32_t cnt_eff;
+      const uint32_t nseg = find_intervals(S, tile, cnt, cnt_eff);
+      // the last interval of a tile may continue in the next tile unless the block ends here
+      const bool tail_open = !last_tile && cnt_eff == cnt;
+      uint32_t sidx = 0, consumed = 0;
+      if (large) {                               // the first interval continues the large one
+        uint32_t m;
+        sort_intervals(S, tile, 0, 1, m);
+        fold_sorted(S, m, table);
+        if (!(nseg == 1 && tail_open)) {
+          finish_large(S, large_epoch, table, out, race_out);
+          large = false;
         }
-        const uint32_t t_end = lo;
-        const bool complete = t_end < cnt || pos + cnt == n;
-        if (large && e == large_epoch) {
-          fold_chunk(S, rec + s, t_end - s, nb, table);
-          if (complete) {
-            finish_large(S, e, nb, table, out, race_out);
-            large = false;
-          }
-          s = t_end;
-          continue;
-        }
-        if (!complete) {
-          if (s > 0) break;                          // restage from the start of this interval
-          large = true;                              // interval larger than a tile
-          large_epoch = e;
-          fold_chunk(S, rec, t_end, nb, table);
-          s = t_end;
-          continue;
-        }
-        check_interval(S, rec + s, t_end - s, e, nb, out, race_out);
-        s = t_end;
+        sidx = 1;
+        consumed = S.seg_start[1];
       }
-      pos += s;
-      __syncthreads();                               // tile fully consumed before it is restaged
+      const uint32_t ncomplete = tail_open ? nseg - 1 : nseg;
+      while (!large && sidx < ncomplete) {
+        uint32_t m;
+        const uint32_t kept = sort_intervals(S, tile, sidx, ncomplete - sidx, m);
+        emit_races(S, m, out, race_out);
+        sidx += kept;
+        consumed = S.seg_start[sidx];
+      }
+      if (!large && sidx == 0 && tail_open) {     // one interval fills the whole tile
+        large = true;
+        large_epoch = rec_epoch(tile[0]);
+        uint32_t m;
+        sort_intervals(S, tile, 0, 1, m);
+        fold_sorted(S, m, table);
+        consumed = cnt;
+      }
+      pos += consumed;
+      if (pos < n) {                             // restage the rest of this block
+        if (tid == 0) {
+          const uint32_t o2 = pos & 1u, c2 = min(T, n - pos);
+          bulk_load(S.tile[cur], region + (pos - o2), ((c2 + o2 + 1u) & ~1u) * 8u, &mbar[cur]);
+        }
+        __syncthreads();
+      }
     }
     if (tid == 0) {
       A.blocks[gb].n_race = race_out;
       if (failed) atomicOr(A.error_flag, 1u);
     }
     if (failed) break;
+    if (!prefetched) next_gb = claim(cur ^ 1u);
+    gb = next_gb;
+    cur ^= 1u;
+    __syncthreads();
   }
 }
 
 }  // namespace
 
-uint32_t check_smem_bytes_bits(uint32_t max_bits) {
-  const uint32_t maxnb = 1u << max_bits;
-  return (T + 2) * 8 + T * 8 + maxnb * 4 + (2 * T > maxnb ? 2 * T : maxnb) * 4 + (maxnb / 32 + 1) * 4 + 36 * 4 + 16;
+uint32_t check_smem_bytes() {
+  return 2 * (T + 2) * 8 + T * 8 + T * 4 + NB * 4 + 2 * T * 4 + (MAXSEG + 4) * 4 + 3 * MAXSEG * 4 +
+         (NB / 32 + 1) * 4 + 36 * 4 + 64;
 }
 
 cudaError_t init_check_attributes(uint32_t smem_optin) {
@@ -423,7 +521,7 @@ cudaError_t init_kernel_attributes(uint32_t smem_optin) {
 }
 
 cudaError_t launch_check(const CheckArgs& a, uint32_t ctas, cudaStream_t s) {
-  k_check<<<ctas, NT, check_smem_bytes_bits(a.max_key_bits), s>>>(a, a.max_key_bits);
+  k_check<<<ctas, NT, check_smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -127,18 +127,23 @@ __device__ __forceinline__ int32_t alu(uint32_t op, int32_t x, int32_t y, bool& 
 // Wait until every other warp of the block has published a clock >= need.  With
 // `order` (store stage), also wait for lower warps whose store of this same round
 // (clock == need) touches an overlapping range of the same memory space.
+// `omin` is a lower bound of the other warps' clocks (clocks only grow within a
+// barrier interval); when it already decides the wait, no clock is read.
 __device__ __forceinline__ bool wait_clocks(const uint32_t* clk, const int32_t* rlo, const int32_t* rhi,
                                             const uint32_t* rsp, uint32_t nw, uint32_t w, uint32_t lane,
                                             uint32_t need, bool order, int32_t lo, int32_t hi, uint32_t sp,
-                                            uint32_t limit) {
+                                            uint32_t limit, uint32_t& omin) {
+  if (omin > need || (!order && omin == need)) return true;
   for (uint32_t it = 0; it < limit; ++it) {
     bool ok = true;
+    uint32_t c = kInf;
     if (lane < nw && lane != w) {
-      const uint32_t c = ld_acquire_cta(clk + lane);
+      c = ld_acquire_cta(clk + lane);
       ok = c >= need;
       if (ok && order && lane < w && c == need) ok = !(rsp[lane] == sp && rlo[lane] <= hi && lo <= rhi[lane]);
     }
     if (__all_sync(FULL, ok)) {
+      omin = __reduce_min_sync(FULL, c);
       __syncwarp();
       return true;
     }
@@ -231,8 +236,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nthr = nw * 32;
   const uint32_t tid = w * 32 + lane;
-  const uint32_t bdim = Ls->bdim, shw = Ls->shw, ncode = Ls->ncode, log_cap = Ls->log_cap;
-  const GroupLayout G = group_layout(nthr, shw, ncode);
+  const uint32_t bdim = Ls->bdim, shw = Ls->shw, ncode = Ls->ncode, log_cap = Ls->log_cap, nrows = Ls->nrows;
+  const GroupLayout G = group_layout(nthr, shw, ncode, nrows);
   uint32_t* regs = reinterpret_cast<uint32_t*>(gsm + G.regs);
   int32_t* sh = reinterpret_cast<int32_t*>(gsm + G.sh);
   uint32_t* clk = reinterpret_cast<uint32_t*>(gsm + G.clk);
@@ -247,10 +252,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   unsigned long long* region = A.log + Ls->log_base + (unsigned long long)block * log_cap;
   const bool logging = A.check_races != 0;
   const uint32_t budget = A.budget, spin = A.spin_limit;
+  uint32_t* myregs = regs + tid;                 // row r of this thread: myregs[r * nthr]
 
-  // ---- block start: registers = params then zeros, shared memory zeroed
-  for (uint32_t r = 0; r < kRegRows; ++r)
-    regs[r * nthr + tid] = (r < Ls->nparams) ? (uint32_t)Ls->params[r] : 0u;
+  // ---- block start: registers = params then zeros (the last row stays zero), shared zeroed
+  for (uint32_t r = 0; r < nrows; ++r) myregs[r * nthr] = (r < Ls->nparams) ? (uint32_t)Ls->params[r] : 0u;
   for (uint32_t i = tid; i < shw; i += nthr) sh[i] = 0;
   for (uint32_t i = tid; i <= ncode; i += nthr) {
     err[2 * i] = 0;
@@ -265,32 +270,33 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   group_sync(bar_id, nthr);
 
   uint32_t pc = Ls->entry, st = tid < bdim ? ST_RUN : ST_NONE, wpc = 0;
-  uint32_t k = 0, epoch = 0, front_cap = log_cap;
-  unsigned long long n_instr = 0, n_gacc = 0;
+  uint32_t k = 0, epoch = 0, front_cap = log_cap, omin = 0;
+  uint32_t n_instr = 0, n_gacc = 0;              // per lane: executed instructions, global accesses
+  const unsigned long long lane_rec = (unsigned long long)tid << 14;
+  unsigned long long epoch_rec = 0;              // epoch << 38
 
   for (;;) {  // barrier intervals
     bool limit = false, timeout = false;
     for (;;) {  // rounds
-      const uint32_t runm = __ballot_sync(FULL, st == ST_RUN);
-      if (runm == 0) break;
-      if (k >= budget) { limit = true; break; }
       const uint32_t p = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
+      if (p == kInf) break;                      // no runnable lane
+      if (k >= budget) { limit = true; break; }
       const bool act = (st == ST_RUN) && (pc == p);
-      const uint32_t actm = __ballot_sync(FULL, act);
       const uint2 ins = ir[p];
       const uint32_t op = ins.x & 0x3Fu;
       const uint32_t d = (ins.x >> 8) & 0xFFu, ra = (ins.x >> 16) & 0xFFu, rb = ins.x >> 24;
       const int32_t imm = (int32_t)ins.y;
-      const int32_t va = (int32_t)regs[ra * nthr + tid];
-      const int32_t vb = (ins.x & SR_BIMM) ? imm : (int32_t)regs[rb * nthr + tid];
+      const int32_t va = (int32_t)myregs[ra * nthr];
+      const int32_t vb = (ins.x & SR_BIMM) ? imm : (int32_t)myregs[rb * nthr];
+      const bool wr = act && d != kNoDest;
       uint32_t npc = p + 1;
       bool memop = false;
-      if (lane == 0) n_instr += __popc(actm);
+      n_instr += act;
 
       if (op <= SR_OP_SNE) {
         bool dz = false;
         const int32_t r = alu(op, va, vb, dz);
-        if (act && d != kZeroReg) regs[d * nthr + tid] = (uint32_t)r;
+        if (wr) myregs[d * nthr] = (uint32_t)r;
         if (op == SR_OP_DIV || op == SR_OP_REM) {
           const uint32_t em = __ballot_sync(FULL, act && dz);
           if (em) note_err(err, bv, p, w, em, lane);
@@ -303,7 +309,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
                                : imm == SR_SREG_BDIM ? bdim
                                : imm == SR_SREG_GDIM ? Ls->grid
                                                      : 32u;
-            if (act && d != kZeroReg) regs[d * nthr + tid] = v;
+            if (wr) myregs[d * nthr] = v;
             break;
           }
           case SR_OP_LDS:
@@ -312,19 +318,22 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             const bool shared = op == SR_OP_LDS;
             const int32_t addr = (int32_t)((uint32_t)va + (uint32_t)imm);
             const bool inb = act && (uint32_t)addr < (shared ? shw : arena_words);
-            if (nw > 1 && !wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k, false, 0, 0, 0, spin)) {
+            if (nw > 1 && !wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k, false, 0, 0, 0, spin, omin)) {
               timeout = true;
               break;
             }
             int32_t v = 0;
             if (inb) v = shared ? sh[addr] : arena[addr];
-            if (act && d != kZeroReg) regs[d * nthr + tid] = (uint32_t)v;
+            if (wr) myregs[d * nthr] = (uint32_t)v;
             const uint32_t em = __ballot_sync(FULL, act && !inb);
             if (em) note_err(err, bv, p, w, em, lane);
             if (shared) {
-              if (logging) log_access(bv, region, front_cap, inb, make_record(epoch, addr, tid, K_R, p), lane);
-            } else if (lane == 0) {
-              n_gacc += __popc(actm);
+              if (logging)
+                log_access(bv, region, front_cap, inb,
+                           epoch_rec | lane_rec | (unsigned long long)(K_R << 12 | p) | (unsigned long long)addr << 24,
+                           lane);
+            } else {
+              n_gacc += act;
             }
             break;
           }
@@ -343,7 +352,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
                 rsp[w] = shared;
                 st_release_cta(&clk[w], 4u * k + 1u);
               }
-              if (!wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k + 1u, true, lo, hi, shared, spin)) {
+              if (!wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k + 1u, true, lo, hi, shared, spin, omin)) {
                 timeout = true;
                 break;
               }
@@ -359,9 +368,12 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             const uint32_t em = __ballot_sync(FULL, act && !inb);
             if (em) note_err(err, bv, p, w, em, lane);
             if (shared) {
-              if (logging) log_access(bv, region, front_cap, inb, make_record(epoch, addr, tid, K_W, p), lane);
-            } else if (lane == 0) {
-              n_gacc += __popc(actm);
+              if (logging)
+                log_access(bv, region, front_cap, inb,
+                           epoch_rec | lane_rec | (unsigned long long)(K_W << 12 | p) | (unsigned long long)addr << 24,
+                           lane);
+            } else {
+              n_gacc += act;
             }
             break;
           }
@@ -371,7 +383,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             const bool inb = act && (uint32_t)addr < shw;
             if (nw > 1) {
               if (lane == 0) st_release_cta(&clk[w], 4u * k + 2u);
-              if (!wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k + 2u, false, 0, 0, 0, spin)) {
+              if (!wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k + 2u, false, 0, 0, 0, spin, omin)) {
                 timeout = true;
                 break;
               }
@@ -379,7 +391,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (inb) atomicAdd(&sh[addr], vb);
             const uint32_t em = __ballot_sync(FULL, act && !inb);
             if (em) note_err(err, bv, p, w, em, lane);
-            if (logging) log_access(bv, region, front_cap, inb, make_record(epoch, addr, tid, K_A, p), lane);
+            if (logging)
+              log_access(bv, region, front_cap, inb,
+                         epoch_rec | lane_rec | (unsigned long long)(K_A << 12 | p) | (unsigned long long)addr << 24,
+                         lane);
             break;
           }
           case SR_OP_BRA: npc = (uint32_t)imm; break;
@@ -461,14 +476,17 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     if (bv->decision != DEC_RELEASE) break;
     if (st == ST_WAIT) st = ST_RUN;
     k = bv->k0;
+    omin = 4u * k;                               // every clock was reset to 4 * k0
     epoch = bv->epoch;
+    epoch_rec = (unsigned long long)epoch << 38;
     front_cap = log_cap - 2u * bv->n_misc;
   }
 
   // ---- block finished
+  const uint32_t wi = __reduce_add_sync(FULL, n_instr), wg = __reduce_add_sync(FULL, n_gacc);
   if (lane == 0) {
-    atomicAdd(&A.counters->thread_instrs, n_instr);
-    if (n_gacc) atomicAdd(&A.counters->global_accesses, n_gacc);
+    atomicAdd(&A.counters->thread_instrs, (unsigned long long)wi);
+    if (wg) atomicAdd(&A.counters->global_accesses, (unsigned long long)wg);
   }
   if (tid == 0) {
     const uint32_t front = log_cap - 2u * bv->n_misc;
@@ -486,8 +504,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   }
 }
 
-// One CTA per simulated block; one kernel launch per (program, launch).
-__global__ void __launch_bounds__(1024) k_interp_plain(RunArgs A, uint32_t li) {
+// One CTA per simulated block; one kernel launch per (program, launch).  MINB = 2 caps
+// registers so that two 1024-thread CTAs fit an SM.
+template <int MINB>
+__global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t li) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LaunchDev Ls;
   __shared__ __align__(8) unsigned long long mbar;
@@ -573,7 +593,7 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
 
 uint32_t interp_plain_smem(const LaunchDev& L) {
   const uint32_t nthr = ((L.bdim + 31) / 32) * 32;
-  return L.ir_bytes + group_layout(nthr, L.shw, L.ncode).total;
+  return L.ir_bytes + group_layout(nthr, L.shw, L.ncode, L.nrows).total;
 }
 
 // dynamic shared memory may use what the kernel's static shared memory leaves of the opt-in limit
@@ -587,13 +607,26 @@ static cudaError_t allow_dynamic_smem(K kernel, uint32_t smem_optin) {
 }
 
 cudaError_t init_interp_attributes(uint32_t smem_optin) {
-  cudaError_t e = allow_dynamic_smem(k_interp_plain, smem_optin);
+  cudaError_t e = allow_dynamic_smem(k_interp_plain<1>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2>, smem_optin);
   return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched, smem_optin) : e;
 }
 
-cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, cudaStream_t s) {
+// variant: 1 = one CTA per SM budget (no register cap), 2 = two CTAs per SM, 0 = the one
+// with more resident warps for this launch (ties: 1)
+cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, uint32_t variant, cudaStream_t s) {
   const uint32_t threads = ((L.bdim + 31) / 32) * 32;
-  k_interp_plain<<<L.grid, threads, interp_plain_smem(L), s>>>(a, li);
+  const uint32_t smem = interp_plain_smem(L);
+  if (variant == 0) {
+    int b1 = 0, b2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_interp_plain<1>, (int)threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_interp_plain<2>, (int)threads, smem);
+    variant = b2 > b1 ? 2 : 1;
+  }
+  if (variant == 2)
+    k_interp_plain<2><<<L.grid, threads, smem, s>>>(a, li);
+  else
+    k_interp_plain<1><<<L.grid, threads, smem, s>>>(a, li);
   return cudaGetLastError();
 }
 

@@ -230,14 +230,40 @@ int validate(const sr_program* p, char* msg, size_t len) {
   return SR_OK;
 }
 
-// pack one instruction: RZ and unused register fields point at the zero row (16)
-uint2 pack(const sr_instr& in) {
+// Register renaming of one program: the registers it touches (plus the parameter
+// registers r0..r(maxp-1)) become rows 0..n-1 in ascending order, the zero row is n.
+struct RegMap {
+  uint8_t row[256];
+  uint32_t nrows;
+};
+RegMap map_registers(const sr_program& P) {
+  bool used[16] = {};
+  uint32_t maxp = 0;
+  for (uint32_t l = 0; l < P.nlaunches; ++l) maxp = std::max(maxp, P.launches[l].nparams);
+  for (uint32_t r = 0; r < maxp; ++r) used[r] = true;
+  for (uint32_t pc = 0; pc < P.ncode; ++pc) {
+    const uint32_t w = P.code[pc].op_d_a_b, op = w & 0xFFu, b = op & 0x7Fu;
+    const uint32_t d = (w >> 8) & 0xFFu, ra = (w >> 16) & 0xFFu, rb = (w >> 24) & 0xFFu;
+    if (op_writes_d(b) && d < 16) used[d] = true;
+    if (op_reads_a(b) && ra < 16) used[ra] = true;
+    if (op_reads_b(op) && rb < 16) used[rb] = true;
+  }
+  RegMap m;
+  uint32_t n = 0;
+  for (uint32_t r = 0; r < 16; ++r) m.row[r] = used[r] ? (uint8_t)n++ : 0;
+  m.nrows = n + 1;
+  return m;
+}
+
+// pack one instruction: sources that are RZ or unused read the zero row; destinations
+// that are RZ or absent become kNoDest
+uint2 pack(const sr_instr& in, const RegMap& m) {
   const uint32_t w = in.op_d_a_b, op = w & 0xFFu, b = op & 0x7Fu;
   uint32_t d = (w >> 8) & 0xFFu, ra = (w >> 16) & 0xFFu, rb = (w >> 24) & 0xFFu;
-  auto map = [](uint32_t r) { return r == SR_RZ ? sr::kZeroReg : r; };
-  d = op_writes_d(b) ? map(d) : sr::kZeroReg;
-  ra = op_reads_a(b) ? map(ra) : sr::kZeroReg;
-  rb = op_reads_b(op) ? map(rb) : sr::kZeroReg;
+  const uint32_t zrow = m.nrows - 1;
+  d = (op_writes_d(b) && d != SR_RZ) ? m.row[d] : sr::kNoDest;
+  ra = (op_reads_a(b) && ra != SR_RZ) ? m.row[ra] : zrow;
+  rb = (op_reads_b(op) && rb != SR_RZ) ? m.row[rb] : zrow;
   return make_uint2(op | d << 8 | ra << 16 | rb << 24, (uint32_t)in.imm);
 }
 
@@ -311,7 +337,8 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       const uint32_t ctas = std::min<uint32_t>(ra.nitems, (uint32_t)c->sms * std::max(1u, o.ctas_per_sm));
       if (ctas) CUDA_TRY(c, sr::launch_interp_batched(ra, ctas, b->batched_smem, s));
     } else {
-      for (uint32_t li = w.li0; li < w.li1; ++li) CUDA_TRY(c, sr::launch_interp_plain(ra, li, b->launches[li], s));
+      for (uint32_t li = w.li0; li < w.li1; ++li)
+        CUDA_TRY(c, sr::launch_interp_plain(ra, li, b->launches[li], o.interp_variant, s));
     }
     mark();
     if (o.check_races) {
@@ -326,7 +353,6 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       ca.work_head = (uint32_t*)b->work_head.p + wi;
       ca.error_flag = (uint32_t*)b->err_flag.p;
       ca.spin_limit = o.spin_limit;
-      ca.max_key_bits = b->max_key_bits;
       CUDA_TRY(c, cudaMemsetAsync(ca.work_head, 0, 4, s));
       const uint32_t ctas = std::min<uint32_t>(b->check_ctas, w.gb1 - w.gb0);
       if (ctas) CUDA_TRY(c, sr::launch_check(ca, ctas, s));
@@ -368,10 +394,9 @@ int sr_create(sr_ctx** out, const sr_opts* opts) {
   sr_opts& o = c->opts;
   if (o.round_budget == 0) o.round_budget = 1u << 24;
   if (o.loop_log_records == 0) o.loop_log_records = 65536;
-  if (o.check_ctas_per_sm == 0) o.check_ctas_per_sm = 1;
   if (o.ctas_per_sm == 0) o.ctas_per_sm = 1;
   if (o.spin_limit == 0) o.spin_limit = 1u << 26;
-  if (o.round_budget > sr::kMaxBudget || o.mode > SR_MODE_BATCHED) {
+  if (o.round_budget > sr::kMaxBudget || o.mode > SR_MODE_BATCHED || o.interp_variant > 2) {
     delete c;
     return fail(nullptr, SR_E_INVAL, "round_budget above 2^26 or unknown mode");
   }
@@ -431,8 +456,10 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   for (uint32_t i = 0; i < n; ++i) {
     const sr_program& P = progs[i];
     code_off[i] = (uint32_t)code.size();
-    for (uint32_t pc = 0; pc < P.ncode; ++pc) code.push_back(pack(P.code[pc]));
-    code.push_back(make_uint2(SR_OP_EXIT | sr::kZeroReg << 8 | sr::kZeroReg << 16 | sr::kZeroReg << 24, 0));
+    const RegMap rm = map_registers(P);
+    for (uint32_t pc = 0; pc < P.ncode; ++pc) code.push_back(pack(P.code[pc], rm));
+    const uint32_t z = rm.nrows - 1;
+    code.push_back(make_uint2(SR_OP_EXIT | sr::kNoDest << 8 | z << 16 | z << 24, 0));
     if (code.size() & 1) code.push_back(make_uint2(SR_OP_EXIT, 0));
     b->arena_off[i] = arena_total;
     b->arena_words[i] = P.global_words;
@@ -474,8 +501,9 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       d.arena_off = b->arena_off[i];
       d.arena_words = P.global_words;
       d.ir_bytes = sr::ir_smem_bytes(P.ncode);
+      d.nrows = rm.nrows;
       const uint32_t nw = (L.block_dim + 31) / 32;
-      d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode).total;
+      d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode, rm.nrows).total;
       if (d.ir_bytes + d.group_bytes > smem_budget) {
         delete b;
         return fail(c, SR_E_INVAL, "program %u launch %u: %u bytes of shared memory needed, %u available", i, l,
@@ -541,7 +569,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       }
     w.item1 = (uint32_t)b->items.size();
   }
-  b->check_ctas = (uint32_t)c->sms * o.check_ctas_per_sm;
+  b->check_ctas = (uint32_t)c->sms;          // one 1024-thread checker CTA per SM
 
   // ---- device buffers
   int rc = SR_OK;

@@ -8,8 +8,10 @@
 
 namespace sr {
 
-constexpr uint32_t kRegRows = 17;     // r0..r15 + one zero row; packed RZ fields point at row 16
-constexpr uint32_t kZeroReg = 16;
+// Packed instructions (device copy): register fields are rows of the program's compacted
+// register file (only the registers the program uses, plus one zero row last); a
+// destination field of kNoDest drops the write (RZ or an opcode without a result).
+constexpr uint32_t kNoDest = 31;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kMaxBudget = 1u << 26;  // epochs and rounds stay below 2^26
 
@@ -42,7 +44,7 @@ struct LaunchDev {
   uint64_t log_base;                     // record offset of block 0's region
   uint64_t arena_off, arena_words;       // word offset of the program's working arena
   uint32_t groups, group_bytes;          // batched mode: blocks per CTA, smem per block
-  uint32_t ir_bytes, pad;                // smem bytes of the staged code
+  uint32_t ir_bytes, nrows;              // smem bytes of the staged code; register rows (zero row last)
 };
 
 // Per simulated block, written by the interpreter (n_log, n_misc, flags) and the checker (n_race).
@@ -75,10 +77,10 @@ struct GroupLayout {
   uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, total;
 };
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
-__host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode) {
+__host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode, uint32_t nrows) {
   GroupLayout g;
   uint32_t o = 0;
-  g.regs = o; o += align16(kRegRows * nthr * 4u);
+  g.regs = o; o += align16(nrows * nthr * 4u);
   g.sh = o;   o += align16(shw * 4u);
   g.clk = o;  o += 32 * 4;
   g.rlo = o;  o += 32 * 4;
@@ -98,7 +100,7 @@ __host__ __device__ inline uint32_t ir_smem_bytes(uint32_t ncode) {
 cudaError_t init_kernel_attributes(uint32_t smem_optin);
 cudaError_t init_interp_attributes(uint32_t smem_optin);
 cudaError_t init_check_attributes(uint32_t smem_optin);
-cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, cudaStream_t s);
+cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, uint32_t variant, cudaStream_t s);
 cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, cudaStream_t s);
 uint32_t interp_plain_smem(const LaunchDev& L);
 
@@ -112,12 +114,12 @@ struct CheckArgs {
   uint32_t* work_head;
   uint32_t* error_flag;
   uint32_t spin_limit;
-  uint32_t max_key_bits;        // largest address width over the launches (<= 14)
 };
 cudaError_t launch_check(const CheckArgs& a, uint32_t ctas, cudaStream_t s);
-uint32_t check_smem_bytes_bits(uint32_t max_bits);
-constexpr uint32_t kCheckThreads = 512;
+uint32_t check_smem_bytes();
+constexpr uint32_t kCheckThreads = 1024;
 constexpr uint32_t kCheckTile = 4096;          // records per staged tile
+constexpr uint32_t kCheckBins = 12288;         // counting-sort bins (>= the largest shared array)
 constexpr uint32_t kScratchWords = 1u << 14;   // summaries per CTA in the large-interval path
 
 struct CompactArgs {
