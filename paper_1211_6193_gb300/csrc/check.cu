@@ -174,6 +174,7 @@ struct Smem {
   uint32_t* sbin;               // T: bin of sorted[i]
   uint32_t* bins;               // NB
   uint32_t* flags;              // 2T
+  uint16_t* segidx;             // T: interval of each tile record
   uint32_t* seg_start;          // MAXSEG + 1 (record index of each interval of the tile)
   uint32_t* seg_lo;             // MAXSEG: lowest address of the interval
   uint32_t* seg_hi;             // MAXSEG
@@ -201,12 +202,7 @@ __device__ uint32_t sort_intervals(const Smem& S, const unsigned long long* tile
     const bool valid = i < end;
     uint32_t sg = 0, a = 0;
     if (valid) {
-      uint32_t lo = s0, hi = s0 + nseg - 1;     // interval of record i
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (S.seg_start[mid] <= i) lo = mid; else hi = mid - 1;
-      }
-      sg = lo;
+      sg = S.segidx[i];
       a = rec_addr(tile[i]);
     }
     const uint32_t sg0 = __shfl_sync(FULL, sg, 0);
@@ -252,12 +248,8 @@ __device__ uint32_t sort_intervals(const Smem& S, const unsigned long long* tile
   for (uint32_t b = tid; b < nb; b += NT) S.bins[b] = 0;
   __syncthreads();
   for (uint32_t i = base + tid; i < mend; i += NT) {
-    uint32_t lo = s0, hi = s0 + kept - 1;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi + 1) >> 1;
-      if (S.seg_start[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    const uint32_t b = S.seg_off[lo] + rec_addr(tile[i]) - S.seg_lo[lo];
+    const uint32_t sg = S.segidx[i];
+    const uint32_t b = S.seg_off[sg] + rec_addr(tile[i]) - S.seg_lo[sg];
     S.flags[T + (i - base)] = b;
     atomicAdd(&S.bins[b], 1u);
   }
@@ -286,8 +278,21 @@ __device__ void emit_races(const Smem& S, uint32_t m, uint4* out, uint32_t& race
   for (uint32_t i = tid; i < m; i += NT) {
     uint32_t f = 0;
     if (i == 0 || S.sbin[i] != S.sbin[i - 1]) {
-      uint32_t b, c;
-      f = summ_race(run_summary(S, i, S.bins[S.sbin[i]]), b, c);
+      // cheap pass: one thread only, or reads only / atomics only, cannot race
+      const uint32_t end = S.bins[S.sbin[i]];
+      uint32_t tmin = 0xFFFFu, tmax = 0, kinds = 0;
+      for (uint32_t j = i; j < end; ++j) {
+        const unsigned long long r = S.sorted[j];
+        const uint32_t t = rec_tid(r);
+        tmin = min(tmin, t);
+        tmax = max(tmax, t);
+        kinds |= 1u << rec_kind(r);
+      }
+      const bool maybe = tmin != tmax && ((kinds & (1u << K_W)) || kinds == ((1u << K_R) | (1u << K_A)));
+      if (maybe) {
+        uint32_t b, c;
+        f = summ_race(run_summary(S, i, end), b, c);
+      }
     }
     S.flags[i] = f;
     S.flags[T + i] = f;
@@ -363,11 +368,13 @@ __device__ uint32_t find_intervals(const Smem& S, const unsigned long long* tile
   }
   uint32_t total;
   uint32_t o = cta_scan_value(c, S.wtot, &total);
-  for (uint32_t j = 0; j < PER; ++j)
+  for (uint32_t j = 0; j < PER; ++j) {
     if (f >> j & 1u) {
       if (o <= MAXSEG) S.seg_start[o] = i0 + j;
       ++o;
     }
+    if (i0 + j < cnt) S.segidx[i0 + j] = (uint16_t)min(o - 1, 0xFFFFu);   // interval of record i0 + j
+  }
   __syncthreads();
   const uint32_t nseg = min(total, MAXSEG);
   if (total <= MAXSEG && threadIdx.x == 0) S.seg_start[nseg] = cnt;
@@ -388,6 +395,7 @@ __global__ void __launch_bounds__(NT, 1) k_check(CheckArgs A) {
   S.sbin = reinterpret_cast<uint32_t*>(p); p += T * 4;
   S.bins = reinterpret_cast<uint32_t*>(p); p += NB * 4;
   S.flags = reinterpret_cast<uint32_t*>(p); p += 2 * T * 4;
+  S.segidx = reinterpret_cast<uint16_t*>(p); p += T * 2;
   S.seg_start = reinterpret_cast<uint32_t*>(p); p += (MAXSEG + 4) * 4;
   S.seg_lo = reinterpret_cast<uint32_t*>(p); p += MAXSEG * 4;
   S.seg_hi = reinterpret_cast<uint32_t*>(p); p += MAXSEG * 4;
@@ -503,7 +511,7 @@ __global__ void __launch_bounds__(NT, 1) k_check(CheckArgs A) {
 }  // namespace
 
 uint32_t check_smem_bytes() {
-  return 2 * (T + 2) * 8 + T * 8 + T * 4 + NB * 4 + 2 * T * 4 + (MAXSEG + 4) * 4 + 3 * MAXSEG * 4 +
+  return 2 * (T + 2) * 8 + T * 8 + T * 4 + NB * 4 + 2 * T * 4 + T * 2 + (MAXSEG + 4) * 4 + 3 * MAXSEG * 4 +
          (NB / 32 + 1) * 4 + 36 * 4 + 64;
 }
 

@@ -271,6 +271,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
 
   uint32_t pc = Ls->entry, st = tid < bdim ? ST_RUN : ST_NONE, wpc = 0;
   uint32_t k = 0, epoch = 0, front_cap = log_cap, omin = 0;
+  // pn: the pc the warp issues next (the lowest pc of its runnable lanes, kInf if none);
+  // while every runnable lane sits at pn (conv) it is advanced without a reduction
+  bool conv = true;
+  uint32_t pn = Ls->entry;
   uint32_t n_instr = 0, n_gacc = 0;              // per lane: executed instructions, global accesses
   const unsigned long long lane_rec = (unsigned long long)tid << 14;
   unsigned long long epoch_rec = 0;              // epoch << 38
@@ -278,7 +282,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   for (;;) {  // barrier intervals
     bool limit = false, timeout = false;
     for (;;) {  // rounds
-      const uint32_t p = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
+      const uint32_t p = pn;
       if (p == kInf) break;                      // no runnable lane
       if (k >= budget) { limit = true; break; }
       const bool act = (st == ST_RUN) && (pc == p);
@@ -289,7 +293,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const int32_t va = (int32_t)myregs[ra * nthr];
       const int32_t vb = (ins.x & SR_BIMM) ? imm : (int32_t)myregs[rb * nthr];
       const bool wr = act && d != kNoDest;
-      uint32_t npc = p + 1;
+      uint32_t npc = p + 1, cn = p + 1;         // cn: the warp's next pc while converged
       bool memop = false;
       n_instr += act;
 
@@ -397,20 +401,37 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
                          lane);
             break;
           }
-          case SR_OP_BRA: npc = (uint32_t)imm; break;
-          case SR_OP_BRZ: npc = va == 0 ? (uint32_t)imm : p + 1; break;
-          case SR_OP_BRNZ: npc = va != 0 ? (uint32_t)imm : p + 1; break;
+          case SR_OP_BRA: npc = cn = (uint32_t)imm; break;
+          case SR_OP_BRZ:
+          case SR_OP_BRNZ: {
+            const bool taken = (va == 0) == (op == SR_OP_BRZ);
+            npc = taken ? (uint32_t)imm : p + 1;
+            if (conv) {                          // a split branch ends the converged run
+              const uint32_t tm = __ballot_sync(FULL, act && taken);
+              if (tm != 0 && tm != __ballot_sync(FULL, act)) conv = false;
+              if (tm) cn = (uint32_t)imm;
+            }
+            break;
+          }
           case SR_OP_BAR:
             if (act) { st = ST_WAIT; wpc = p; }
+            conv = false;
             break;
           default:  // EXIT, and the EXIT sentinel after the last instruction
             if (act) st = ST_EXIT;
+            conv = false;
             break;
         }
       }
       if (timeout) break;
       if (act) pc = npc;
       ++k;
+      if (conv) {
+        pn = cn;
+      } else {
+        pn = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
+        conv = __all_sync(FULL, st != ST_RUN || pc == pn);
+      }
       // publish progress; after a memory instruction every lane's access must be
       // ordered before the clock (warp barrier, then a release by lane 0)
       if (memop) __syncwarp();
@@ -475,6 +496,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     group_sync(bar_id, nthr);
     if (bv->decision != DEC_RELEASE) break;
     if (st == ST_WAIT) st = ST_RUN;
+    pn = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
+    conv = __all_sync(FULL, st != ST_RUN || pc == pn);
     k = bv->k0;
     omin = 4u * k;                               // every clock was reset to 4 * k0
     epoch = bv->epoch;
