@@ -199,6 +199,33 @@ int sr_batch_stats(sr_ctx* ctx, sr_batch* batch, sr_stats* out);
 void sr_free_batch(sr_ctx* ctx, sr_batch* batch);
 const char* sr_last_error(sr_ctx* ctx);
 
+/* ---------------------------------------------------------------- no-allocation entry point
+ * The paper has no counterpart to this call: it serves callers that cannot allocate
+ * device memory - code that runs while a CUDA graph is being captured, frameworks that
+ * own every byte of the GPU through their own allocator, or processes that forbid
+ * cudaMalloc after start-up.  It runs the whole check of one program (the same kernels
+ * as load_programs + run_and_check + fetch_reports, plain mode, default options) and
+ * allocates nothing: every intermediate buffer lives in one file-scope __device__ array
+ * of SR_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process
+ * exits.
+ *   prog       host descriptors of the program (prog->global_init is not read);
+ *   d_arena    device memory, prog->global_words int32: the initial arena in, the final
+ *              arena out (updated in place);
+ *   d_reports  device memory for report_cap records: the sorted reports (at most report_cap);
+ *   n_reports  host: total number of reports;  status: host, SR_ST_* bits of the program.
+ * Synchronous on `stream`.  Returns SR_E_RANGE when the program needs more scratch than
+ * the array holds (more than 256 launches, or logs that do not fit even one launch at a
+ * time) or when report_cap < *n_reports (extra reports dropped), SR_E_INVAL for an
+ * invalid program, SR_E_CUDA for a failed CUDA call.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress and sets the kernels' shared-memory attributes; make that first
+ * call before any stream capture.  All calls share the one array and it keeps the last
+ * call's contents: calls that overlap on the GPU (other streams, other host threads) race
+ * and corrupt each other's results. */
+#define SR_NOALLOC_SCRATCH_BYTES (32u << 20)
+int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena, sr_report* d_reports, uint64_t report_cap,
+                             uint64_t* n_reports, uint32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,7 +73,9 @@ class sr_stats(C.Structure):
 
 
 EXPORTS = ["sr_create", "sr_destroy", "sr_validate_program", "load_programs", "run_and_check", "fetch_reports",
-           "fetch_memory", "sr_batch_status", "sr_batch_stats", "sr_free_batch", "sr_last_error"]
+           "fetch_memory", "sr_batch_status", "sr_batch_stats", "sr_free_batch", "sr_last_error",
+           "sr_check_program_noalloc"]
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 _lib = None
 _lock = threading.Lock()
@@ -103,6 +105,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.sr_free_batch.restype = None
         lib.sr_last_error.argtypes = [vp]
         lib.sr_last_error.restype = C.c_char_p
+        lib.sr_check_program_noalloc.argtypes = [C.POINTER(sr_program), vp, vp, u64, C.POINTER(u64),
+                                                 C.POINTER(u32), vp]
         for name in EXPORTS:
             if name not in ("sr_destroy", "sr_free_batch", "sr_last_error"):
                 getattr(lib, name).restype = C.c_int

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsimtcheck.so")
-SOURCES = ["interp.cu", "check.cu", "compact.cu", "runtime.cpp"]
+SOURCES = ["interp.cu", "check.cu", "compact.cu", "runtime.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +31,8 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "sr_internal.h"), os.path.join(INCLUDE, "simtcheck.h"), __file__]
+    files += [os.path.join(CSRC, h) for h in ("sr_internal.h", "host_prep.h")]
+    files += [os.path.join(INCLUDE, "simtcheck.h"), __file__]
     return files
 
 

@@ -1,0 +1,232 @@
+// noalloc.cu - sr_check_program_noalloc: the whole check of one program without any
+// device (or host heap) allocation.
+//
+// Some callers cannot allocate: code running inside a CUDA graph that is being
+// captured, inside a framework that owns every byte of device memory, or in a process
+// that forbids cudaMalloc after start-up.  This entry point runs the same kernels as
+// load_programs + run_and_check, but every intermediate buffer (packed code, launch
+// table, access logs, per-block results, scan and checker scratch) lives in one
+// file-scope __device__ array of SR_NOALLOC_SCRATCH_BYTES.  The caller passes the inputs
+// (program descriptors in host memory, the global arena on the device) and the outputs
+// (the arena, updated in place, and a device report buffer).
+#include <algorithm>
+
+#include "host_prep.h"
+#include "sr_internal.h"
+
+namespace {
+
+// The scratch: every GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SR_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+constexpr uint32_t kMaxLaunches = 256;
+constexpr uint32_t kMaxWaves = 256;
+constexpr uint32_t kCheckCtas = 8;          // checker CTAs (each owns 256 KB of summary table)
+
+void* g_scratch_addr[kMaxDevices];           // device address of the array, per device
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct NoallocWave {
+  uint32_t li0, li1, gb0, gb1;
+};
+
+}  // namespace
+
+using namespace sr::host;
+
+extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena, sr_report* d_reports,
+                                        uint64_t report_cap, uint64_t* n_reports, uint32_t* status,
+                                        void* stream) {
+  if (!prog || (prog->global_words && !d_arena) || (report_cap && !d_reports) || !n_reports || !status)
+    return SR_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  char msg[256];
+  // validation reads only the code and launches; the arena is the caller's device buffer
+  sr_program pv = *prog;
+  static const int32_t one_word = 0;
+  pv.global_init = &one_word;
+  if (validate(&pv, msg, sizeof msg) != SR_OK) return SR_E_INVAL;
+  if (prog->nlaunches > kMaxLaunches) return SR_E_RANGE;
+
+  // ---- once per device: the array's device address and the kernels' attributes
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= kMaxDevices) return SR_E_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return SR_E_CUDA;
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e == cudaSuccess) e = sr::init_kernel_attributes((uint32_t)optin);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return SR_E_CUDA;
+    }
+    g_scratch_addr[dev] = ptr;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+
+  // ---- pack code and launch table (host stack only)
+  const uint32_t ncode = prog->ncode;
+  uint2 code[SR_MAX_CODE + 2];
+  const RegMap rm = map_registers(*prog);
+  for (uint32_t pc = 0; pc < ncode; ++pc) code[pc] = pack(prog->code[pc], rm);
+  const uint32_t z = rm.nrows - 1;
+  code[ncode] = make_uint2(SR_OP_EXIT | sr::kNoDest << 8 | z << 16 | z << 24, 0);
+  uint32_t npacked = ncode + 1;
+  if (npacked & 1) code[npacked++] = make_uint2(SR_OP_EXIT, 0);
+
+  uint8_t colour[SR_MAX_CODE + 1];
+  uint32_t acc[SR_MAX_CODE + 1], bar[SR_MAX_CODE + 1], spc[SR_MAX_CODE + 1], snx[SR_MAX_CODE + 1];
+  const BoundScratch ws{colour, acc, bar, spc, snx};
+  sr::LaunchDev L[kMaxLaunches];
+  uint64_t nblocks = 0;
+  for (uint32_t l = 0; l < prog->nlaunches; ++l) {
+    const sr_launch& pl = prog->launches[l];
+    const KernelBound k = bound_kernel(prog->code, ncode, prog->kernel_entry[pl.kernel], ws);
+    sr::LaunchDev d{};
+    d.prog = 0;
+    d.launch = l;
+    d.entry = prog->kernel_entry[pl.kernel];
+    d.ncode = ncode;
+    d.code_off = 0;
+    d.grid = pl.grid;
+    d.bdim = pl.block_dim;
+    d.shw = pl.shmem_words;
+    d.nparams = pl.nparams;
+    for (uint32_t q = 0; q < 4; ++q) d.params[q] = q < pl.nparams ? pl.params[q] : 0;
+    d.block_base = (uint32_t)nblocks;
+    d.key_bits = key_bits_for(std::max(1u, pl.shmem_words));
+    const uint64_t cap = launch_log_cap(k, pl.block_dim, 1, 65536);
+    if (cap >= (1ull << 31)) return SR_E_RANGE;
+    d.log_cap = (uint32_t)cap;
+    d.arena_off = 0;
+    d.arena_words = prog->global_words;
+    d.ir_bytes = sr::ir_smem_bytes(ncode);
+    d.nrows = rm.nrows;
+    const uint32_t nw = (pl.block_dim + 31) / 32;
+    d.group_bytes = sr::group_layout(nw * 32, pl.shmem_words, ncode, rm.nrows).total;
+    d.groups = 1;
+    if (d.ir_bytes + d.group_bytes + 1024 > (uint32_t)optin) return SR_E_RANGE;
+    nblocks += pl.grid;
+    L[l] = d;
+  }
+  const uint32_t nl = prog->nlaunches;
+
+  // ---- scratch layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += up256(bytes ? bytes : 1);
+    return o;
+  };
+  const size_t o_code = take((size_t)npacked * 8);
+  const size_t o_launch = take((size_t)std::max(1u, nl) * sizeof(sr::LaunchDev));
+  const size_t o_blocks = take((size_t)nblocks * sizeof(sr::BlockRes));
+  const size_t o_status = take(8);                     // status, abort mark
+  const size_t o_counters = take(sizeof(sr::Counters));
+  const size_t o_total = take(8);
+  const size_t o_heads = take(kMaxWaves * 4 + 4);      // checker work heads + error flag
+  const size_t o_offsets = take(((size_t)nblocks + 1) * 8);
+  const size_t o_partials = take(sr::compact_partials_count((uint32_t)nblocks) * 8);
+  const uint32_t cctas = std::min<uint32_t>(kCheckCtas, (uint32_t)sms);
+  const size_t o_table = take((size_t)cctas * sr::kScratchWords * 16);
+  if (off >= SR_NOALLOC_SCRATCH_BYTES) return SR_E_RANGE;
+  const size_t o_log = off;
+  const uint64_t log_records = (SR_NOALLOC_SCRATCH_BYTES - off) / 8;
+
+  // waves: consecutive launches whose logs fit the remaining scratch together
+  NoallocWave waves[kMaxWaves];
+  uint32_t nwaves = 0;
+  uint64_t used = 0;
+  for (uint32_t l = 0; l < nl; ++l) {
+    const uint64_t need = (uint64_t)L[l].grid * L[l].log_cap;
+    if (need > log_records) return SR_E_RANGE;        // one launch alone does not fit
+    if (nwaves == 0 || used + need > log_records) {
+      if (nwaves == kMaxWaves) return SR_E_RANGE;
+      waves[nwaves++] = NoallocWave{l, l, L[l].block_base, L[l].block_base};
+      used = 0;
+    }
+    L[l].log_base = used;
+    used += need;
+    waves[nwaves - 1].li1 = l + 1;
+    waves[nwaves - 1].gb1 = L[l].block_base + L[l].grid;
+  }
+
+  // ---- upload and reset (pageable sources are staged before the calls return)
+#define NA_TRY(call)                                  \
+  do {                                                \
+    if ((call) != cudaSuccess) {                      \
+      cudaGetLastError();                             \
+      return SR_E_CUDA;                               \
+    }                                                 \
+  } while (0)
+  NA_TRY(cudaMemcpyAsync(base + o_code, code, (size_t)npacked * 8, cudaMemcpyHostToDevice, s));
+  if (nl) NA_TRY(cudaMemcpyAsync(base + o_launch, L, (size_t)nl * sizeof(sr::LaunchDev), cudaMemcpyHostToDevice, s));
+  NA_TRY(cudaMemsetAsync(base + o_blocks, 0, (size_t)nblocks * sizeof(sr::BlockRes), s));
+  NA_TRY(cudaMemsetAsync(base + o_status, 0, 4, s));
+  NA_TRY(cudaMemsetAsync(base + o_status + 4, 0xFF, 4, s));
+  NA_TRY(cudaMemsetAsync(base + o_counters, 0, sizeof(sr::Counters), s));
+  NA_TRY(cudaMemsetAsync(base + o_total, 0, 8, s));
+  NA_TRY(cudaMemsetAsync(base + o_heads, 0, kMaxWaves * 4 + 4, s));
+
+  sr::RunArgs ra{};
+  ra.launches = reinterpret_cast<const sr::LaunchDev*>(base + o_launch);
+  ra.nlaunches = nl;
+  ra.budget = 1u << 24;
+  ra.check_races = 1;
+  ra.spin_limit = 1u << 26;
+  ra.code = reinterpret_cast<const uint2*>(base + o_code);
+  ra.arena = d_arena;
+  ra.log = reinterpret_cast<unsigned long long*>(base + o_log);
+  ra.blocks = reinterpret_cast<sr::BlockRes*>(base + o_blocks);
+  ra.prog_status = reinterpret_cast<uint32_t*>(base + o_status);
+  ra.prog_abort = reinterpret_cast<uint32_t*>(base + o_status + 4);
+  ra.counters = reinterpret_cast<sr::Counters*>(base + o_counters);
+  uint32_t* heads = reinterpret_cast<uint32_t*>(base + o_heads);
+  for (uint32_t wi = 0; wi < nwaves; ++wi) {
+    const NoallocWave& w = waves[wi];
+    for (uint32_t li = w.li0; li < w.li1; ++li) NA_TRY(sr::launch_interp_plain(ra, li, L[li], 0, s));
+    sr::CheckArgs ca{};
+    ca.launches = ra.launches;
+    ca.nlaunches = nl;
+    ca.gb0 = w.gb0;
+    ca.gb1 = w.gb1;
+    ca.log = ra.log;
+    ca.blocks = ra.blocks;
+    ca.scratch = reinterpret_cast<uint4*>(base + o_table);
+    ca.work_head = heads + wi;
+    ca.error_flag = heads + kMaxWaves;
+    ca.spin_limit = ra.spin_limit;
+    const uint32_t ctas = std::min<uint32_t>(cctas, w.gb1 - w.gb0);
+    if (ctas) NA_TRY(sr::launch_check(ca, ctas, s));
+    sr::CompactArgs ka{};
+    ka.launches = ra.launches;
+    ka.nlaunches = nl;
+    ka.gb0 = w.gb0;
+    ka.gb1 = w.gb1;
+    ka.total = reinterpret_cast<unsigned long long*>(base + o_total);
+    ka.log = ra.log;
+    ka.blocks = ra.blocks;
+    ka.offsets = reinterpret_cast<unsigned long long*>(base + o_offsets);
+    ka.partials = reinterpret_cast<unsigned long long*>(base + o_partials);
+    ka.out = d_reports;
+    ka.out_cap = report_cap;
+    ka.counters = ra.counters;
+    NA_TRY(sr::launch_compact_scan(ka, s));
+    NA_TRY(sr::launch_compact_emit(ka, s));
+  }
+  unsigned long long total = 0;
+  uint32_t st = 0, err = 0;
+  NA_TRY(cudaMemcpyAsync(&total, base + o_total, 8, cudaMemcpyDeviceToHost, s));
+  NA_TRY(cudaMemcpyAsync(&st, base + o_status, 4, cudaMemcpyDeviceToHost, s));
+  NA_TRY(cudaMemcpyAsync(&err, heads + kMaxWaves, 4, cudaMemcpyDeviceToHost, s));
+  NA_TRY(cudaStreamSynchronize(s));
+#undef NA_TRY
+  *n_reports = total;
+  *status = st;
+  if (err) return SR_E_TIMEOUT;
+  return total > report_cap ? SR_E_RANGE : SR_OK;
+}

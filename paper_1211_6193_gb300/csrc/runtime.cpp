@@ -16,9 +16,11 @@
 #include <string>
 #include <vector>
 
+#include "host_prep.h"
 #include "sr_internal.h"
 
 using sr::LaunchDev;
+using namespace sr::host;
 
 namespace {
 
@@ -116,161 +118,6 @@ int alloc_buf(sr_ctx* c, DevBuf& b, size_t bytes, cudaStream_t s, const char* wh
   b.bytes = bytes ? bytes : 16;
   if (!b.p) return fail(c, SR_E_NOMEM, "device allocation of %zu bytes for %s failed", bytes, what);
   return SR_OK;
-}
-
-// which operand fields an opcode reads or writes
-bool op_writes_d(uint32_t b) {
-  return (b >= SR_OP_MOV && b <= SR_OP_SNE) || b == SR_OP_S2R || b == SR_OP_LDG || b == SR_OP_LDS;
-}
-bool op_reads_a(uint32_t b) {
-  return (b >= SR_OP_ADD && b <= SR_OP_SNE) || b == SR_OP_LDG || b == SR_OP_STG || b == SR_OP_LDS ||
-         b == SR_OP_STS || b == SR_OP_ATOMS || b == SR_OP_BRZ || b == SR_OP_BRNZ;
-}
-bool op_reads_b(uint32_t op) {
-  const uint32_t b = op & 0x7Fu;
-  return ((b >= SR_OP_MOV && b <= SR_OP_SNE) && !(op & SR_BIMM)) || b == SR_OP_STG || b == SR_OP_STS ||
-         b == SR_OP_ATOMS;
-}
-bool is_shared_access(uint32_t b) { return b == SR_OP_LDS || b == SR_OP_STS || b == SR_OP_ATOMS; }
-bool can_err(uint32_t b) {
-  return b == SR_OP_LDS || b == SR_OP_STS || b == SR_OP_ATOMS || b == SR_OP_LDG || b == SR_OP_STG ||
-         b == SR_OP_DIV || b == SR_OP_REM;
-}
-
-// Static bound for one kernel: the largest number of shared accesses and barriers a
-// single thread can execute, or "unbounded" if the control-flow graph from the entry
-// has a cycle.
-struct KernelBound {
-  bool cyclic = false;
-  uint32_t accesses = 0, barriers = 0, err_pcs = 0;
-};
-KernelBound bound_kernel(const sr_instr* code, uint32_t ncode, uint32_t entry) {
-  KernelBound kb;
-  // iterative DFS with colours; longest paths by memoised post-order
-  std::vector<uint8_t> colour(ncode + 1, 0);
-  std::vector<uint32_t> acc(ncode + 1, 0), bar(ncode + 1, 0);
-  std::vector<std::pair<uint32_t, uint32_t>> stack;   // (pc, next successor index)
-  auto succ = [&](uint32_t pc, uint32_t i, uint32_t& out) -> bool {
-    if (pc >= ncode) return false;
-    const uint32_t b = code[pc].op_d_a_b & 0x7Fu;
-    const uint32_t t = (uint32_t)code[pc].imm;
-    if (b == SR_OP_EXIT) return false;
-    if (b == SR_OP_BRA) { if (i == 0) { out = t; return true; } return false; }
-    if (b == SR_OP_BRZ || b == SR_OP_BRNZ) {
-      if (i == 0) { out = pc + 1; return true; }
-      if (i == 1) { out = t; return true; }
-      return false;
-    }
-    if (i == 0) { out = pc + 1; return true; }
-    return false;
-  };
-  stack.push_back({entry, 0});
-  colour[entry] = 1;
-  while (!stack.empty()) {
-    auto& top = stack.back();
-    uint32_t nxt;
-    if (succ(top.first, top.second, nxt)) {
-      top.second++;
-      if (colour[nxt] == 1) { kb.cyclic = true; return kb; }
-      if (colour[nxt] == 0) { colour[nxt] = 1; stack.push_back({nxt, 0}); }
-      continue;
-    }
-    const uint32_t pc = top.first;
-    uint32_t a = 0, br = 0, s;
-    for (uint32_t i = 0; succ(pc, i, s); ++i) { a = std::max(a, acc[s]); br = std::max(br, bar[s]); }
-    if (pc < ncode) {
-      const uint32_t b = code[pc].op_d_a_b & 0x7Fu;
-      a += is_shared_access(b);
-      br += b == SR_OP_BAR;
-      kb.err_pcs += can_err(b);
-    }
-    acc[pc] = a;
-    bar[pc] = br;
-    colour[pc] = 2;
-    stack.pop_back();
-  }
-  kb.accesses = acc[entry];
-  kb.barriers = bar[entry];
-  return kb;
-}
-
-int validate(const sr_program* p, char* msg, size_t len) {
-  auto bad = [&](const char* fmt, uint32_t x, uint32_t y) {
-    if (msg && len) snprintf(msg, len, fmt, x, y);
-    return SR_E_INVAL;
-  };
-  if (!p || !p->code || p->ncode == 0 || p->ncode > SR_MAX_CODE) return bad("code size %u outside 1..%u", p ? p->ncode : 0, SR_MAX_CODE);
-  if (!p->kernel_entry || p->nkernels == 0) return bad("no kernels (%u, %u)", 0, 0);
-  for (uint32_t k = 0; k < p->nkernels; ++k)
-    if (p->kernel_entry[k] >= p->ncode) return bad("kernel %u entry %u out of range", k, p->kernel_entry[k]);
-  for (uint32_t pc = 0; pc < p->ncode; ++pc) {
-    const uint32_t w = p->code[pc].op_d_a_b, op = w & 0xFFu, b = op & 0x7Fu;
-    const uint32_t d = (w >> 8) & 0xFFu, ra = (w >> 16) & 0xFFu, rb = (w >> 24) & 0xFFu;
-    const int32_t imm = p->code[pc].imm;
-    const bool alu = b >= SR_OP_MOV && b <= SR_OP_SNE;
-    if (b < SR_OP_MOV || b > SR_OP_EXIT || (op & 0x40u) || ((op & SR_BIMM) && !alu)) return bad("pc %u: bad opcode 0x%x", pc, op);
-    auto reg_ok = [](uint32_t r) { return r < 16 || r == SR_RZ; };
-    if ((op_writes_d(b) && !reg_ok(d)) || (op_reads_a(b) && !reg_ok(ra)) || (op_reads_b(op) && !reg_ok(rb)))
-      return bad("pc %u: bad register field (op %u)", pc, b);
-    if ((b == SR_OP_BRA || b == SR_OP_BRZ || b == SR_OP_BRNZ) && (imm < 0 || (uint32_t)imm > p->ncode))
-      return bad("pc %u: branch target %u out of range", pc, (uint32_t)imm);
-    if (b == SR_OP_S2R && (imm < 0 || imm > SR_SREG_WARPSIZE)) return bad("pc %u: bad special register %u", pc, (uint32_t)imm);
-  }
-  if (p->nlaunches && !p->launches) return bad("launch table missing (%u launches)", p->nlaunches, 0);
-  for (uint32_t l = 0; l < p->nlaunches; ++l) {
-    const sr_launch& L = p->launches[l];
-    if (L.kernel >= p->nkernels) return bad("launch %u: kernel %u out of range", l, L.kernel);
-    if (L.grid == 0 || L.grid > (1u << 30)) return bad("launch %u: grid %u", l, L.grid);
-    if (L.block_dim == 0 || L.block_dim > SR_MAX_BLOCK_DIM) return bad("launch %u: block_dim %u", l, L.block_dim);
-    if (L.shmem_words > SR_MAX_SHMEM_WORDS) return bad("launch %u: shmem_words %u", l, L.shmem_words);
-    if (L.nparams > 4) return bad("launch %u: nparams %u", l, L.nparams);
-  }
-  if (p->global_words >= (1ull << 31)) return bad("global arena too large (%u)", (uint32_t)(p->global_words >> 20), 0);
-  if (p->global_words && !p->global_init) return bad("global_init missing (%u words)", (uint32_t)p->global_words, 0);
-  return SR_OK;
-}
-
-// Register renaming of one program: the registers it touches (plus the parameter
-// registers r0..r(maxp-1)) become rows 0..n-1 in ascending order, the zero row is n.
-struct RegMap {
-  uint8_t row[256];
-  uint32_t nrows;
-};
-RegMap map_registers(const sr_program& P) {
-  bool used[16] = {};
-  uint32_t maxp = 0;
-  for (uint32_t l = 0; l < P.nlaunches; ++l) maxp = std::max(maxp, P.launches[l].nparams);
-  for (uint32_t r = 0; r < maxp; ++r) used[r] = true;
-  for (uint32_t pc = 0; pc < P.ncode; ++pc) {
-    const uint32_t w = P.code[pc].op_d_a_b, op = w & 0xFFu, b = op & 0x7Fu;
-    const uint32_t d = (w >> 8) & 0xFFu, ra = (w >> 16) & 0xFFu, rb = (w >> 24) & 0xFFu;
-    if (op_writes_d(b) && d < 16) used[d] = true;
-    if (op_reads_a(b) && ra < 16) used[ra] = true;
-    if (op_reads_b(op) && rb < 16) used[rb] = true;
-  }
-  RegMap m;
-  uint32_t n = 0;
-  for (uint32_t r = 0; r < 16; ++r) m.row[r] = used[r] ? (uint8_t)n++ : 0;
-  m.nrows = n + 1;
-  return m;
-}
-
-// pack one instruction: sources that are RZ or unused read the zero row; destinations
-// that are RZ or absent become kNoDest
-uint2 pack(const sr_instr& in, const RegMap& m) {
-  const uint32_t w = in.op_d_a_b, op = w & 0xFFu, b = op & 0x7Fu;
-  uint32_t d = (w >> 8) & 0xFFu, ra = (w >> 16) & 0xFFu, rb = (w >> 24) & 0xFFu;
-  const uint32_t zrow = m.nrows - 1;
-  d = (op_writes_d(b) && d != SR_RZ) ? m.row[d] : sr::kNoDest;
-  ra = (op_reads_a(b) && ra != SR_RZ) ? m.row[ra] : zrow;
-  rb = (op_reads_b(op) && rb != SR_RZ) ? m.row[rb] : zrow;
-  return make_uint2(op | d << 8 | ra << 16 | rb << 24, (uint32_t)in.imm);
-}
-
-uint32_t key_bits_for(uint32_t shw) {
-  uint32_t b = 1;
-  while ((1u << b) < shw) ++b;
-  return b;
 }
 
 void free_batch_buffers(sr_ctx* c, sr_batch* b, cudaStream_t s) {
@@ -465,7 +312,12 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
     b->arena_words[i] = P.global_words;
     arena_total += (P.global_words + 3) & ~3ull;
     std::vector<KernelBound> kb(P.nkernels);
-    for (uint32_t k = 0; k < P.nkernels; ++k) kb[k] = bound_kernel(P.code, P.ncode, P.kernel_entry[k]);
+    {
+      std::vector<uint8_t> colour(P.ncode + 1);
+      std::vector<uint32_t> acc(P.ncode + 1), bar(P.ncode + 1), spc(P.ncode + 1), snx(P.ncode + 1);
+      const BoundScratch ws{colour.data(), acc.data(), bar.data(), spc.data(), snx.data()};
+      for (uint32_t k = 0; k < P.nkernels; ++k) kb[k] = bound_kernel(P.code, P.ncode, P.kernel_entry[k], ws);
+    }
     for (uint32_t l = 0; l < P.nlaunches; ++l) {
       const sr_launch& L = P.launches[l];
       LaunchDev d{};
@@ -482,17 +334,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       d.block_base = (uint32_t)nblocks;
       d.key_bits = key_bits_for(std::max(1u, L.shmem_words));
       const KernelBound& k = kb[L.kernel];
-      uint64_t recs, misc;
-      if (k.cyclic) {
-        recs = o.loop_log_records;
-        misc = std::max<uint64_t>(256, 4ull * (1 + k.err_pcs));
-      } else {
-        recs = (uint64_t)k.accesses * L.block_dim;
-        misc = (uint64_t)(k.barriers + 1) * (1 + k.err_pcs) + 1;
-      }
-      if (!o.check_races) recs = 0;
-      uint64_t cap = recs + 2 * misc;
-      cap = (cap + 1) & ~1ull;
+      const uint64_t cap = launch_log_cap(k, L.block_dim, o.check_races, o.loop_log_records);
       if (cap >= (1ull << 31)) {
         delete b;
         return fail(c, SR_E_INVAL, "program %u launch %u: access log bound too large", i, l);
