@@ -1,22 +1,25 @@
-"""Benchmark: checked shared accesses per second on the plain single-program workload.
+"""Benchmark: checked shared accesses per second (race-checked SIMT interpretation).
 
-Workload: a shared-memory tree reduction over 2^24 int32 values uniform in [0, 100)
-(SplitMix64 seed 1), 16384 blocks x 1024 threads, the barrier after level 3 missing
-(so every block reports 32 races).  One step = one pass of the whole hot path: arena
-reset, SIMT interpretation with access logging, race check of every barrier interval,
-barrier checks, canonical report ordering.
+Default workload (the plain single program): a shared-memory tree reduction over 2^24
+int32 values uniform in [0, 100) (SplitMix64 seed 1), 16384 blocks x 1024 threads, the
+barrier after level 3 missing (every block reports 32 races).  One step = one pass of
+the whole hot path: arena reset, SIMT interpretation with access logging, race check of
+every barrier interval, barrier checks, canonical report ordering.
 
-  value  : checked shared accesses / s with programs resident on the device
+  value  : checked shared accesses / s with the programs resident on the device
   e2e    : the same metric through the C ABI from pinned host buffers, per step
            load_programs (H2D) + run_and_check + fetch_reports + fetch_memory (D2H)
-  roofline / cpu_baseline / clocks as described in the design doc
+  roofline, cpu_baseline, clocks: see the design doc (measurement section)
 
+Other workloads (--workload): ``batched`` = 4096 seed-generated programs (batched and
+plain paths both timed), ``stencil2d`` = the 8192^2, 16-launch log-heavy stencil.
 --impl reference times the CPU oracle on a bounded block sample of the same workload.
-Under torchrun each rank runs its own copy of the workload (seed 1 + rank): weak scaling.
+Under torchrun each rank runs its own copy of the workload (seed + rank): weak scaling.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -30,8 +33,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "checked shared accesses/s (race-checked SIMT interpretation)"
 UNIT = "accesses/s"
-WORKLOAD = "plain single program: shared-memory tree reduction over 2^24 int32, 16384 blocks x 1024 threads, " \
-           "missing barrier at level 3 (seed 1)"
+WORKLOADS = {
+    "reduction": "plain single program: shared-memory tree reduction over 2^24 int32, 16384 blocks x 1024 threads, "
+                 "missing barrier at level 3 (seed 1)",
+    "batched": "batched: 4096 seed-generated programs (reduction / 1-D stencil / 32x32 transpose / shared-atomic "
+               "histogram), blocks log-uniform 1-4096, blockDim 32-1024, 30% planted bugs (seed 3)",
+    "stencil2d": "log-heavy: 2-D 5-point stencil on 8192x8192 int32, 32x32 blocks, 16 launches, staging barrier "
+                 "omitted in launch 8 (seed 4)",
+}
 
 
 def parse():
@@ -40,27 +49,35 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="reduction", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-blocks", type=int, default=16384)
     ap.add_argument("--interp-variant", type=int, default=0, choices=[0, 1, 2],
                     help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-blocks", type=int, default=0, help="oracle sample (blocks per launch; 0 = auto)")
     ap.add_argument("--blocks", type=int, default=16384,
-                    help="blocks of the reduction (default: the full 2^24-element workload; smaller only "
-                         "for profiling captures)")
+                    help="blocks of the reduction (default: the full workload; smaller only for profiling)")
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def workload(rank: int, blocks: int = 16384):
-    from paper_1211_6193_gb300.workloads import families
-    return families.reduction_plain(n_blocks=blocks, bdim=1024, seed=1 + rank, omit_level=3)
+def workload(name: str, rank: int, blocks: int = 16384):
+    from paper_1211_6193_gb300.workloads import families, stencil2d
+    if name == "reduction":
+        return [families.reduction_plain(n_blocks=blocks, bdim=1024, seed=1 + rank, omit_level=3)]
+    if name == "batched":
+        return families.batch(n_programs=4096, seed=3 + rank)
+    return [stencil2d.program(log2w=13, steps=16, buggy_launch=8, seed=4 + rank)]
+
+
+def workload_label(args):
+    if args.workload == "reduction" and args.blocks != 16384:
+        return f"reduction, {args.blocks} blocks x 1024 threads (profiling size)"
+    return WORKLOADS[args.workload]
 
 
 # ----------------------------------------------------------------- clocks
@@ -102,8 +119,9 @@ class ClockSampler:
         os.unlink(self.f.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        num = lambda x: x.replace(".", "").isdigit()
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for r in rows if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
@@ -111,43 +129,92 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle
-def oracle_rate(prog, sample_blocks: int):
+def oracle_rate(progs, sample_blocks: int):
+    """Oracle on `sample_blocks` blocks of every launch, all host cores."""
     import oracle
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    r = oracle.run([prog], max_blocks=sample_blocks, nthreads=cores)
+    r = oracle.run(progs, max_blocks=sample_blocks, nthreads=cores)
     dt = time.perf_counter() - t0
     return r.shared_accesses / dt, r.thread_instrs / dt, cores, dt, r.shared_accesses
+
+
+def default_sample(name: str) -> int:
+    return {"reduction": 16384, "batched": 8, "stencil2d": 256}[name]
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    prog = workload(0, args.blocks)
+    progs = workload(args.workload, 0, args.blocks)
+    sample = args.cpu_sample_blocks or default_sample(args.workload)
     for _ in range(args.warmup):
-        oracle_rate(prog, 64)
-    per = []
-    acc = ins = 0
+        oracle_rate(progs, 1)
+    per, acc = [], 0
+    cores = os.cpu_count() or 1
     for _ in range(args.steps):
-        rate, irate, cores, dt, n = oracle_rate(prog, args.cpu_sample_blocks)
+        _, _, cores, dt, n = oracle_rate(progs, sample)
         per.append(dt)
         acc += n
-    total = sum(per)
-    value = acc / total
-    sample = f"blocks 0..{args.cpu_sample_blocks - 1} of the workload per step, oracle on {cores} host threads"
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "cpu oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    value = acc / sum(per)
+    desc = f"first {sample} blocks of every launch per step, oracle on {cores} host threads"
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": workload_label(args), "parallelism": "cpu oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
 # ----------------------------------------------------------------- GPU
+def src_sha(*names):
+    h = hashlib.sha1()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1211_6193_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel: str, src: str, blocks: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    t = json.load(open(path)).get(kernel)
+    if not t or t.get("src_sha1") != src:
+        return None
+    return t["dram_bytes_per_block"] * blocks
+
+
+def measure(binding, torch, progs, mode, variant, steps, warmup, flush, stream):
+    """Time `steps` runs of run_and_check on resident programs (L2 flushed between steps)."""
+    ctx = binding.Context(mode=mode, profile=True, interp_variant=variant, use_graph=False)
+    batch = ctx.load_programs(progs)
+    for _ in range(max(3, warmup)):
+        batch.run_and_check()
+    n_reports = len(batch.fetch_reports())
+    stats = batch.stats()
+    stage = {"reset": [], "interp": [], "check": [], "compact": []}
+    per_step = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run_and_check()
+        e1.record(stream)
+        e1.synchronize()
+        per_step.append(e0.elapsed_time(e1))
+        s = batch.stats()
+        for k in stage:
+            stage[k].append(getattr(s, "ms_" + k))
+    batch.free()
+    ctx.close()
+    return stats, n_reports, per_step, {k: statistics.mean(v) for k, v in stage.items()}
+
+
 def run_native(args):
-    import numpy as np
     import torch
 
     from paper_1211_6193_gb300 import binding
@@ -158,21 +225,14 @@ def run_native(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    prog = workload(rank, args.blocks)
-    peaks = {}
+    progs = workload(args.workload, rank, args.blocks)
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = json.load(open(pk))
+    peaks = json.load(open(pk)) if os.path.exists(pk) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-
-    ctx = binding.Context(mode=args.mode, profile=True, interp_variant=args.interp_variant)
-    batch = ctx.load_programs([prog])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 129 MB L2
-    for _ in range(max(3, args.warmup)):
-        batch.run_and_check()
-    n_reports = len(batch.fetch_reports())
-    st = batch.stats()
+    nblocks = sum(l.grid for p in progs for l in p.launches)
 
     def barrier():
         torch.cuda.synchronize()
@@ -180,24 +240,12 @@ def run_native(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    stage = {"interp": [], "check": [], "compact": [], "reset": []}
-    per_step = []
+    mode = "batched" if args.workload == "batched" else args.mode
     with ClockSampler(local) as clocks:
         barrier()
         t_wall = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            batch.run_and_check()
-            e1.record(stream)
-            e1.synchronize()
-            per_step.append(e0.elapsed_time(e1))
-            s = batch.stats()
-            stage["interp"].append(s.ms_interp)
-            stage["check"].append(s.ms_check)
-            stage["compact"].append(s.ms_compact)
-            stage["reset"].append(s.ms_reset)
+        st, n_reports, per_step, stage = measure(binding, torch, progs, mode, args.interp_variant, args.steps,
+                                                 args.warmup, flush, stream)
         barrier()
         t_wall = time.perf_counter() - t_wall
     clk = clocks.summary()
@@ -206,73 +254,82 @@ def run_native(args):
         t = torch.tensor([dev_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         dev_ms = float(t.item())
-    acc_per_step = st.shared_accesses
-    value = world * acc_per_step * args.steps / (dev_ms / 1e3)
+    value = world * st.shared_accesses * args.steps / (dev_ms / 1e3)
     thread_instr_rate = world * st.thread_instrs * args.steps / (dev_ms / 1e3)
 
-    # ---- roofline of the dominant kernel (algorithmic bytes / CUDA-event duration)
-    interp_ms = statistics.mean(stage["interp"])
-    check_ms = statistics.mean(stage["check"])
-    compact_ms = statistics.mean(stage["compact"])
-    dominant = max((interp_ms, "interpreter"), (check_ms, "race check"), (compact_ms, "compaction"))
-    interp_bytes = 8 * st.shared_accesses + 4 * st.global_accesses
-    check_bytes = 8 * st.shared_accesses + 16 * (n_reports)
-    compact_bytes = 16 * n_reports + 32 * n_reports
-    dom_bytes, dom_ms = {"interpreter": (interp_bytes, interp_ms), "race check": (check_bytes, check_ms),
-                         "compaction": (compact_bytes, compact_ms)}[dominant[1]]
-    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dominant[1], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                "stage_ms": {"reset": statistics.mean(stage["reset"]), "interp": interp_ms, "check": check_ms,
-                             "compact": compact_ms},
-                "checker_hbm_frac": (check_bytes / (check_ms / 1e3) / 1e9) / hbm_peak if check_ms > 0 else None}
+    plain = None
+    if args.workload == "batched":     # the same programs through one kernel launch per (program, launch)
+        pst, _, pper, pstage = measure(binding, torch, progs, "plain", args.interp_variant, max(2, args.steps // 2),
+                                       1, flush, stream)
+        pms = sum(pper) / len(pper)
+        plain = {"value": pst.shared_accesses / (pms / 1e3), "ms_per_step": pms, "stage_ms": pstage,
+                 "batched_speedup": pms / (dev_ms / args.steps)}
 
-    # ---- end to end through the C ABI from pinned host buffers
-    arena_pinned = torch.empty(prog.global_init.size, dtype=torch.int32, pin_memory=True)
-    arena_pinned.numpy()[:] = prog.global_init
-    prog_pinned = type(prog)(prog.code, prog.kernel_entry, prog.launches, arena_pinned.numpy(), prog.name)
-    out_arena = torch.empty(prog.global_init.size, dtype=torch.int32, pin_memory=True).numpy()
-    h2d = prog.global_init.nbytes + prog.code.nbytes
-    d2h = out_arena.nbytes + n_reports * 32
-    e2e_times = []
-    ctx_e2e = binding.Context(mode=args.mode, report_cap=max(16, n_reports), interp_variant=args.interp_variant)
-    for i in range(1 + min(args.steps, 5)):
-        barrier()
-        t0 = time.perf_counter()
-        with ctx_e2e.load_programs([prog_pinned]) as b:
-            b.run_and_check()
-            reps = b.fetch_reports()
-            b.fetch_memory(0, out_arena)
-        torch.cuda.synchronize()
-        if i:
-            e2e_times.append(time.perf_counter() - t0)
-    e2e_value = world * acc_per_step / statistics.mean(e2e_times)
+    # ---- rooflines: the interpreter (dominant) is bound by integer issue, the checker by HBM
+    int_peak = 152 * 128 * sm_max * 1e6            # int32 lane-ops/s: 152 SMs x 128 lanes x max clock
+    interp_rate = st.thread_instrs / (stage["interp"] / 1e3)
+    check_bytes = 8 * st.shared_accesses + 16 * n_reports
+    check_gbs = check_bytes / (stage["check"] / 1e3) / 1e9 if stage["check"] > 0 else 0.0
+    isha, csha = src_sha("interp.cu", "sr_internal.h"), src_sha("check.cu", "sr_internal.h")
+    roofline = {"bound": "alu", "kernel": "k_interp_plain" if mode == "plain" else "k_interp_batched",
+                "achieved": interp_rate, "peak": int_peak, "unit": "int32 ops/s", "frac": interp_rate / int_peak,
+                "algorithmic_unit": "simulated thread-instruction",
+                "traffic": traffic_per_launch("k_interp_plain", isha, nblocks) if mode == "plain" else None,
+                "peak_source": "derived: 152 SMs x 128 int32 lanes x sm_max_mhz (MEASURED_PEAKS.json)",
+                "stage_ms": stage,
+                "checker": {"bound": "hbm", "kernel": "k_check", "achieved": check_gbs, "peak": hbm_peak,
+                            "unit": "GB/s", "frac": check_gbs / hbm_peak, "peak_source": peak_src,
+                            "algorithmic_bytes": "8 B read per logged access + 16 B per race entry",
+                            "traffic": traffic_per_launch("k_check", csha, nblocks)}}
+
+    # ---- end to end through the C ABI from pinned host buffers (single-program workloads)
+    e2e = None
+    if args.workload != "batched":
+        prog = progs[0]
+        arena_pinned = torch.empty(prog.global_init.size, dtype=torch.int32, pin_memory=True)
+        arena_pinned.numpy()[:] = prog.global_init
+        prog_pinned = type(prog)(prog.code, prog.kernel_entry, prog.launches, arena_pinned.numpy(), prog.name)
+        out_arena = torch.empty(prog.global_init.size, dtype=torch.int32, pin_memory=True).numpy()
+        h2d = prog.global_init.nbytes + prog.code.nbytes
+        d2h = out_arena.nbytes + n_reports * 32
+        times = []
+        ctx_e2e = binding.Context(mode=mode, report_cap=max(16, n_reports), interp_variant=args.interp_variant)
+        for i in range(1 + min(args.steps, 5)):
+            barrier()
+            t0 = time.perf_counter()
+            with ctx_e2e.load_programs([prog_pinned]) as b:
+                b.run_and_check()
+                b.fetch_reports()
+                b.fetch_memory(0, out_arena)
+            torch.cuda.synchronize()
+            if i:
+                times.append(time.perf_counter() - t0)
+        ctx_e2e.close()
+        e2e = {"value": world * st.shared_accesses / statistics.mean(times), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, irate, cores, dt, n = oracle_rate(prog, args.cpu_sample_blocks)
+        sample = args.cpu_sample_blocks or default_sample(args.workload)
+        rate, irate, cores, dt, n = oracle_rate(progs, sample)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"blocks 0..{args.cpu_sample_blocks - 1} of the workload ({n} accesses, {dt:.1f} s)",
+               "sample": f"first {sample} blocks of every launch ({n} accesses, {dt:.1f} s)",
                "thread_instrs_per_s": irate}
-    kernels_per_step = 6 if args.mode == "plain" else 6
+    launches_per_step = sum(len(p.launches) for p in progs) if mode == "plain" else 1
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.blocks == 16384 else f"reduction, {args.blocks} blocks x 1024",
-                       "mode": args.mode, "blocks": args.blocks, "threads_per_block": 1024,
-                       "parallelism": f"{world} independent replicas" if world > 1 else "single GPU",
-                       "l2": "flushed between timed steps (256 MB write), log > L2"},
-            "sim_thread_instrs_per_s": thread_instr_rate,
-            "shared_accesses_per_step": acc_per_step, "reports_per_step": n_reports,
-            "wall_s": t_wall,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "gpu_launches": kernels_per_step * args.steps}
+            "config": {"workload": workload_label(args), "mode": mode, "blocks": nblocks,
+                       "programs": len(progs), "parallelism": f"{world} independent replicas" if world > 1
+                       else "single GPU", "l2": "flushed between timed steps (256 MB write); logs exceed L2"},
+            "sim_thread_instrs_per_s": thread_instr_rate, "shared_accesses_per_step": st.shared_accesses,
+            "reports_per_step": n_reports, "wall_s": t_wall, "e2e": e2e, "roofline": roofline,
+            "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": args.steps * (launches_per_step + 5)}
+    if plain is not None:
+        line["plain_path"] = plain
     if rank == 0:
         print(json.dumps(line), flush=True)
-    batch.free()
-    ctx.close()
-    ctx_e2e.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -26,6 +26,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr uint32_t NT = kCheckThreads;
 constexpr uint32_t T = kCheckTile;
 constexpr uint32_t NB = kCheckBins;
+constexpr uint32_t NBUF = kCheckBuffers;
 constexpr uint32_t NONE = 0xFFFFu;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -169,9 +170,9 @@ __device__ uint32_t cta_exclusive_scan(uint32_t* a, uint32_t len, uint32_t* wtot
 constexpr uint32_t MAXSEG = 256;   // barrier intervals handled per staged tile
 
 struct Smem {
-  unsigned long long* tile[2];  // T + 2 staged records each (double buffer)
+  unsigned long long* tile[2];  // T + 2 staged records each (NBUF buffers)
   unsigned long long* sorted;   // T
-  uint32_t* sbin;               // T: bin of sorted[i]
+  uint16_t* sbin;               // T: bin of sorted[i]
   uint32_t* bins;               // NB
   uint32_t* flags;              // 2T
   uint16_t* segidx;             // T: interval of each tile record
@@ -259,7 +260,7 @@ __device__ uint32_t sort_intervals(const Smem& S, const unsigned long long* tile
     const uint32_t b = S.flags[T + i];
     const uint32_t pos = atomicAdd(&S.bins[b], 1u);
     S.sorted[pos] = tile[base + i];
-    S.sbin[pos] = b;
+    S.sbin[pos] = (uint16_t)b;
   }
   __syncthreads();
   m_out = m;
@@ -383,16 +384,17 @@ __device__ uint32_t find_intervals(const Smem& S, const unsigned long long* tile
   return nseg;
 }
 
-__global__ void __launch_bounds__(NT, 1) k_check(CheckArgs A) {
+__global__ void __launch_bounds__(NT, kCheckCtasPerSm) k_check(CheckArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ uint32_t s_next;
   Smem S;
   unsigned char* p = smem;
   S.tile[0] = reinterpret_cast<unsigned long long*>(p); p += (T + 2) * 8;
-  S.tile[1] = reinterpret_cast<unsigned long long*>(p); p += (T + 2) * 8;
+  S.tile[1] = NBUF == 2 ? reinterpret_cast<unsigned long long*>(p) : S.tile[0];
+  p += (NBUF - 1) * (T + 2) * 8;
   S.sorted = reinterpret_cast<unsigned long long*>(p); p += T * 8;
-  S.sbin = reinterpret_cast<uint32_t*>(p); p += T * 4;
+  S.sbin = reinterpret_cast<uint16_t*>(p); p += T * 2;
   S.bins = reinterpret_cast<uint32_t*>(p); p += NB * 4;
   S.flags = reinterpret_cast<uint32_t*>(p); p += 2 * T * 4;
   S.segidx = reinterpret_cast<uint16_t*>(p); p += T * 2;
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(NT, 1) k_check(CheckArgs A) {
       const uint32_t off = pos & 1u, cnt = min(T, n - pos);
       const unsigned long long* tile = S.tile[cur] + off;
       const bool last_tile = pos + cnt == n;
-      if (last_tile && !prefetched) {            // stage the next block while this one is checked
+      if (NBUF == 2 && last_tile && !prefetched) {   // stage the next block while this one is checked
         next_gb = claim(cur ^ 1u);
         prefetched = true;
       }
@@ -460,6 +462,10 @@ __global__ void __launch_bounds__(NT, 1) k_check(CheckArgs A) {
       // the last interval of a tile may continue in the next tile unless the block ends here
       const bool tail_open = !last_tile && cnt_eff == cnt;
       uint32_t sidx = 0, consumed = 0;
+      if (large && rec_epoch(tile[0]) != large_epoch) {   // it ended exactly at the last tile boundary
+        finish_large(S, large_epoch, table, out, race_out);
+        large = false;
+      }
       if (large) {                               // the first interval continues the large one
         uint32_t m;
         sort_intervals(S, tile, 0, 1, m);
@@ -501,9 +507,9 @@ __global__ void __launch_bounds__(NT, 1) k_check(CheckArgs A) {
       if (failed) atomicOr(A.error_flag, 1u);
     }
     if (failed) break;
-    if (!prefetched) next_gb = claim(cur ^ 1u);
+    if (!prefetched) next_gb = claim(NBUF == 2 ? cur ^ 1u : 0u);
     gb = next_gb;
-    cur ^= 1u;
+    if (NBUF == 2) cur ^= 1u;
     __syncthreads();
   }
 }
@@ -511,7 +517,7 @@ __global__ void __launch_bounds__(NT, 1) k_check(CheckArgs A) {
 }  // namespace
 
 uint32_t check_smem_bytes() {
-  return 2 * (T + 2) * 8 + T * 8 + T * 4 + NB * 4 + 2 * T * 4 + T * 2 + (MAXSEG + 4) * 4 + 3 * MAXSEG * 4 +
+  return NBUF * (T + 2) * 8 + T * 8 + T * 2 + NB * 4 + 2 * T * 4 + T * 2 + (MAXSEG + 4) * 4 + 3 * MAXSEG * 4 +
          (NB / 32 + 1) * 4 + 36 * 4 + 64;
 }
 

@@ -411,7 +411,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       }
     w.item1 = (uint32_t)b->items.size();
   }
-  b->check_ctas = (uint32_t)c->sms;          // one 1024-thread checker CTA per SM
+  b->check_ctas = (uint32_t)c->sms * sr::kCheckCtasPerSm;
 
   // ---- device buffers
   int rc = SR_OK;

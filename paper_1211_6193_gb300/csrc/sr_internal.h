@@ -117,8 +117,10 @@ struct CheckArgs {
 };
 cudaError_t launch_check(const CheckArgs& a, uint32_t ctas, cudaStream_t s);
 uint32_t check_smem_bytes();
-constexpr uint32_t kCheckThreads = 1024;
-constexpr uint32_t kCheckTile = 4096;          // records per staged tile
+constexpr uint32_t kCheckThreads = 512;
+constexpr uint32_t kCheckTile = 2048;          // records per staged tile
+constexpr uint32_t kCheckBuffers = 1;          // staged tiles per CTA (2 = prefetch the next block)
+constexpr uint32_t kCheckCtasPerSm = 2;
 constexpr uint32_t kCheckBins = 12288;         // counting-sort bins (>= the largest shared array)
 constexpr uint32_t kScratchWords = 1u << 14;   // summaries per CTA in the large-interval path
 

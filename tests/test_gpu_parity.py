@@ -156,6 +156,29 @@ def test_edge_cases(B, mode):
                   loop_log_records=1 << 18)
 
 
+def _large_interval_programs():
+    """Barrier intervals of 1, 2, 3 and 6 tiles of 2048 records, some ending exactly on a
+    tile boundary, with write-read races on a few words between them."""
+    out = []
+    for k in (2, 4, 6, 3):
+        a = ir.Asm()
+        a.s2r(ir.r2, ir.TID)
+        for j in range(k):                           # k stores per thread: k * 1024 records
+            a.sts(ir.r2, ir.r2, 1024 * j)
+        a.bar()
+        for j in range(k):                           # k loads per thread, one of them racy below
+            a.lds(ir.r3, ir.r2, 1024 * j).add(ir.r4, ir.r4, ir.r3)
+        a.and_(ir.r5, ir.r2, 7).sts(ir.r5, ir.r2)    # 1024 stores to 8 words in the same interval
+        a.bar().stg(ir.r2, ir.r4).exit()
+        out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 3, 1024, 1024 * k, ())], np.zeros(1024, np.int32)))
+    return out
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_intervals_larger_than_a_staged_tile(B, mode):
+    assert_parity(B, _large_interval_programs(), mode)
+
+
 def test_race_check_disabled_keeps_memory_and_barrier_reports(B):
     progs = families.batch(n_programs=24, seed=8, max_grid=4, bug_rate=0.6)
     want = oracle.run(progs, check_races=False)
