@@ -40,6 +40,8 @@ WORKLOADS = {
                "histogram), blocks log-uniform 1-4096, blockDim 32-1024, 30% planted bugs (seed 3)",
     "stencil2d": "log-heavy: 2-D 5-point stencil on 8192x8192 int32, 32x32 blocks, 16 launches, staging barrier "
                  "omitted in launch 8 (seed 4)",
+    "serving": "serving: Poisson arrivals at 2000 jobs/s (seed 5) of programs from the batched generator "
+               "(pool of 512, seed 5), admission by predicted log bytes under a 120 GB budget",
 }
 
 
@@ -55,6 +57,7 @@ def parse():
                     help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-blocks", type=int, default=0, help="oracle sample (blocks per launch; 0 = auto)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving trace length (s)")
     ap.add_argument("--blocks", type=int, default=16384,
                     help="blocks of the reduction (default: the full workload; smaller only for profiling)")
     return ap.parse_args()
@@ -71,6 +74,8 @@ def workload(name: str, rank: int, blocks: int = 16384):
         return [families.reduction_plain(n_blocks=blocks, bdim=1024, seed=1 + rank, omit_level=3)]
     if name == "batched":
         return families.batch(n_programs=4096, seed=3 + rank)
+    if name == "serving":
+        return families.batch(n_programs=512, seed=5 + rank)
     return [stencil2d.program(log2w=13, steps=16, buggy_launch=8, seed=4 + rank)]
 
 
@@ -140,7 +145,7 @@ def oracle_rate(progs, sample_blocks: int):
 
 
 def default_sample(name: str) -> int:
-    return {"reduction": 16384, "batched": 8, "stencil2d": 256}[name]
+    return {"reduction": 16384, "batched": 8, "stencil2d": 256, "serving": 8}[name]
 
 
 def run_reference(args):
@@ -212,6 +217,36 @@ def measure(binding, torch, progs, mode, variant, steps, warmup, flush, stream):
     batch.free()
     ctx.close()
     return stats, n_reports, per_step, {k: statistics.mean(v) for k, v in stage.items()}
+
+
+def run_serving(args):
+    import torch
+
+    from paper_1211_6193_gb300 import serving
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pool = serving.job_pool(512, seed=5 + rank)
+    arrivals = serving.poisson_trace(2000.0, args.serve_seconds, seed=5 + rank)
+    jobs = [serving.Job(k, pool[k % len(pool)], t) for k, t in enumerate(arrivals)]
+    warm = serving.Server(log_budget_bytes=120 << 30, max_inflight=4)
+    warm.serve([serving.Job(k, pool[k], 0.0) for k in range(16)])      # load kernels, warm the allocator
+    warm.close()
+    srv = serving.Server(log_budget_bytes=120 << 30, max_inflight=4)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        _, st = srv.serve(jobs, on_result=lambda jid, r: None)      # latency recorded, result dropped
+        torch.cuda.synchronize()
+    srv.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": st.accesses_per_s * world, "unit": UNIT, "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": st.seconds * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["serving"], "trace_seconds": args.serve_seconds, "jobs": st.jobs},
+            "serving": {"p50_latency_ms": st.p50_ms, "p99_latency_ms": st.p99_ms, "jobs_per_s": st.jobs_per_s,
+                        "batches": st.batches, "mean_batch_jobs": st.mean_batch_jobs,
+                        "max_inflight_batches": st.max_inflight_seen, "peak_log_bytes": st.peak_log_bytes},
+            "clocks": clocks.summary()}), flush=True)
 
 
 def run_native(args):
@@ -338,6 +373,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_native(args)
 

@@ -186,11 +186,20 @@ int run_and_check(sr_ctx* ctx, sr_batch* batch, void* stream);
  * dst == NULL only queries the size.  SR_E_RANGE if cap < total (dst untouched). */
 int fetch_reports(sr_ctx* ctx, sr_batch* batch, sr_report* dst, uint64_t cap, uint64_t* n_total);
 
-/* Copy program `prog`'s final global arena (n_words = its size) to dst. */
+/* prog value of fetch_memory / sr_batch_status that addresses every program at once. */
+#define SR_ALL_PROGRAMS 0xFFFFFFFFu
+
+/* Copy program `prog`'s final global arena (n_words = its size) to dst.  With
+ * prog == SR_ALL_PROGRAMS every arena is copied in one copy, in program order, program k's
+ * at word offset sum over i < k of round_up(global_words_i, 4) (each arena starts on a
+ * 16-byte boundary; padding words are zero); n_words = that sum over all programs.  dst == NULL only queries the size;
+ * SR_E_RANGE if cap_words < n_words.  Synchronises with the batch's stream; dst may be
+ * pageable or page-locked host memory (page-locked copies run at link speed). */
 int fetch_memory(sr_ctx* ctx, sr_batch* batch, uint32_t prog, int32_t* dst, uint64_t cap_words,
                  uint64_t* n_words);
 
-/* SR_ST_* bits of program `prog` after the last run_and_check. */
+/* SR_ST_* bits of program `prog` after the last run_and_check; with prog ==
+ * SR_ALL_PROGRAMS, status points to an array of the batch's n programs' bits. */
 int sr_batch_status(sr_ctx* ctx, sr_batch* batch, uint32_t prog, uint32_t* status);
 
 /* Counters of the last run (synchronises). */

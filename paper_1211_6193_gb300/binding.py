@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsimtcheck.so")
 
 # return codes / constants (include/simtcheck.h)
 SR_OK, SR_E_INVAL, SR_E_NOMEM, SR_E_CUDA, SR_E_TIMEOUT, SR_E_RANGE = 0, -1, -2, -3, -4, -5
+SR_ALL_PROGRAMS = 0xFFFFFFFF
 MODE_PLAIN, MODE_BATCHED = 0, 1
 RACE, DIVERGENCE, DEADLOCK, STEP_LIMIT, ERR_OOB_SHARED, ERR_OOB_GLOBAL, ERR_DIV0 = range(1, 8)
 ST_DEADLOCK, ST_STEP_LIMIT, ST_LOG_OVERFLOW, ST_INTERNAL = 1, 2, 4, 8
@@ -139,6 +140,18 @@ class _Marshalled:
             a.global_init, a.global_words = (arena.ctypes.data if arena.size else None), arena.size
 
 
+def host_empty(n: int, dtype, pinned: bool = False) -> np.ndarray:
+    """Uninitialised host array; page-locked (from PyTorch's caching host allocator) when
+    ``pinned``, so that device-to-host copies into it run at link speed.  The returned
+    array keeps its page-locked block alive until the array and its views are gone."""
+    dtype = np.dtype(dtype)
+    if not pinned:
+        return np.empty(n, dtype=dtype)
+    import torch
+    t = torch.empty(max(1, n * dtype.itemsize), dtype=torch.uint8, pin_memory=True)
+    return t.numpy()[: n * dtype.itemsize].view(dtype)
+
+
 def _stream_handle(stream) -> int:
     if stream is None:
         import torch
@@ -247,15 +260,16 @@ class Batch:
     def __init__(self, ctx: Context, handle, programs: Sequence[Program]):
         self.ctx, self.handle = ctx, handle
         self.nprogs = len(programs)
+        self.arena_words = [int(np.asarray(p.global_init).size) for p in programs]
 
     def run_and_check(self, stream=None) -> None:
         self.ctx._check(self.ctx.lib.run_and_check(self.ctx.handle, self.handle, _stream_handle(stream)))
 
-    def fetch_reports(self) -> np.ndarray:
+    def fetch_reports(self, pinned: bool = False) -> np.ndarray:
         lib = self.ctx.lib
         n = C.c_uint64()
         self.ctx._check(lib.fetch_reports(self.ctx.handle, self.handle, None, 0, C.byref(n)))
-        out = np.zeros(int(n.value), dtype=REPORT_DTYPE)
+        out = host_empty(int(n.value), REPORT_DTYPE, pinned)
         if n.value:
             self.ctx._check(lib.fetch_reports(self.ctx.handle, self.handle, out.ctypes.data, n.value, C.byref(n)))
         return out
@@ -269,10 +283,30 @@ class Batch:
         self.ctx._check(lib.fetch_memory(self.ctx.handle, self.handle, prog, out.ctypes.data, out.size, C.byref(n)))
         return out
 
+    def fetch_all_memory(self, pinned: bool = False) -> List[np.ndarray]:
+        """Every program's final arena with one copy (views into one host buffer)."""
+        lib = self.ctx.lib
+        n = C.c_uint64()
+        self.ctx._check(lib.fetch_memory(self.ctx.handle, self.handle, SR_ALL_PROGRAMS, None, 0, C.byref(n)))
+        buf = host_empty(int(n.value), np.int32, pinned)
+        self.ctx._check(lib.fetch_memory(self.ctx.handle, self.handle, SR_ALL_PROGRAMS,
+                                         buf.ctypes.data if buf.size else None, buf.size, C.byref(n)))
+        out, off = [], 0
+        for w in self.arena_words:
+            out.append(buf[off: off + w])
+            off += (w + 3) & ~3
+        return out
+
     def status(self, prog: int) -> int:
         st = C.c_uint32()
         self.ctx._check(self.ctx.lib.sr_batch_status(self.ctx.handle, self.handle, prog, C.byref(st)))
         return int(st.value)
+
+    def all_status(self) -> np.ndarray:
+        st = np.zeros(max(1, self.nprogs), dtype=np.uint32)
+        self.ctx._check(self.ctx.lib.sr_batch_status(self.ctx.handle, self.handle, SR_ALL_PROGRAMS,
+                                                     st.ctypes.data_as(C.POINTER(C.c_uint32))))
+        return st[: self.nprogs]
 
     def stats(self) -> Stats:
         s = sr_stats()

@@ -453,6 +453,8 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   cudaError_t e = up(b->code, code.data(), code.size() * 8);
   if (e == cudaSuccess) e = up(b->launches_d, b->launches.data(), nl * sizeof(LaunchDev));
   if (e == cudaSuccess) e = up(b->items_d, b->items.data(), b->items.size() * 8);
+  // zero the padding between arenas (each starts on a 16-byte boundary)
+  if (e == cudaSuccess && b->total_arena) e = cudaMemsetAsync(b->arena_init.p, 0, b->total_arena * 4, s);
   for (uint32_t i = 0; i < n && e == cudaSuccess; ++i)
     if (progs[i].global_words)
       e = cudaMemcpyAsync((int32_t*)b->arena_init.p + b->arena_off[i], progs[i].global_init,
@@ -521,7 +523,8 @@ int fetch_reports(sr_ctx* c, sr_batch* b, sr_report* dst, uint64_t cap, uint64_t
     CUDA_TRY(c, cudaStreamSynchronize(s));
   }
   uint32_t err = 0;
-  CUDA_TRY(c, cudaMemcpy(&err, b->err_flag.p, 4, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpyAsync(&err, b->err_flag.p, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
   if (n_total) *n_total = total;
   if (err) return fail(c, SR_E_TIMEOUT, "the race checker's staging wait gave up");
   if (!dst) return SR_OK;
@@ -533,22 +536,26 @@ int fetch_reports(sr_ctx* c, sr_batch* b, sr_report* dst, uint64_t cap, uint64_t
 
 int fetch_memory(sr_ctx* c, sr_batch* b, uint32_t prog, int32_t* dst, uint64_t cap_words, uint64_t* n_words) {
   if (!c || !b) return fail(c, SR_E_INVAL, "null argument");
-  if (prog >= b->nprogs) return fail(c, SR_E_INVAL, "program %u out of range", prog);
-  const uint64_t nw = b->arena_words[prog];
+  const bool all = prog == SR_ALL_PROGRAMS;
+  if (!all && prog >= b->nprogs) return fail(c, SR_E_INVAL, "program %u out of range", prog);
+  // arenas are laid out back to back in program order
+  const uint64_t nw = all ? b->total_arena : b->arena_words[prog];
+  const uint64_t off = all ? 0 : b->arena_off[prog];
   if (n_words) *n_words = nw;
   if (!dst) return SR_OK;
   if (cap_words < nw) return fail(c, SR_E_RANGE, "arena has %llu words", (unsigned long long)nw);
   const DevBuf& src = b->ran ? b->arena_work : b->arena_init;
-  if (nw)
-    CUDA_TRY(c, cudaMemcpyAsync(dst, (int32_t*)src.p + b->arena_off[prog], nw * 4, cudaMemcpyDeviceToHost, b->stream));
+  if (nw) CUDA_TRY(c, cudaMemcpyAsync(dst, (int32_t*)src.p + off, nw * 4, cudaMemcpyDeviceToHost, b->stream));
   CUDA_TRY(c, cudaStreamSynchronize(b->stream));
   return SR_OK;
 }
 
 int sr_batch_status(sr_ctx* c, sr_batch* b, uint32_t prog, uint32_t* status) {
   if (!c || !b || !status) return fail(c, SR_E_INVAL, "null argument");
-  if (prog >= b->nprogs) return fail(c, SR_E_INVAL, "program %u out of range", prog);
-  CUDA_TRY(c, cudaMemcpyAsync(status, (uint32_t*)b->prog_status.p + prog, 4, cudaMemcpyDeviceToHost, b->stream));
+  const bool all = prog == SR_ALL_PROGRAMS;
+  if (!all && prog >= b->nprogs) return fail(c, SR_E_INVAL, "program %u out of range", prog);
+  CUDA_TRY(c, cudaMemcpyAsync(status, (uint32_t*)b->prog_status.p + (all ? 0 : prog),
+                              4 * (all ? b->nprogs : 1), cudaMemcpyDeviceToHost, b->stream));
   CUDA_TRY(c, cudaStreamSynchronize(b->stream));
   return SR_OK;
 }

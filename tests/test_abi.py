@@ -63,6 +63,12 @@ def test_opcode_numbers_match_header():
     assert "#define SR_BIMM 0x80u" in txt and ir.BIMM == 0x80
 
 
+def test_all_programs_sentinel_matches_header():
+    txt = open(os.path.join(ROOT, "include", "simtcheck.h")).read()
+    assert re.search(r"#define SR_ALL_PROGRAMS 0x([0-9A-Fa-f]+)u", txt).group(1).lower() == \
+        f"{binding.SR_ALL_PROGRAMS:x}"
+
+
 def _validate(lib, prog):
     m = binding._Marshalled([prog])
     buf = ctypes.create_string_buffer(256)

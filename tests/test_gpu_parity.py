@@ -198,6 +198,14 @@ def test_waves_and_graph_and_repeat(B):
                 assert [tuple(int(x) for x in r) for r in b.fetch_reports()] == want.report_tuples()
                 for i in range(len(progs)):
                     assert np.array_equal(b.fetch_memory(i), want.arenas[i])
+            # the whole-batch forms: one copy of every arena (pageable and page-locked), every status
+            for pinned in (False, True):
+                whole = b.fetch_all_memory(pinned=pinned)
+                assert len(whole) == len(progs)
+                assert all(np.array_equal(x, w) for x, w in zip(whole, want.arenas))
+            st = b.all_status()
+            assert list(st) == [b.status(i) for i in range(len(progs))]
+            assert list(st & 3) == list(want.status)
 
 
 def test_log_overflow_is_reported_not_silent(B):
