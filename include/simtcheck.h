@@ -153,7 +153,11 @@ typedef struct {
                                 processed in waves that fit); 0 = min(96 GB, half the free memory) */
   uint32_t report_cap;       /* initial report buffer (records); grown on demand; 0 = 1 << 20 */
   const sr_allocator* allocator;  /* NULL = cudaMallocAsync / cudaFreeAsync */
+  uint32_t check_variant;    /* race-check kernel shape, 1..SR_CHECK_VARIANTS (consumer threads,
+                                records per stage, stages, CTAs per SM); 0 = the default */
 } sr_opts;
+
+#define SR_CHECK_VARIANTS 4
 
 typedef struct {
   uint64_t thread_instrs;    /* simulated thread-instructions executed */

@@ -63,7 +63,7 @@ class sr_opts(C.Structure):
                 ("ctas_per_sm", C.c_uint32), ("loop_log_records", C.c_uint32),
                 ("interp_variant", C.c_uint32), ("use_graph", C.c_uint32), ("profile", C.c_uint32),
                 ("spin_limit", C.c_uint32), ("log_budget_mb", C.c_uint32), ("report_cap", C.c_uint32),
-                ("allocator", C.POINTER(sr_allocator))]
+                ("allocator", C.POINTER(sr_allocator)), ("check_variant", C.c_uint32)]
 
 
 class sr_stats(C.Structure):
@@ -208,7 +208,7 @@ class Context:
     def __init__(self, check_races: bool = True, round_budget: int = 0, mode: str = "plain", ctas_per_sm: int = 0,
                  loop_log_records: int = 0, interp_variant: int = 0, use_graph: bool = False,
                  profile: bool = False, spin_limit: int = 0, log_budget_mb: int = 0, report_cap: int = 0,
-                 torch_allocator: bool = True):
+                 torch_allocator: bool = True, check_variant: int = 0):
         self.lib = load_library()
         self.allocator = TorchAllocator() if torch_allocator else None
         o = sr_opts()
@@ -217,6 +217,7 @@ class Context:
         o.ctas_per_sm, o.loop_log_records, o.interp_variant = ctas_per_sm, loop_log_records, interp_variant
         o.use_graph, o.profile, o.spin_limit = int(use_graph), int(profile), spin_limit
         o.log_budget_mb, o.report_cap = log_budget_mb, report_cap
+        o.check_variant = check_variant
         if self.allocator is not None:
             o.allocator = C.pointer(self.allocator.struct)
         self.opts = o

@@ -1,33 +1,51 @@
-// check.cu - race check of the access logs (segmented sort + run scan).
+// check.cu - race check of the access logs.
 //
 // Sec. 3.1 of the paper: a race is two threads accessing the same shared location
 // with no synchronisation point in between, at least one access writing; the access
 // history is cleared at every __syncthreads().  The interpreter wrote one 8-byte
-// record per shared access into a per-block log region, records of a barrier interval
-// contiguous and intervals in order.  This kernel groups each interval's records by
-// word address (a counting sort of the interval staged in shared memory, or a warp
-// __match_any_sync for intervals of at most 32 records) and reduces every group to a
-// summary: the two smallest distinct tids per access kind, and the pc range.  Those
-// summaries decide the conflict classes and the smallest conflicting pair exactly (a
-// lexicographically smallest conflicting pair always uses one of the two smallest tids
-// of each kind involved).  Race entries (epoch, addr, pair, class|pcs; 16 bytes) are
-// written back in address order at the front of the block's region; every entry
-// consumes at least two records, so the writes never reach records not yet read.
+// record per shared access into a per-block log region, the records of a barrier
+// interval contiguous and the intervals in order.
 //
-// Records are staged with TMA bulk copies (cp.async.bulk + mbarrier).  Intervals
-// larger than one tile are folded chunk by chunk into a per-CTA summary table in
-// global memory indexed by address.
+// Grouping the records of an interval by word address is a counting sort whose one
+// digit is the whole 14-bit address, so the groups are never materialised: a table in
+// shared memory holds one 32-bit word per shared word,
+//     tag:18 | first tid:10 | second-tid flag:1 | access kinds:3,
+// updated by one compare-and-swap per record.  Those bits decide whether an address
+// races (two distinct tids, and a write or both a read and an atomic), so a race-free
+// interval is dropped by advancing the tag.  An interval with a racy address is read a
+// second time from the log: each racy address gets an exact summary (the two smallest
+// distinct tids per access kind, and the pc range), from which the conflict classes and
+// the lexicographically smallest conflicting pair follow exactly (such a pair always
+// uses one of the two smallest tids of each kind involved).  Race entries (epoch, addr,
+// pair, class|pcs; 16 bytes) are written in address order at the front of the block's
+// region; every entry consumes at least two records of its interval, so the writes
+// never reach records not yet read.
+//
+// One producer warp per CTA claims groups of blocks and streams their records into a
+// ring of shared-memory stages with TMA bulk copies (cp.async.bulk + mbarrier); the
+// consumer warps take stage after stage and meet at a named barrier only where an
+// interval ends.  Every wait is bounded: a wait that gives up sets the error flag, and
+// the producer drains its copies in flight before the CTA exits.
 #include "sr_internal.h"
 
 namespace sr {
 namespace {
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
-constexpr uint32_t NT = kCheckThreads;
-constexpr uint32_t T = kCheckTile;
-constexpr uint32_t NB = kCheckBins;
-constexpr uint32_t NBUF = kCheckBuffers;
 constexpr uint32_t NONE = 0xFFFFu;
+constexpr uint32_t NB = kCheckBins;
+constexpr uint32_t NBW = NB / 32;              // words of the racy-address bitmap
+constexpr uint32_t DS = NB / 4;                // exact summaries per round (4 table words each)
+constexpr uint32_t END = 0xFFFFFFFFu;
+
+// table word: tag << 14 | tid << 4 | MULTI | kind bits (1 << K_R, 1 << K_W, 1 << K_A)
+constexpr uint32_t TAG_MOD = 1u << 18;
+constexpr uint32_t MULTI = 8u;
+constexpr uint32_t KB_R = 1u << K_R, KB_W = 1u << K_W, KB_A = 1u << K_A;
+
+__device__ __forceinline__ bool entry_racy(uint32_t x) {
+  return (x & MULTI) && ((x & KB_W) || (x & (KB_R | KB_A)) == (KB_R | KB_A));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -38,34 +56,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // pc: low 16 bits lowest pc, high 16 bits highest pc.
 struct Summ { uint32_t r, w, a, pc; };
 
-__device__ __forceinline__ Summ summ_empty() { return Summ{0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, NONE}; }
-
 __device__ __forceinline__ uint32_t min2_add(uint32_t m, uint32_t t) {
   const uint32_t m1 = m & 0xFFFFu, m2 = m >> 16;
   if (t == m1 || t == m2) return m;
   if (t < m1) return m1 << 16 | t;
   if (t < m2) return t << 16 | m1;
   return m;
-}
-__device__ __forceinline__ uint32_t min2_merge(uint32_t m, uint32_t o) {
-  if ((o & 0xFFFFu) != NONE) m = min2_add(m, o & 0xFFFFu);
-  if ((o >> 16) != NONE) m = min2_add(m, o >> 16);
-  return m;
-}
-__device__ __forceinline__ void summ_add(Summ& s, unsigned long long rec) {
-  const uint32_t t = rec_tid(rec), k = rec_kind(rec), pc = rec_pc(rec);
-  if (k == K_R) s.r = min2_add(s.r, t);
-  else if (k == K_W) s.w = min2_add(s.w, t);
-  else s.a = min2_add(s.a, t);
-  const uint32_t lo = min(s.pc & 0xFFFFu, pc), hi = max(s.pc >> 16, pc);
-  s.pc = hi << 16 | lo;
-}
-__device__ __forceinline__ void summ_merge(Summ& s, const Summ& o) {
-  s.r = min2_merge(s.r, o.r);
-  s.w = min2_merge(s.w, o.w);
-  s.a = min2_merge(s.a, o.a);
-  const uint32_t lo = min(s.pc & 0xFFFFu, o.pc & 0xFFFFu), hi = max(s.pc >> 16, o.pc >> 16);
-  s.pc = hi << 16 | lo;
 }
 
 // Conflict classes (write-write, write-read, write-atomic, atomic-read between
@@ -95,10 +91,6 @@ __device__ __forceinline__ bool summ_race(const Summ& s, uint32_t& bout, uint32_
 }
 
 // ---------------------------------------------------------------- TMA staging
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-  asm volatile("mbarrier.init.shared.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
   asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
   asm volatile(
@@ -107,426 +99,713 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phase, uint32_t limit) {
+__device__ __forceinline__ void mbar_init_count(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// non-blocking test of phase completion (a bounded spin loop calls it)
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.test_wait.parity.shared.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for a phase: polls with a growing sleep so that a waiting warp leaves
+// the issue slots and the shared-memory pipe to the warps doing work.  Gives up after
+// `limit` polls, or as soon as *abort is set.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phase, uint32_t limit,
+                                          const volatile uint32_t* abort) {
+  uint32_t ns = 32;
   for (uint32_t it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    if (done) return true;
+    if (mbar_test(bar, phase)) return true;
+    if (*abort) return false;
+    __nanosleep(ns);
+    ns = min(ns * 2u, 256u);
   }
   return false;
 }
 
-// ---------------------------------------------------------------- CTA scans
-// Exclusive scan of one value per thread over the CTA; returns the prefix, total in *tot.
-__device__ uint32_t cta_scan_value(uint32_t v, uint32_t* wtot, uint32_t* tot) {
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(FULL, inc, o);
-    if (lane >= (uint32_t)o) inc += y;
-  }
-  if (lane == 31) wtot[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    const uint32_t x0 = lane < NT / 32 ? wtot[lane] : 0u;
-    uint32_t x = x0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, x, o);
-      if (lane >= (uint32_t)o) x += y;
-    }
-    if (lane < NT / 32) wtot[lane] = x - x0;
-    if (lane == 31) wtot[32] = x;
-  }
-  __syncthreads();
-  const uint32_t r = wtot[wid] + inc - v;
-  *tot = wtot[32];
-  __syncthreads();
-  return r;
+// ---------------------------------------------------------------- consumer barriers
+// Named barrier 1 joins the NC consumer threads; the producer warp never takes part.
+template <uint32_t NC>
+__device__ __forceinline__ void cbar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
+}
+template <uint32_t NC>
+__device__ __forceinline__ bool cbar_or(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{ .reg .pred a, b; setp.ne.u32 a, %1, 0; bar.red.or.pred b, 1, %2, a; selp.u32 %0, 1, 0, b; }"
+      : "=r"(r)
+      : "r"((uint32_t)p), "n"(NC)
+      : "memory");
+  return r != 0;
 }
 
-// In-place exclusive scan of a[0..len) (shared memory); returns the total.
-__device__ uint32_t cta_exclusive_scan(uint32_t* a, uint32_t len, uint32_t* wtot) {
-  const uint32_t per = (len + NT - 1) / NT;
-  const uint32_t b0 = min(len, threadIdx.x * per), b1 = min(len, b0 + per);
-  uint32_t sum = 0;
-  for (uint32_t i = b0; i < b1; ++i) sum += a[i];
-  uint32_t total;
-  uint32_t run = cta_scan_value(sum, wtot, &total);
-  for (uint32_t i = b0; i < b1; ++i) {
-    const uint32_t v = a[i];
-    a[i] = run;
-    run += v;
+// Exclusive prefix of the popcounts of bm[0..nw) into pre[]; returns the total.  Ends
+// with the consumers synchronised.
+template <uint32_t NC>
+__device__ uint32_t scan_bitmap(const uint32_t* bm, uint32_t* pre, uint32_t nw, uint32_t* wtot) {
+  constexpr uint32_t Q = (NBW + NC - 1) / NC, NCW = NC / 32;
+  const uint32_t c = threadIdx.x, lane = c & 31u, w = c >> 5;
+  uint32_t v[Q], s = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < Q; ++q) {
+    const uint32_t i = c * Q + q;
+    v[q] = i < nw ? __popc(bm[i]) : 0u;
+    s += v[q];
   }
-  __syncthreads();
+  uint32_t x = s;
+#pragma unroll
+  for (uint32_t o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wtot[w] = x;
+  cbar<NC>();
+  if (w == 0) {
+    const uint32_t t = lane < NCW ? wtot[lane] : 0u;
+    uint32_t z = t;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, z, o);
+      if (lane >= o) z += y;
+    }
+    if (lane < NCW) wtot[lane] = z - t;
+    if (lane == 31) wtot[NCW] = z;
+  }
+  cbar<NC>();
+  uint32_t base = wtot[w] + x - s;
+#pragma unroll
+  for (uint32_t q = 0; q < Q; ++q) {
+    const uint32_t i = c * Q + q;
+    if (i < nw) pre[i] = base;
+    base += v[q];
+  }
+  const uint32_t total = wtot[NCW];
+  cbar<NC>();
   return total;
 }
 
-constexpr uint32_t MAXSEG = 256;   // barrier intervals handled per staged tile
+// One record (low and high words) into the address table, the tag in the high bits of
+// tagw.  An entry that becomes racy marks the interval in *racy.
+__device__ __forceinline__ void table_add(uint32_t* tab, uint32_t lo, uint32_t hi, uint32_t tagw, uint32_t tag,
+                                          volatile uint32_t* racy, bool& bad) {
+  const uint32_t a = __funnelshift_r(lo, hi, 24) & 0x3FFFu;   // record bits 24..37
+  if (a >= NB) {
+    bad = true;
+    return;
+  }
+  const uint32_t t4 = (lo >> 10) & 0x3FF0u;                   // tid << 4
+  const uint32_t kb = 1u << ((lo >> 12) & 3u);
+  uint32_t old = *(volatile uint32_t*)(tab + a);
+  for (;;) {
+    const uint32_t nw = (old & ~0x3FFFu) != tagw ? (tagw | t4 | kb)
+                                                 : (old | kb | ((old & 0x3FF0u) != t4 ? MULTI : 0u));
+    if (nw == old) return;
+    const uint32_t prev = atomicCAS(tab + a, old, nw);
+    if (prev == old) {
+      if ((nw & MULTI) && entry_racy(nw)) *racy = tag;
+      return;
+    }
+    old = prev;
+  }
+}
 
-struct Smem {
-  unsigned long long* tile[2];  // T + 2 staged records each (NBUF buffers)
-  unsigned long long* sorted;   // T
-  uint16_t* sbin;               // T: bin of sorted[i]
-  uint32_t* bins;               // NB
-  uint32_t* flags;              // 2T
-  uint16_t* segidx;             // T: interval of each tile record
-  uint32_t* seg_start;          // MAXSEG + 1 (record index of each interval of the tile)
-  uint32_t* seg_lo;             // MAXSEG: lowest address of the interval
-  uint32_t* seg_hi;             // MAXSEG
-  uint32_t* seg_off;            // MAXSEG: first bin of the interval
-  uint32_t* touched;            // NB / 32 + 1 bitmap (large intervals)
-  uint32_t* wtot;               // 36 scan words
-  uint32_t* misc;               // broadcast words
+// The records of mask `m` (bit j: record j) into the table at once: all entries are
+// read, all new values computed, and all compare-and-swaps issued before any result is
+// needed.  A swap that lost a race (another thread, or an earlier record of this same
+// thread, wrote the entry) is redone by table_add.
+template <uint32_t P>
+__device__ __forceinline__ void table_add_set(uint32_t* tab, const uint32_t (&lo)[P], const uint32_t (&hi)[P],
+                                              uint32_t m, uint32_t tagw, uint32_t tag, volatile uint32_t* racy,
+                                              bool& bad) {
+  uint32_t a[P], x[P], o[P], n[P];
+#pragma unroll
+  for (uint32_t j = 0; j < P; ++j) {
+    a[j] = __funnelshift_r(lo[j], hi[j], 24) & 0x3FFFu;
+    if (((m >> j) & 1u) && a[j] >= NB) {
+      bad = true;
+      m &= ~(1u << j);
+    }
+    x[j] = ((lo[j] >> 10) & 0x3FF0u) | 1u << ((lo[j] >> 12) & 3u);
+  }
+#pragma unroll
+  for (uint32_t j = 0; j < P; ++j) o[j] = ((m >> j) & 1u) ? *(volatile uint32_t*)(tab + a[j]) : 0u;
+#pragma unroll
+  for (uint32_t j = 0; j < P; ++j) {
+    const uint32_t t4 = x[j] & 0x3FF0u, kb = x[j] & 7u;
+    n[j] = (o[j] & ~0x3FFFu) != tagw ? (tagw | x[j]) : (o[j] | kb | ((o[j] & 0x3FF0u) != t4 ? MULTI : 0u));
+  }
+  uint32_t retry = 0, hit = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < P; ++j) {
+    if (((m >> j) & 1u) && n[j] != o[j]) {
+      const uint32_t prev = atomicCAS(tab + a[j], o[j], n[j]);
+      if (prev != o[j]) retry |= 1u << j;
+      else if ((n[j] & MULTI) && entry_racy(n[j])) hit = 1;
+    }
+  }
+  if (hit) *racy = tag;
+  if (retry) {
+#pragma unroll
+    for (uint32_t j = 0; j < P; ++j)
+      if ((retry >> j) & 1u) table_add(tab, lo[j], hi[j], tagw, tag, racy, bad);
+  }
+}
+
+// One record into an exact summary held in four table words {r, w, a, pc}.
+__device__ __forceinline__ void slot_add(uint32_t* sl, unsigned long long r) {
+  const uint32_t t = rec_tid(r), pc = rec_pc(r);
+  uint32_t* m = sl + rec_kind(r);                 // K_R, K_W, K_A index r, w, a
+  uint32_t old = *(volatile uint32_t*)m;
+  for (;;) {
+    const uint32_t nw = min2_add(old, t);
+    if (nw == old) break;
+    const uint32_t prev = atomicCAS(m, old, nw);
+    if (prev == old) break;
+    old = prev;
+  }
+  old = *(volatile uint32_t*)(sl + 3);
+  for (;;) {
+    const uint32_t nw = max(old >> 16, pc) << 16 | min(old & 0xFFFFu, pc);
+    if (nw == old) break;
+    const uint32_t prev = atomicCAS(sl + 3, old, nw);
+    if (prev == old) break;
+    old = prev;
+  }
+}
+
+// Exact pass over a racy interval [s, e) of the block whose region is `region` (the
+// consumers are synchronised on entry and on return).  Returns the number of race
+// entries written at region (as 16-byte entries) + race_out.
+template <uint32_t NC>
+__device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t* bm, uint32_t* pre, uint32_t* wtot,
+                                               uint4* stage_out, unsigned long long* region, uint32_t race_out,
+                                               uint32_t shw, uint32_t tagw, uint32_t epoch, uint32_t s, uint32_t e) {
+  constexpr uint32_t NCW = NC / 32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t nw = (shw + 31u) >> 5;
+  for (uint32_t wd = warp; wd < nw; wd += NCW) {
+    const uint32_t a = wd * 32u + lane;
+    const uint32_t x = a < shw ? tab[a] : 0u;
+    const uint32_t bits = __ballot_sync(FULL, a < shw && (x & ~0x3FFFu) == tagw && entry_racy(x));
+    if (lane == 0) bm[wd] = bits;
+  }
+  cbar<NC>();
+  const uint32_t M = scan_bitmap<NC>(bm, pre, nw, wtot);
+  uint4* const dst = M <= DS ? reinterpret_cast<uint4*>(region) + race_out : stage_out;
+  for (uint32_t r0 = 0; r0 < M; r0 += DS) {
+    const uint32_t nr = min(DS, M - r0);
+    for (uint32_t j = tid; j < 4u * nr; j += NC) tab[j] = (j & 3u) == 3u ? NONE : 0xFFFFFFFFu;
+    cbar<NC>();
+    for (uint32_t i = s + tid; i < e; i += NC) {
+      const unsigned long long r = region[i];
+      const uint32_t a = rec_addr(r);
+      if (a >= shw) continue;                     // (a logged address is always below shw)
+      const uint32_t word = bm[a >> 5], bit = 1u << (a & 31u);
+      if (!(word & bit)) continue;
+      const uint32_t rank = pre[a >> 5] + __popc(word & (bit - 1u)) - r0;
+      if (rank < nr) slot_add(tab + 4u * rank, r);
+    }
+    cbar<NC>();
+    for (uint32_t wd = warp; wd < nw; wd += NCW) {
+      const uint32_t word = bm[wd];
+      if (!((word >> lane) & 1u)) continue;
+      const uint32_t rank = pre[wd] + __popc(word & ((1u << lane) - 1u)) - r0;
+      if (rank >= nr) continue;
+      const uint32_t* sl = tab + 4u * rank;
+      uint32_t b = 0, c = 0;
+      summ_race(Summ{sl[0], sl[1], sl[2], sl[3]}, b, c);
+      dst[r0 + rank] = make_uint4(epoch, wd * 32u + lane, b, c);
+    }
+    cbar<NC>();
+  }
+  if (M > DS) {                                   // entries were staged: place them now
+    uint4* out = reinterpret_cast<uint4*>(region) + race_out;
+    for (uint32_t i = tid; i < M; i += NC) out[i] = __ldcg(stage_out + i);
+  }
+  for (uint32_t j = tid; j < 4u * min(M, DS); j += NC) tab[j] = 0;
+  cbar<NC>();
+  return M;
+}
+
+// End of the interval [s, e) with epoch `epoch` (consumers synchronised): races of a
+// racy interval, then the next tag and parity.
+template <uint32_t NC>
+__device__ __forceinline__ void close_interval(uint32_t* tab, uint32_t* bm, uint32_t* pre, uint32_t* wtot,
+                                               uint4* stage_out, volatile uint32_t* s_racy,
+                                               unsigned long long* region, uint32_t& race_out, uint32_t shw,
+                                               uint32_t& iv, uint32_t& par, uint32_t& tag, uint32_t& tagw,
+                                               uint32_t epoch, uint32_t s, uint32_t e) {
+  if (s_racy[par] == tag)
+    race_out += racy_interval<NC>(tab, bm, pre, wtot, stage_out, region, race_out, shw, tagw, epoch, s, e);
+  par ^= 1u;
+  if (++iv % TAG_MOD == 0) {                      // tags wrap: forget every entry
+    cbar<NC>();                                   // everyone has read s_racy
+    for (uint32_t i = threadIdx.x; i < NB; i += NC) tab[i] = 0;
+    if (threadIdx.x < 2) s_racy[threadIdx.x] = 0;
+    cbar<NC>();
+    ++iv;
+  }
+  tag = iv % TAG_MOD;
+  tagw = tag << 14;
+}
+
+// The records of one stage (this thread's PER records, as low/high words, nval valid;
+// e0 / elast the epochs of the stage's first and last records, ebefore that of the record
+// before this thread's first), applied interval by interval.  Intervals end here at the
+// stage start (1), inside the stage (2) or at the block end (3); `release` is called once
+// the stage's records have all been read.  Returns the last reason handled (2 if a corrupt
+// log stopped the pass before the release).
+template <uint32_t NC, uint32_t PER, class Release>
+__device__ __forceinline__ uint32_t stage_pass(
+    uint32_t* tab, uint32_t* bm, uint32_t* pre, uint32_t* wtot, uint4* stage_out, volatile uint32_t* s_racy,
+    volatile uint32_t* s_npos, volatile uint32_t* s_nep, BlockRes* blocks, const uint32_t (&lo)[PER],
+    const uint32_t (&hi)[PER], uint32_t nval, uint32_t cbase, uint32_t e0, uint32_t ebefore, uint32_t elast,
+    bool first, bool last, uint32_t pos, uint32_t cnt, uint32_t n, uint32_t gb, unsigned long long* region,
+    uint32_t shw, uint32_t& race_out, uint32_t& ep, uint32_t& ivs, uint32_t& iv, uint32_t& par, uint32_t& tag,
+    uint32_t& tagw, bool& bad, Release release) {
+  uint32_t why = (!first && e0 != ep) ? 1u : 0u;
+  for (;;) {
+    if (why) {
+      cbar<NC>();
+      uint32_t end = n, nep = ep;
+      if (why == 1) {
+        end = pos;
+        nep = e0;
+      } else if (why == 2) {
+        const uint32_t np = s_npos[par];
+        nep = s_nep[par];
+        if (nep <= ep || np >= cnt) {             // epochs out of order: a corrupt log
+          bad = true;
+          return 2;
+        }
+        end = pos + np;
+      }
+      close_interval<NC>(tab, bm, pre, wtot, stage_out, s_racy, region, race_out, shw, iv, par, tag, tagw, ep, ivs,
+                         end);
+      if (why == 3) {
+        if (threadIdx.x == 0) blocks[gb].n_race = race_out;
+        return 3;
+      }
+      ep = nep;
+      ivs = end;
+      why = 0;
+    }
+    uint32_t m = (1u << nval) - 1u;               // this thread's records of interval `ep`
+    if (!(e0 == ep && elast == ep)) {             // the stage holds more than interval `ep`
+#pragma unroll
+      for (uint32_t j = 0; j < PER; ++j) {
+        const uint32_t e = hi[j] >> 6;
+        const uint32_t pe = j ? hi[j ? j - 1 : 0] >> 6 : ebefore;
+        if (e != ep) m &= ~(1u << j);
+        // the record whose predecessor is older notes where the next interval starts
+        if (j < nval && e > ep && pe <= ep && cbase + j > 0) {
+          s_npos[par] = cbase + j;
+          s_nep[par] = e;
+        }
+      }
+    }
+    table_add_set<PER>(tab, lo, hi, m, tagw, tag, s_racy + par, bad);
+    if (elast != ep) {
+      why = 2;
+      continue;
+    }
+    release();
+    if (!last) return 0;
+    why = 3;
+  }
+}
+
+// A stage of the ring: where its records come from.
+struct Desc {
+  unsigned long long* region;   // the block's log region
+  uint32_t gb, pos, cnt, n;     // block, first record of the stage, records staged, records of the block
+  uint32_t shw, flags;          // the launch's shared words; 1 = first stage of the block, 2 = last
 };
 
-// Counting sort of records rec[0..m) (intervals s0..s0+nseg-1 of the tile, starting at
-// record seg_start[s0]) by (interval, address): each interval owns the bins of its own
-// address range, so the sorted order is exactly (epoch, address).  Returns the number
-// of intervals that fit the bin budget (at least one).  Afterwards sorted/sbin hold the
-// records and their bins, bins[b] is the end of bin b's run.
-__device__ uint32_t sort_intervals(const Smem& S, const unsigned long long* tile, uint32_t s0, uint32_t nseg,
-                                   uint32_t& m_out) {
-  const uint32_t tid = threadIdx.x;
-  const uint32_t base = S.seg_start[s0], end = S.seg_start[s0 + nseg];
-  for (uint32_t i = tid; i < nseg; i += NT) { S.seg_lo[s0 + i] = 0xFFFFFFFFu; S.seg_hi[s0 + i] = 0; }
-  __syncthreads();
-  // per-interval address range: a warp whose 32 records share one interval reduces them
-  // first (one atomic pair per warp instead of per record)
-  for (uint32_t i0 = base + (tid & ~31u); i0 < end; i0 += NT) {
-    const uint32_t i = i0 + (tid & 31u);
-    const bool valid = i < end;
-    uint32_t sg = 0, a = 0;
-    if (valid) {
-      sg = S.segidx[i];
-      a = rec_addr(tile[i]);
+template <uint32_t NC, uint32_t T, uint32_t NBUF>
+struct CheckCfg {
+  static constexpr uint32_t NT = NC + 32;       // consumers + one producer warp
+  static constexpr uint32_t NCW = NC / 32;
+  static constexpr uint32_t PER = T / NC;       // records per consumer thread and stage
+  static_assert(PER >= 2 && PER % 2 == 0 && PER * NC == T, "stage must split into pairs of records");
+  static constexpr uint32_t TILE_BYTES = T * 8;
+  static constexpr uint32_t O_TABLE = NBUF * TILE_BYTES;
+  static constexpr uint32_t O_BM = O_TABLE + NB * 4;
+  static constexpr uint32_t O_PRE = O_BM + NBW * 4;
+  static constexpr uint32_t O_DESC = O_PRE + NBW * 4;
+  static constexpr uint32_t O_MISC = O_DESC + NBUF * (uint32_t)sizeof(Desc);
+  static constexpr uint32_t MISC_WORDS = 8 + NCW + 1;
+  static constexpr uint32_t SMEM = O_MISC + MISC_WORDS * 4;
+};
+
+template <uint32_t NC, uint32_t T, uint32_t NBUF, uint32_t MINB>
+__global__ void __launch_bounds__(NC + 32, MINB) k_check(CheckArgs A) {
+  using C = CheckCfg<NC, T, NBUF>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[NBUF], empty[NBUF];
+  const unsigned long long* tiles = reinterpret_cast<const unsigned long long*>(smem);
+  uint32_t* tab = reinterpret_cast<uint32_t*>(smem + C::O_TABLE);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem + C::O_BM);
+  uint32_t* pre = reinterpret_cast<uint32_t*>(smem + C::O_PRE);
+  Desc* desc = reinterpret_cast<Desc*>(smem + C::O_DESC);
+  uint32_t* misc = reinterpret_cast<uint32_t*>(smem + C::O_MISC);
+  volatile uint32_t* s_racy = misc;              // [2] tag of the racy interval, by interval parity
+  volatile uint32_t* s_npos = misc + 2;          // [2] first record of the next interval in the stage
+  volatile uint32_t* s_nep = misc + 4;           // [2] its epoch
+  volatile uint32_t* s_fail = misc + 6;
+  uint32_t* wtot = misc + 8;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+
+  for (uint32_t i = tid; i < NB; i += C::NT) tab[i] = 0;
+  if (tid < 8) misc[tid] = 0;
+  if (tid == 0) {
+    for (uint32_t b = 0; b < NBUF; ++b) {
+      mbar_init_count(&full[b], 1);
+      mbar_init_count(&empty[b], C::NCW);
     }
-    const uint32_t sg0 = __shfl_sync(FULL, sg, 0);
-    if (__all_sync(FULL, !valid || sg == sg0)) {
-      const uint32_t mn = __reduce_min_sync(FULL, valid ? a : 0xFFFFFFFFu);
-      const uint32_t mx = __reduce_max_sync(FULL, valid ? a : 0u);
-      if ((tid & 31u) == 0) {
-        atomicMin(&S.seg_lo[sg0], mn);
-        atomicMax(&S.seg_hi[sg0], mx);
-      }
-    } else if (valid) {
-      atomicMin(&S.seg_lo[sg], a);
-      atomicMax(&S.seg_hi[sg], a);
-    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // bin offsets: a prefix of the intervals whose ranges fit NB bins together (one warp);
-  // a single range never exceeds NB, so at least one interval is always kept
-  if (tid < 32) {
-    uint32_t run = 0, kept = 0;
-    for (uint32_t c = 0; c < nseg; c += 32) {
-      const uint32_t i = c + tid;
-      const uint32_t r = i < nseg ? S.seg_hi[s0 + i] - S.seg_lo[s0 + i] + 1 : 0u;
-      uint32_t inc = r;
+
+  if (warp == C::NCW) {
+    // ------------------------------------------------------------ producer warp
+    uint32_t k = 0;
+    bool failed = false;
+    auto claim = [&]() {
+      uint32_t v = 0;
+      if (lane == 0) v = A.item0 + atomicAdd(A.work_head, 1u);
+      return __shfl_sync(FULL, v, 0);
+    };
+    // wait until stage buffer `buf` is free for the chunk numbered k
+    auto acquire = [&](uint32_t buf) {
+      bool ok = true;
+      if (lane == 0 && k >= NBUF) {
+        const uint32_t ph = ((k / NBUF) & 1u) ^ 1u;
+        ok = mbar_wait(&empty[buf], ph, A.spin_limit, s_fail);
+      }
+      return __shfl_sync(FULL, (uint32_t)ok, 0) != 0;
+    };
+    uint32_t item = claim();
+    while (item < A.item1 && !failed) {
+      uint32_t lo = A.li0, hi = A.li1 - 1;       // launch owning the item
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (A.launches[mid].check_item <= item) lo = mid; else hi = mid - 1;
+      }
+      const LaunchDev* L = A.launches + lo;
+      const uint32_t first = L->block_base + (item - L->check_item) * L->check_group;
+      const uint32_t nb = min(L->check_group, L->block_base + L->grid - first);
+      const uint32_t n_l = lane < nb ? A.blocks[first + lane].n_log : 0u;
+      const unsigned long long* log0 = A.log + L->log_base;
+      const uint32_t cap = L->log_cap, base = L->block_base, shw = L->shw;
+      const uint32_t next = claim();               // in flight while this item streams
+      for (uint32_t b = 0; b < nb && !failed; ++b) {
+        const uint32_t n = __shfl_sync(FULL, n_l, b);
+        if (!n) continue;
+        unsigned long long* region = const_cast<unsigned long long*>(log0) + (unsigned long long)(first + b - base) * cap;
+        for (uint32_t pos = 0; pos < n; pos += T) {
+          const uint32_t buf = k % NBUF;
+          if (!acquire(buf)) { failed = true; break; }
+          if (lane == 0) {
+            const uint32_t cnt = min(T, n - pos);
+            Desc& d = desc[buf];
+            d.region = region;
+            d.gb = first + b;
+            d.pos = pos;
+            d.cnt = cnt;
+            d.n = n;
+            d.shw = shw;
+            d.flags = (pos == 0 ? 1u : 0u) | (pos + cnt == n ? 2u : 0u);
+            bulk_load(const_cast<unsigned long long*>(tiles) + (size_t)buf * T, region + pos, ((cnt + 1u) & ~1u) * 8u,
+                      &full[buf]);
+          }
+          __syncwarp();
+          ++k;
+        }
+      }
+      item = next;
+    }
+    if (!failed) {
+      const uint32_t buf = k % NBUF;
+      if (acquire(buf)) {
+        if (lane == 0) {
+          desc[buf].gb = END;
+          mbar_arrive(&full[buf]);
+        }
+      } else {
+        failed = true;
+      }
+    }
+    if (failed) {
+      if (lane == 0) {
+        *s_fail = 1;
+        atomicOr(A.error_flag, 1u);
+        // every copy issued must land before the CTA may exit
+        for (uint32_t b = 0; b < NBUF && b < k; ++b) {
+          const uint32_t last = b + ((k - 1 - b) / NBUF) * NBUF;
+          const uint32_t never = 0;
+          mbar_wait(&full[b], (last / NBUF) & 1u, A.spin_limit, &never);
+        }
+      }
+      __syncwarp();
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumer warps
+  const uint32_t cbase = tid * C::PER;
+  uint4* const stage_out = A.scratch + (size_t)blockIdx.x * kScratchWords;
+  uint32_t iv = 1, par = 0, tag = 1, tagw = 1u << 14;
+  // per block
+  unsigned long long* region = nullptr;
+  uint32_t gb = 0, race_out = 0, ep = 0, ivs = 0, shw = 0;
+
+  for (uint32_t k = 0;; ++k) {
+    const uint32_t buf = k % NBUF;
+    const bool ok = mbar_wait(&full[buf], (k / NBUF) & 1u, A.spin_limit, s_fail);
+    if (cbar_or<NC>(!ok)) {
+      if (tid == 0) {
+        *s_fail = 1;
+        atomicOr(A.error_flag, 1u);
+      }
+      return;
+    }
+    const Desc& d = desc[buf];
+    const uint32_t d_gb = d.gb;
+    if (d_gb == END) break;
+    const uint32_t d_pos = d.pos, d_cnt = d.cnt, d_n = d.n, d_flags = d.flags;
+    const unsigned long long* tile = tiles + (size_t)buf * T;
+    const uint32_t e0 = rec_epoch(tile[0]);
+    if (d_flags & 1u) {
+      region = d.region;
+      gb = d_gb;
+      shw = d.shw;
+      race_out = 0;
+      ep = e0;
+      ivs = 0;
+    }
+    // this thread's records as (low, high) words; the epoch is the high word >> 6
+    uint32_t lo[C::PER], hi[C::PER];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, inc, o);
-        if (tid >= (uint32_t)o) inc += y;
-      }
-      const bool fits = i < nseg && run + inc <= NB;   // a prefix of the lanes (inc grows)
-      const uint32_t nf = __popc(__ballot_sync(FULL, fits));
-      if (fits) S.seg_off[s0 + i] = run + inc - r;
-      if (nf) run += __shfl_sync(FULL, inc, nf - 1);
-      kept += nf;
-      if (nf < 32) break;
+    for (uint32_t j = 0; j < C::PER; j += 2) {
+      const uint4 v = *reinterpret_cast<const uint4*>(tile + cbase + j);
+      lo[j] = v.x;
+      hi[j] = v.y;
+      lo[j + 1] = v.z;
+      hi[j + 1] = v.w;
     }
-    if (tid == 0) { S.misc[0] = kept; S.misc[1] = run; }
-  }
-  __syncthreads();
-  const uint32_t kept = S.misc[0], nb = S.misc[1];
-  const uint32_t mend = S.seg_start[s0 + kept];
-  const uint32_t m = mend - base;
-  for (uint32_t b = tid; b < nb; b += NT) S.bins[b] = 0;
-  __syncthreads();
-  for (uint32_t i = base + tid; i < mend; i += NT) {
-    const uint32_t sg = S.segidx[i];
-    const uint32_t b = S.seg_off[sg] + rec_addr(tile[i]) - S.seg_lo[sg];
-    S.flags[T + (i - base)] = b;
-    atomicAdd(&S.bins[b], 1u);
-  }
-  __syncthreads();
-  cta_exclusive_scan(S.bins, nb, S.wtot);
-  for (uint32_t i = tid; i < m; i += NT) {
-    const uint32_t b = S.flags[T + i];
-    const uint32_t pos = atomicAdd(&S.bins[b], 1u);
-    S.sorted[pos] = tile[base + i];
-    S.sbin[pos] = (uint16_t)b;
-  }
-  __syncthreads();
-  m_out = m;
-  return kept;
-}
-
-__device__ __forceinline__ Summ run_summary(const Smem& S, uint32_t i, uint32_t end) {
-  Summ s = summ_empty();
-  for (uint32_t j = i; j < end; ++j) summ_add(s, S.sorted[j]);
-  return s;
-}
-
-// Race entries of sorted intervals, in (epoch, address) order, at out[race_out ...].
-__device__ void emit_races(const Smem& S, uint32_t m, uint4* out, uint32_t& race_out) {
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t i = tid; i < m; i += NT) {
-    uint32_t f = 0;
-    if (i == 0 || S.sbin[i] != S.sbin[i - 1]) {
-      // cheap pass: one thread only, or reads only / atomics only, cannot race
-      const uint32_t end = S.bins[S.sbin[i]];
-      uint32_t tmin = 0xFFFFu, tmax = 0, kinds = 0;
-      for (uint32_t j = i; j < end; ++j) {
-        const unsigned long long r = S.sorted[j];
-        const uint32_t t = rec_tid(r);
-        tmin = min(tmin, t);
-        tmax = max(tmax, t);
-        kinds |= 1u << rec_kind(r);
-      }
-      const bool maybe = tmin != tmax && ((kinds & (1u << K_W)) || kinds == ((1u << K_R) | (1u << K_A)));
-      if (maybe) {
-        uint32_t b, c;
-        f = summ_race(run_summary(S, i, end), b, c);
+    const uint32_t nval = d_cnt > cbase ? min(C::PER, d_cnt - cbase) : 0u;
+    const uint32_t ebefore = cbase ? rec_epoch(tile[min(cbase, d_cnt) - 1]) : 0u;
+    const uint32_t elast = rec_epoch(tile[d_cnt - 1]);
+    bool bad = false;
+    const uint32_t why = stage_pass<NC, C::PER>(
+        tab, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, lo, hi, nval, cbase, e0, ebefore, elast,
+        d_flags & 1u, d_flags & 2u, d_pos, d_cnt, d_n, gb, region, shw, race_out, ep, ivs, iv, par, tag, tagw, bad,
+        [&]() {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[buf]);   // the stage may be refilled
+        });
+    if (bad) {
+      atomicOr(A.error_flag, 2u);
+      if (why == 2) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[buf]);
       }
     }
-    S.flags[i] = f;
-    S.flags[T + i] = f;
   }
-  __syncthreads();
-  const uint32_t total = cta_exclusive_scan(S.flags, m, S.wtot);
-  for (uint32_t i = tid; i < m; i += NT) {
-    if (!S.flags[T + i]) continue;
-    const unsigned long long r = S.sorted[i];
-    uint32_t b = 0, c = 0;
-    summ_race(run_summary(S, i, S.bins[S.sbin[i]]), b, c);
-    out[race_out + S.flags[i]] = make_uint4(rec_epoch(r), rec_addr(r), b, c);
-  }
-  race_out += total;
-  __syncthreads();
 }
 
-// A chunk of an interval larger than a tile: fold run summaries into the per-CTA table.
-__device__ void fold_sorted(const Smem& S, uint32_t m, uint4* table) {
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t i = tid; i < m; i += NT) {
-    if (i != 0 && S.sbin[i] == S.sbin[i - 1]) continue;
-    Summ s = run_summary(S, i, S.bins[S.sbin[i]]);
-    const uint32_t a = rec_addr(S.sorted[i]);
-    const uint32_t bit = 1u << (a & 31);
-    if (atomicOr(&S.touched[a >> 5], bit) & bit) {
-      const uint4 o = table[a];
-      summ_merge(s, Summ{o.x, o.y, o.z, o.w});
+// ---------------------------------------------------------------- register-staged form
+// The same check without the shared-memory ring: every thread loads its records of a
+// stage straight from the log into registers (16-byte loads, coalesced across the warp),
+// the next stage's loads in flight while the current one is processed, and the CTA meets
+// only where an interval ends and between work items.  Nothing waits on a flag here, and
+// all the shared memory goes to the address table, so more CTAs fit on an SM.
+template <uint32_t NC>
+struct RegCfg {
+  static constexpr uint32_t NCW = NC / 32;
+  static constexpr uint32_t O_BM = NB * 4;
+  static constexpr uint32_t O_PRE = O_BM + NBW * 4;
+  static constexpr uint32_t O_MISC = O_PRE + NBW * 4;
+  static constexpr uint32_t MISC_WORDS = 8 + NCW + 1;
+  static constexpr uint32_t SMEM = O_MISC + MISC_WORDS * 4;
+};
+
+// Records [0, nval) of a stage from src (16-byte aligned); the pair that holds the last
+// record may read one record past it, which is still inside the block's region.
+template <uint32_t PER>
+__device__ __forceinline__ void load_records(const unsigned long long* src, uint32_t nval, uint32_t (&lo)[PER],
+                                             uint32_t (&hi)[PER]) {
+#pragma unroll
+  for (uint32_t j = 0; j < PER; j += 2) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (j < nval) v = *reinterpret_cast<const uint4*>(src + j);
+    lo[j] = v.x;
+    hi[j] = v.y;
+    lo[j + 1] = v.z;
+    hi[j + 1] = v.w;
+  }
+}
+
+template <uint32_t NC, uint32_t PER, uint32_t MINB>
+__global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
+  using C = RegCfg<NC>;
+  constexpr uint32_t T = NC * PER;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t* tab = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem + C::O_BM);
+  uint32_t* pre = reinterpret_cast<uint32_t*>(smem + C::O_PRE);
+  uint32_t* misc = reinterpret_cast<uint32_t*>(smem + C::O_MISC);
+  volatile uint32_t* s_racy = misc;              // [2] tag of the racy interval, by interval parity
+  volatile uint32_t* s_npos = misc + 2;          // [2] first record of the next interval in the stage
+  volatile uint32_t* s_nep = misc + 4;           // [2] its epoch
+  volatile uint32_t* s_item = misc + 6;          // [2] next work item, by item parity
+  uint32_t* wtot = misc + 8;
+  const uint32_t tid = threadIdx.x, cbase = tid * PER;
+  uint4* const stage_out = A.scratch + (size_t)blockIdx.x * kScratchWords;
+
+  for (uint32_t i = tid; i < NB; i += NC) tab[i] = 0;
+  if (tid < 8) misc[tid] = 0;
+  if (tid == 0) s_item[0] = A.item0 + atomicAdd(A.work_head, 1u);
+  __syncthreads();
+  uint32_t item = s_item[0], ipar = 0;
+  uint32_t iv = 1, par = 0, tag = 1, tagw = 1u << 14;
+  bool bad = false, stop = false;                // bad: this thread saw a corrupt record; stop: all did
+  while (item < A.item1) {
+    uint32_t next = 0;
+    if (tid == 0) next = A.item0 + atomicAdd(A.work_head, 1u);   // in flight during this item
+    uint32_t lo_l = A.li0, hi_l = A.li1 - 1;     // launch owning the item
+    while (lo_l < hi_l) {
+      const uint32_t mid = (lo_l + hi_l + 1) >> 1;
+      if (A.launches[mid].check_item <= item) lo_l = mid; else hi_l = mid - 1;
     }
-    table[a] = make_uint4(s.r, s.w, s.a, s.pc);
-  }
-  __threadfence_block();
-  __syncthreads();
-}
-
-// End of a large interval: races of every touched address, in address order.
-__device__ void finish_large(const Smem& S, uint32_t epoch, uint4* table, uint4* out, uint32_t& race_out) {
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t a = tid; a < NB; a += NT) {
-    uint32_t f = 0;
-    if (S.touched[a >> 5] & (1u << (a & 31))) {
-      const uint4 o = table[a];
-      uint32_t b, c;
-      f = summ_race(Summ{o.x, o.y, o.z, o.w}, b, c);
-    }
-    S.bins[a] = f;
-  }
-  __syncthreads();
-  const uint32_t total = cta_exclusive_scan(S.bins, NB, S.wtot);
-  for (uint32_t a = tid; a < NB; a += NT) {          // racy flags re-derived from the table
-    if (!(S.touched[a >> 5] & (1u << (a & 31)))) continue;
-    const uint4 o = table[a];
-    uint32_t b = 0, c = 0;
-    if (summ_race(Summ{o.x, o.y, o.z, o.w}, b, c)) out[race_out + S.bins[a]] = make_uint4(epoch, a, b, c);
-  }
-  __syncthreads();
-  race_out += total;
-  for (uint32_t i = tid; i < NB / 32 + 1; i += NT) S.touched[i] = 0;
-  __syncthreads();
-}
-
-// Interval starts of tile[0..cnt) (records are in interval order): at most MAXSEG are
-// kept; returns their number and sets cnt_eff to the end of the last kept interval.
-__device__ uint32_t find_intervals(const Smem& S, const unsigned long long* tile, uint32_t cnt, uint32_t& cnt_eff) {
-  constexpr uint32_t PER = (T + NT - 1) / NT;
-  const uint32_t i0 = threadIdx.x * PER;
-  uint32_t f = 0, c = 0;
-  for (uint32_t j = 0; j < PER; ++j) {
-    const uint32_t i = i0 + j;
-    const bool st = i < cnt && (i == 0 || rec_epoch(tile[i]) != rec_epoch(tile[i - 1]));
-    f |= (uint32_t)st << j;
-    c += st;
-  }
-  uint32_t total;
-  uint32_t o = cta_scan_value(c, S.wtot, &total);
-  for (uint32_t j = 0; j < PER; ++j) {
-    if (f >> j & 1u) {
-      if (o <= MAXSEG) S.seg_start[o] = i0 + j;
-      ++o;
-    }
-    if (i0 + j < cnt) S.segidx[i0 + j] = (uint16_t)min(o - 1, 0xFFFFu);   // interval of record i0 + j
-  }
-  __syncthreads();
-  const uint32_t nseg = min(total, MAXSEG);
-  if (total <= MAXSEG && threadIdx.x == 0) S.seg_start[nseg] = cnt;
-  __syncthreads();
-  cnt_eff = S.seg_start[nseg];
-  return nseg;
-}
-
-__global__ void __launch_bounds__(NT, kCheckCtasPerSm) k_check(CheckArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long mbar[2];
-  __shared__ uint32_t s_next;
-  Smem S;
-  unsigned char* p = smem;
-  S.tile[0] = reinterpret_cast<unsigned long long*>(p); p += (T + 2) * 8;
-  S.tile[1] = NBUF == 2 ? reinterpret_cast<unsigned long long*>(p) : S.tile[0];
-  p += (NBUF - 1) * (T + 2) * 8;
-  S.sorted = reinterpret_cast<unsigned long long*>(p); p += T * 8;
-  S.sbin = reinterpret_cast<uint16_t*>(p); p += T * 2;
-  S.bins = reinterpret_cast<uint32_t*>(p); p += NB * 4;
-  S.flags = reinterpret_cast<uint32_t*>(p); p += 2 * T * 4;
-  S.segidx = reinterpret_cast<uint16_t*>(p); p += T * 2;
-  S.seg_start = reinterpret_cast<uint32_t*>(p); p += (MAXSEG + 4) * 4;
-  S.seg_lo = reinterpret_cast<uint32_t*>(p); p += MAXSEG * 4;
-  S.seg_hi = reinterpret_cast<uint32_t*>(p); p += MAXSEG * 4;
-  S.seg_off = reinterpret_cast<uint32_t*>(p); p += MAXSEG * 4;
-  S.touched = reinterpret_cast<uint32_t*>(p); p += (NB / 32 + 1) * 4;
-  S.wtot = reinterpret_cast<uint32_t*>(p); p += 36 * 4;
-  S.misc = reinterpret_cast<uint32_t*>(p);
-  uint4* table = A.scratch + (size_t)blockIdx.x * kScratchWords;
-  const uint32_t tid = threadIdx.x;
-  uint32_t phases = 0;                           // bit b: mbarrier parity of buffer b
-  if (tid == 0) { mbar_init(&mbar[0]); mbar_init(&mbar[1]); }
-  for (uint32_t i = tid; i < NB / 32 + 1; i += NT) S.touched[i] = 0;
-
-  // next block with a non-empty log, and the start of its staging into buffer `buf`
-  auto claim = [&](uint32_t buf) {
-    if (tid == 0) {
-      uint32_t gb;
-      for (;;) {
-        gb = A.gb0 + atomicAdd(A.work_head, 1u);
-        if (gb >= A.gb1 || A.blocks[gb].n_log) break;
-      }
-      if (gb < A.gb1) {
-        uint32_t lo = 0, hi = A.nlaunches - 1;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (A.launches[mid].block_base <= gb) lo = mid; else hi = mid - 1;
+    const LaunchDev* L = A.launches + lo_l;
+    const uint32_t first = L->block_base + (item - L->check_item) * L->check_group;
+    const uint32_t nb = min(L->check_group, L->block_base + L->grid - first);
+    unsigned long long* const log0 = A.log + L->log_base;
+    const uint32_t cap = L->log_cap, base = L->block_base, shw = L->shw;
+    for (uint32_t b = 0; b < nb; ++b) {
+      const uint32_t gb = first + b;
+      const uint32_t n = A.blocks[gb].n_log;
+      if (!n) continue;
+      unsigned long long* const region = log0 + (unsigned long long)(gb - base) * cap;
+      uint32_t race_out = 0, ep = 0, ivs = 0;
+      uint32_t clo[PER], chi[PER];
+      load_records<PER>(region + cbase, n > cbase ? min(PER, n - cbase) : 0u, clo, chi);
+      for (uint32_t pos = 0; pos < n; pos += T) {
+        const uint32_t cnt = min(T, n - pos);
+        const uint32_t nval = cnt > cbase ? min(PER, cnt - cbase) : 0u;
+        const bool last = pos + T >= n;
+        uint32_t nlo[PER], nhi[PER];
+        if (!last) {                              // the next stage's loads go out first
+          const uint32_t rest = n - pos - T;
+          load_records<PER>(region + pos + T + cbase, rest > cbase ? min(PER, rest - cbase) : 0u, nlo, nhi);
         }
-        const LaunchDev* L = A.launches + lo;
-        const unsigned long long* region = A.log + L->log_base + (unsigned long long)(gb - L->block_base) * L->log_cap;
-        const uint32_t n = A.blocks[gb].n_log, cnt = min(T, n);
-        bulk_load(S.tile[buf], region, ((cnt + 1u) & ~1u) * 8u, &mbar[buf]);
-        S.misc[8] = lo;
+        const uint32_t e0 = rec_epoch(region[pos]);
+        const uint32_t elast = rec_epoch(region[pos + cnt - 1]);
+        const uint32_t ebefore = cbase ? rec_epoch(region[pos + min(cbase, cnt) - 1]) : 0u;
+        if (pos == 0) ep = e0;
+        const uint32_t how =
+            stage_pass<NC, PER>(tab, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, clo, chi, nval,
+                                cbase, e0, ebefore, elast, pos == 0, last, pos, cnt, n, gb, region, shw, race_out, ep,
+                                ivs, iv, par, tag, tagw, bad, []() {});
+        if (how == 2) {                           // (uniform) epochs out of order: give up
+          stop = true;
+          break;
+        }
+        if (!last) {
+#pragma unroll
+          for (uint32_t j = 0; j < PER; ++j) {
+            clo[j] = nlo[j];
+            chi[j] = nhi[j];
+          }
+        }
       }
-      s_next = gb;
+      if (stop) break;
     }
+    if (stop) break;
+    ipar ^= 1u;
+    if (tid == 0) s_item[ipar] = next;
     __syncthreads();
-    return s_next;
-  };
-
-  uint32_t cur = 0;
-  uint32_t gb = claim(cur);
-  while (gb < A.gb1) {
-    const LaunchDev* L = A.launches + S.misc[8];
-    unsigned long long* region = A.log + L->log_base + (unsigned long long)(gb - L->block_base) * L->log_cap;
-    uint4* out = reinterpret_cast<uint4*>(region);
-    const uint32_t n = A.blocks[gb].n_log;
-    uint32_t pos = 0, race_out = 0, large_epoch = 0, next_gb = A.gb1;
-    bool large = false, failed = false, prefetched = false;
-    while (pos < n) {
-      const bool ok = mbar_wait(&mbar[cur], (phases >> cur) & 1u, A.spin_limit);
-      phases ^= 1u << cur;
-      if (__syncthreads_or(!ok)) { failed = true; break; }
-      const uint32_t off = pos & 1u, cnt = min(T, n - pos);
-      const unsigned long long* tile = S.tile[cur] + off;
-      const bool last_tile = pos + cnt == n;
-      if (NBUF == 2 && last_tile && !prefetched) {   // stage the next block while this one is checked
-        next_gb = claim(cur ^ 1u);
-        prefetched = true;
-      }
-      uint32_t cnt_eff;
-      const uint32_t nseg = find_intervals(S, tile, cnt, cnt_eff);
-      // the last interval of a tile may continue in the next tile unless the block ends here
-      const bool tail_open = !last_tile && cnt_eff == cnt;
-      uint32_t sidx = 0, consumed = 0;
-      if (large && rec_epoch(tile[0]) != large_epoch) {   // it ended exactly at the last tile boundary
-        finish_large(S, large_epoch, table, out, race_out);
-        large = false;
-      }
-      if (large) {                               // the first interval continues the large one
-        uint32_t m;
-        sort_intervals(S, tile, 0, 1, m);
-        fold_sorted(S, m, table);
-        if (!(nseg == 1 && tail_open)) {
-          finish_large(S, large_epoch, table, out, race_out);
-          large = false;
-        }
-        sidx = 1;
-        consumed = S.seg_start[1];
-      }
-      const uint32_t ncomplete = tail_open ? nseg - 1 : nseg;
-      while (!large && sidx < ncomplete) {
-        uint32_t m;
-        const uint32_t kept = sort_intervals(S, tile, sidx, ncomplete - sidx, m);
-        emit_races(S, m, out, race_out);
-        sidx += kept;
-        consumed = S.seg_start[sidx];
-      }
-      if (!large && sidx == 0 && tail_open) {     // one interval fills the whole tile
-        large = true;
-        large_epoch = rec_epoch(tile[0]);
-        uint32_t m;
-        sort_intervals(S, tile, 0, 1, m);
-        fold_sorted(S, m, table);
-        consumed = cnt;
-      }
-      pos += consumed;
-      if (pos < n) {                             // restage the rest of this block
-        if (tid == 0) {
-          const uint32_t o2 = pos & 1u, c2 = min(T, n - pos);
-          bulk_load(S.tile[cur], region + (pos - o2), ((c2 + o2 + 1u) & ~1u) * 8u, &mbar[cur]);
-        }
-        __syncthreads();
-      }
-    }
-    if (tid == 0) {
-      A.blocks[gb].n_race = race_out;
-      if (failed) atomicOr(A.error_flag, 1u);
-    }
-    if (failed) break;
-    if (!prefetched) next_gb = claim(NBUF == 2 ? cur ^ 1u : 0u);
-    gb = next_gb;
-    if (NBUF == 2) cur ^= 1u;
-    __syncthreads();
+    item = s_item[ipar];
   }
+  if (bad || stop) atomicOr(A.error_flag, 2u);
+}
+
+template <uint32_t NC, uint32_t PER, uint32_t MINB>
+struct RegVariant {
+  static constexpr uint32_t smem() { return RegCfg<NC>::SMEM; }
+  static cudaError_t init(uint32_t optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_check_reg<NC, PER, MINB>);
+    if (e != cudaSuccess) return e;
+    if (smem() + fa.sharedSizeBytes > optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k_check_reg<NC, PER, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem());
+  }
+  static cudaError_t launch(const CheckArgs& a, uint32_t ctas, cudaStream_t s) {
+    k_check_reg<NC, PER, MINB><<<ctas, NC, smem(), s>>>(a);
+    return cudaGetLastError();
+  }
+};
+
+// Checker variants (consumer threads, records per stage, stages, CTAs per SM).
+template <uint32_t NC, uint32_t T, uint32_t NBUF, uint32_t MINB>
+struct CheckVariant {
+  static constexpr uint32_t smem() { return CheckCfg<NC, T, NBUF>::SMEM; }
+  static cudaError_t init(uint32_t optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_check<NC, T, NBUF, MINB>);
+    if (e != cudaSuccess) return e;
+    if (smem() + fa.sharedSizeBytes > optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k_check<NC, T, NBUF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+  }
+  static cudaError_t launch(const CheckArgs& a, uint32_t ctas, cudaStream_t s) {
+    k_check<NC, T, NBUF, MINB><<<ctas, NC + 32, smem(), s>>>(a);
+    return cudaGetLastError();
+  }
+};
+
+struct VariantEntry {
+  cudaError_t (*init)(uint32_t);
+  cudaError_t (*launch)(const CheckArgs&, uint32_t, cudaStream_t);
+  uint32_t ctas_per_sm;
+};
+template <class V, uint32_t MINB>
+constexpr VariantEntry entry() { return VariantEntry{&V::init, &V::launch, MINB}; }
+
+const VariantEntry kVariants[SR_CHECK_VARIANTS] = {
+    entry<CheckVariant<256, 1024, 3, 2>, 2>(),
+    entry<CheckVariant<128, 512, 4, 3>, 3>(),
+    entry<RegVariant<128, 4, 4>, 4>(),
+    entry<RegVariant<128, 8, 4>, 4>(),
+};
+constexpr uint32_t kDefaultVariant = 3;
+
+const VariantEntry& variant_entry(uint32_t v) {
+  return kVariants[(v >= 1 && v <= SR_CHECK_VARIANTS ? v : kDefaultVariant) - 1];
 }
 
 }  // namespace
 
-uint32_t check_smem_bytes() {
-  return NBUF * (T + 2) * 8 + T * 8 + T * 2 + NB * 4 + 2 * T * 4 + T * 2 + (MAXSEG + 4) * 4 + 3 * MAXSEG * 4 +
-         (NB / 32 + 1) * 4 + 36 * 4 + 64;
-}
+uint32_t check_default_variant() { return kDefaultVariant; }
+uint32_t check_ctas_per_sm(uint32_t variant) { return variant_entry(variant).ctas_per_sm; }
 
 cudaError_t init_check_attributes(uint32_t smem_optin) {
-  cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k_check);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_check, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(smem_optin - (uint32_t)fa.sharedSizeBytes));
+  for (const VariantEntry& v : kVariants) {
+    const cudaError_t e = v.init(smem_optin);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t init_kernel_attributes(uint32_t smem_optin) {
@@ -534,9 +813,8 @@ cudaError_t init_kernel_attributes(uint32_t smem_optin) {
   return e == cudaSuccess ? init_check_attributes(smem_optin) : e;
 }
 
-cudaError_t launch_check(const CheckArgs& a, uint32_t ctas, cudaStream_t s) {
-  k_check<<<ctas, NT, check_smem_bytes(), s>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_check(const CheckArgs& a, uint32_t variant, uint32_t ctas, cudaStream_t s) {
+  return variant_entry(variant).launch(a, ctas, s);
 }
 
 }  // namespace sr

@@ -22,7 +22,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SR_NOALLOC_SCRA
 constexpr int kMaxDevices = 64;
 constexpr uint32_t kMaxLaunches = 256;
 constexpr uint32_t kMaxWaves = 256;
-constexpr uint32_t kCheckCtas = 8;          // checker CTAs (each owns 256 KB of summary table)
+constexpr uint32_t kCheckCtas = 8;          // checker CTAs (each owns 256 KB of race-entry staging)
 
 void* g_scratch_addr[kMaxDevices];           // device address of the array, per device
 
@@ -82,7 +82,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   uint32_t acc[SR_MAX_CODE + 1], bar[SR_MAX_CODE + 1], spc[SR_MAX_CODE + 1], snx[SR_MAX_CODE + 1];
   const BoundScratch ws{colour, acc, bar, spc, snx};
   sr::LaunchDev L[kMaxLaunches];
-  uint64_t nblocks = 0;
+  uint64_t nblocks = 0, check_items = 0;
   for (uint32_t l = 0; l < prog->nlaunches; ++l) {
     const sr_launch& pl = prog->launches[l];
     const KernelBound k = bound_kernel(prog->code, ncode, prog->kernel_entry[pl.kernel], ws);
@@ -109,6 +109,9 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     const uint32_t nw = (pl.block_dim + 31) / 32;
     d.group_bytes = sr::group_layout(nw * 32, pl.shmem_words, ncode, rm.nrows).total;
     d.groups = 1;
+    d.check_group = sr::check_group_for(d.log_cap);
+    d.check_item = (uint32_t)check_items;
+    check_items += (pl.grid + d.check_group - 1) / d.check_group;
     if (d.ir_bytes + d.group_bytes + 1024 > (uint32_t)optin) return SR_E_RANGE;
     nblocks += pl.grid;
     L[l] = d;
@@ -191,17 +194,18 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     for (uint32_t li = w.li0; li < w.li1; ++li) NA_TRY(sr::launch_interp_plain(ra, li, L[li], 0, s));
     sr::CheckArgs ca{};
     ca.launches = ra.launches;
-    ca.nlaunches = nl;
-    ca.gb0 = w.gb0;
-    ca.gb1 = w.gb1;
+    ca.li0 = w.li0;
+    ca.li1 = w.li1;
+    ca.item0 = L[w.li0].check_item;
+    ca.item1 = w.li1 < nl ? L[w.li1].check_item : (uint32_t)check_items;
     ca.log = ra.log;
     ca.blocks = ra.blocks;
     ca.scratch = reinterpret_cast<uint4*>(base + o_table);
     ca.work_head = heads + wi;
     ca.error_flag = heads + kMaxWaves;
     ca.spin_limit = ra.spin_limit;
-    const uint32_t ctas = std::min<uint32_t>(cctas, w.gb1 - w.gb0);
-    if (ctas) NA_TRY(sr::launch_check(ca, ctas, s));
+    const uint32_t ctas = std::min<uint32_t>(cctas, ca.item1 - ca.item0);
+    if (ctas) NA_TRY(sr::launch_check(ca, 0, ctas, s));
     sr::CompactArgs ka{};
     ka.launches = ra.launches;
     ka.nlaunches = nl;

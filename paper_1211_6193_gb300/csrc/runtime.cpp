@@ -55,6 +55,7 @@ struct sr_batch {
   std::vector<uint2> items;
   std::vector<Wave> waves;
   uint32_t nblocks = 0;
+  uint32_t check_items = 0;                // race-check work items of all waves
   uint32_t max_key_bits = 1;
   uint32_t batched_smem = 0;
   uint64_t total_code = 0, total_arena = 0, log_records = 0;
@@ -191,9 +192,10 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
     if (o.check_races) {
       sr::CheckArgs ca{};
       ca.launches = ra.launches;
-      ca.nlaunches = ra.nlaunches;
-      ca.gb0 = w.gb0;
-      ca.gb1 = w.gb1;
+      ca.li0 = w.li0;
+      ca.li1 = w.li1;
+      ca.item0 = b->launches[w.li0].check_item;
+      ca.item1 = w.li1 < b->launches.size() ? b->launches[w.li1].check_item : b->check_items;
       ca.log = ra.log;
       ca.blocks = ra.blocks;
       ca.scratch = (uint4*)b->scratch.p;
@@ -201,8 +203,8 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       ca.error_flag = (uint32_t*)b->err_flag.p;
       ca.spin_limit = o.spin_limit;
       CUDA_TRY(c, cudaMemsetAsync(ca.work_head, 0, 4, s));
-      const uint32_t ctas = std::min<uint32_t>(b->check_ctas, w.gb1 - w.gb0);
-      if (ctas) CUDA_TRY(c, sr::launch_check(ca, ctas, s));
+      const uint32_t ctas = std::min<uint32_t>(b->check_ctas, ca.item1 - ca.item0);
+      if (ctas) CUDA_TRY(c, sr::launch_check(ca, o.check_variant, ctas, s));
     }
     mark();
     sr::CompactArgs ka{};
@@ -243,9 +245,10 @@ int sr_create(sr_ctx** out, const sr_opts* opts) {
   if (o.loop_log_records == 0) o.loop_log_records = 65536;
   if (o.ctas_per_sm == 0) o.ctas_per_sm = 1;
   if (o.spin_limit == 0) o.spin_limit = 1u << 26;
-  if (o.round_budget > sr::kMaxBudget || o.mode > SR_MODE_BATCHED || o.interp_variant > 2) {
+  if (o.round_budget > sr::kMaxBudget || o.mode > SR_MODE_BATCHED || o.interp_variant > 2 ||
+      o.check_variant > SR_CHECK_VARIANTS) {
     delete c;
-    return fail(nullptr, SR_E_INVAL, "round_budget above 2^26 or unknown mode");
+    return fail(nullptr, SR_E_INVAL, "round_budget above 2^26, or unknown mode or kernel variant");
   }
   if (o.allocator && o.allocator->alloc && o.allocator->release) {
     c->alloc = *o.allocator;
@@ -296,7 +299,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   b->arena_off.resize(n);
   b->arena_words.resize(n);
   uint64_t arena_total = 0;
-  uint64_t nblocks = 0;
+  uint64_t nblocks = 0, check_items = 0;
   const uint32_t smem_budget = (uint32_t)std::min<size_t>(c->smem_optin ? c->smem_optin : 227 * 1024, 227 * 1024) /
                                    std::max(1u, o.ctas_per_sm) -
                                1024;
@@ -354,9 +357,12 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       uint32_t g = std::min<uint32_t>(32 / nw, (smem_budget - d.ir_bytes) / d.group_bytes);
       if (nw >= 2) g = std::min<uint32_t>(g, 15);
       d.groups = std::max<uint32_t>(1, std::min<uint32_t>(g, L.grid));
+      d.check_group = sr::check_group_for(d.log_cap);
+      d.check_item = (uint32_t)check_items;
+      check_items += (L.grid + d.check_group - 1) / d.check_group;
       b->max_key_bits = std::max(b->max_key_bits, d.key_bits);
       nblocks += L.grid;
-      if (nblocks >= (1ull << 31)) {
+      if (nblocks >= (1ull << 31) || check_items >= (1ull << 31)) {
         delete b;
         return fail(c, SR_E_INVAL, "too many simulated blocks in one batch");
       }
@@ -364,6 +370,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
     }
   }
   b->nblocks = (uint32_t)nblocks;
+  b->check_items = (uint32_t)check_items;
   b->total_code = code.size();
   b->total_arena = arena_total;
 
@@ -411,7 +418,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       }
     w.item1 = (uint32_t)b->items.size();
   }
-  b->check_ctas = (uint32_t)c->sms * sr::kCheckCtasPerSm;
+  b->check_ctas = (uint32_t)c->sms * sr::check_ctas_per_sm(o.check_variant);
 
   // ---- device buffers
   int rc = SR_OK;

@@ -45,6 +45,7 @@ struct LaunchDev {
   uint64_t arena_off, arena_words;       // word offset of the program's working arena
   uint32_t groups, group_bytes;          // batched mode: blocks per CTA, smem per block
   uint32_t ir_bytes, nrows;              // smem bytes of the staged code; register rows (zero row last)
+  uint32_t check_group, check_item;      // race check: blocks per work item, index of the first item
 };
 
 // Per simulated block, written by the interpreter (n_log, n_misc, flags) and the checker (n_race).
@@ -106,23 +107,29 @@ uint32_t interp_plain_smem(const LaunchDev& L);
 
 struct CheckArgs {
   const LaunchDev* launches;
-  uint32_t nlaunches;
-  uint32_t gb0, gb1;            // block range of the wave
+  uint32_t li0, li1;            // launch range of the wave
+  uint32_t item0, item1;        // work items of the wave (launch li owns items from check_item on)
   unsigned long long* log;
   BlockRes* blocks;
-  uint4* scratch;               // per checker CTA: 1 << 14 summaries (large intervals)
+  uint4* scratch;               // per checker CTA: kScratchWords race entries (intervals with many races)
   uint32_t* work_head;
   uint32_t* error_flag;
   uint32_t spin_limit;
 };
-cudaError_t launch_check(const CheckArgs& a, uint32_t ctas, cudaStream_t s);
-uint32_t check_smem_bytes();
-constexpr uint32_t kCheckThreads = 512;
-constexpr uint32_t kCheckTile = 2048;          // records per staged tile
-constexpr uint32_t kCheckBuffers = 1;          // staged tiles per CTA (2 = prefetch the next block)
-constexpr uint32_t kCheckCtasPerSm = 2;
-constexpr uint32_t kCheckBins = 12288;         // counting-sort bins (>= the largest shared array)
-constexpr uint32_t kScratchWords = 1u << 14;   // summaries per CTA in the large-interval path
+// race-check kernel shapes (variant 1..SR_CHECK_VARIANTS; 0 = default)
+uint32_t check_default_variant();
+uint32_t check_ctas_per_sm(uint32_t variant);
+cudaError_t launch_check(const CheckArgs& a, uint32_t variant, uint32_t ctas, cudaStream_t s);
+constexpr uint32_t kCheckBins = 12288;         // address table entries (>= the largest shared array)
+constexpr uint32_t kScratchWords = 1u << 14;   // race entries per CTA staged in global memory
+constexpr uint32_t kCheckItemRecords = 8192;   // log records a check work item aims at
+constexpr uint32_t kCheckMaxGroup = 32;        // blocks per check work item at most
+
+// blocks per check work item for a launch whose blocks log at most `log_cap` records
+__host__ __device__ inline uint32_t check_group_for(uint32_t log_cap) {
+  const uint32_t g = (kCheckItemRecords + log_cap - 1) / (log_cap ? log_cap : 1);
+  return g < 1 ? 1 : (g > kCheckMaxGroup ? kCheckMaxGroup : g);
+}
 
 struct CompactArgs {
   const LaunchDev* launches;

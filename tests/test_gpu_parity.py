@@ -179,6 +179,33 @@ def test_intervals_larger_than_a_staged_tile(B, mode):
     assert_parity(B, _large_interval_programs(), mode)
 
 
+def _many_racy_addresses_programs():
+    """One interval with more racy words than one round of exact summaries holds (3072):
+    thread t and t ^ 1 both store to words t + 1024 j (j < k), a write-write race per
+    word; k = 8 gives 8192 racy words, k = 3 exactly 3072, and a read of each word by a
+    third thread adds the write-read class."""
+    out = []
+    for k, extra_read in ((8, False), (3, False), (12, True)):
+        a = ir.Asm()
+        a.s2r(ir.r2, ir.TID).xor(ir.r3, ir.r2, 1)
+        for j in range(k):
+            a.sts(ir.r2, ir.r2, 1024 * j).sts(ir.r3, ir.r2, 1024 * j)
+        if extra_read:
+            a.xor(ir.r4, ir.r2, 2)
+            for j in range(k):
+                a.lds(ir.r5, ir.r4, 1024 * j).add(ir.r6, ir.r6, ir.r5)
+        a.bar().stg(ir.r2, ir.r6).exit()
+        out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 2, 1024, 1024 * k, ())], np.zeros(1024, np.int32)))
+    return out
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_more_racy_words_than_one_summary_round(B, mode):
+    got, _ = assert_parity(B, _many_racy_addresses_programs(), mode)
+    races = [r for r in got.report_tuples() if r[0] == oracle.RACE]
+    assert len(races) == 2 * (8 + 3 + 12) * 1024
+
+
 def test_race_check_disabled_keeps_memory_and_barrier_reports(B):
     progs = families.batch(n_programs=24, seed=8, max_grid=4, bug_rate=0.6)
     want = oracle.run(progs, check_races=False)
