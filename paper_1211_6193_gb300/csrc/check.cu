@@ -99,6 +99,10 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Pull [p, p + bytes) into L2 (no destination; p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void mbar_init_count(unsigned long long* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -401,11 +405,12 @@ __device__ __forceinline__ uint32_t stage_pass(
     }
     uint32_t m = (1u << nval) - 1u;               // this thread's records of interval `ep`
     if (!(e0 == ep && elast == ep)) {             // the stage holds more than interval `ep`
+      m = 0;
 #pragma unroll
       for (uint32_t j = 0; j < PER; ++j) {
         const uint32_t e = hi[j] >> 6;
         const uint32_t pe = j ? hi[j ? j - 1 : 0] >> 6 : ebefore;
-        if (e != ep) m &= ~(1u << j);
+        if (j < nval && e == ep) m |= 1u << j;
         // the record whose predecessor is older notes where the next interval starts
         if (j < nval && e > ep && pe <= ep && cbase + j > 0) {
           s_npos[par] = cbase + j;
@@ -413,7 +418,7 @@ __device__ __forceinline__ uint32_t stage_pass(
         }
       }
     }
-    table_add_set<PER>(tab, lo, hi, m, tagw, tag, s_racy + par, bad);
+    if (__any_sync(FULL, m != 0)) table_add_set<PER>(tab, lo, hi, m, tagw, tag, s_racy + par, bad);
     if (elast != ep) {
       why = 2;
       continue;
@@ -635,7 +640,9 @@ struct RegCfg {
   static constexpr uint32_t NCW = NC / 32;
   static constexpr uint32_t O_BM = NB * 4;
   static constexpr uint32_t O_PRE = O_BM + NBW * 4;
-  static constexpr uint32_t O_MISC = O_PRE + NBW * 4;
+  static constexpr uint32_t O_ITEM = O_PRE + NBW * 4;          // [2] x {item, launch, n[32]}
+  static constexpr uint32_t ITEM_WORDS = 2 + kCheckMaxGroup;
+  static constexpr uint32_t O_MISC = O_ITEM + 2 * ITEM_WORDS * 4;
   static constexpr uint32_t MISC_WORDS = 8 + NCW + 1;
   static constexpr uint32_t SMEM = O_MISC + MISC_WORDS * 4;
 };
@@ -656,6 +663,40 @@ __device__ __forceinline__ void load_records(const unsigned long long* src, uint
   }
 }
 
+constexpr uint32_t kAheadStages = 8;             // L2 prefetch distance inside a block
+
+// Warp 0: resolve work item `item` into sh = {item, launch, n_log of each of its blocks}
+// and pull the first stages of every block into L2.
+__device__ __forceinline__ void item_setup(const CheckArgs& A, uint32_t item, volatile uint32_t* sh,
+                                           uint32_t ahead_records) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t li = 0, nb = 0, first = 0;
+  if (item < A.item1) {
+    uint32_t lo = A.li0, hi = A.li1 - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (A.launches[mid].check_item <= item) lo = mid; else hi = mid - 1;
+    }
+    const LaunchDev* L = A.launches + lo;
+    li = lo;
+    first = L->block_base + (item - L->check_item) * L->check_group;
+    nb = min(L->check_group, L->block_base + L->grid - first);
+    if (lane < nb) {
+      const uint32_t n = A.blocks[first + lane].n_log;
+      sh[2 + lane] = n;
+      if (n) {
+        const unsigned long long* region =
+            A.log + L->log_base + (unsigned long long)(first + lane - L->block_base) * L->log_cap;
+        prefetch_l2(region, ((min(n, ahead_records) + 1u) & ~1u) * 8u);
+      }
+    }
+  }
+  if (lane == 0) {
+    sh[0] = item;
+    sh[1] = li;
+  }
+}
+
 template <uint32_t NC, uint32_t PER, uint32_t MINB>
 __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
   using C = RegCfg<NC>;
@@ -664,55 +705,69 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
   uint32_t* tab = reinterpret_cast<uint32_t*>(smem);
   uint32_t* bm = reinterpret_cast<uint32_t*>(smem + C::O_BM);
   uint32_t* pre = reinterpret_cast<uint32_t*>(smem + C::O_PRE);
+  volatile uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + C::O_ITEM);
   uint32_t* misc = reinterpret_cast<uint32_t*>(smem + C::O_MISC);
   volatile uint32_t* s_racy = misc;              // [2] tag of the racy interval, by interval parity
   volatile uint32_t* s_npos = misc + 2;          // [2] first record of the next interval in the stage
   volatile uint32_t* s_nep = misc + 4;           // [2] its epoch
-  volatile uint32_t* s_item = misc + 6;          // [2] next work item, by item parity
   uint32_t* wtot = misc + 8;
   const uint32_t tid = threadIdx.x, cbase = tid * PER;
   uint4* const stage_out = A.scratch + (size_t)blockIdx.x * kScratchWords;
 
   for (uint32_t i = tid; i < NB; i += NC) tab[i] = 0;
   if (tid < 8) misc[tid] = 0;
-  if (tid == 0) s_item[0] = A.item0 + atomicAdd(A.work_head, 1u);
+  if (tid < 32) {
+    uint32_t item = 0;
+    if (tid == 0) item = A.item0 + atomicAdd(A.work_head, 1u);
+    item_setup(A, __shfl_sync(FULL, item, 0), s_items, kAheadStages * T);
+  }
   __syncthreads();
-  uint32_t item = s_item[0], ipar = 0;
+  uint32_t ipar = 0;
   uint32_t iv = 1, par = 0, tag = 1, tagw = 1u << 14;
   bool bad = false, stop = false;                // bad: this thread saw a corrupt record; stop: all did
-  while (item < A.item1) {
+  for (;;) {
+    volatile uint32_t* sh = s_items + ipar * C::ITEM_WORDS;
+    const uint32_t item = sh[0];
+    if (item >= A.item1) break;
     uint32_t next = 0;
     if (tid == 0) next = A.item0 + atomicAdd(A.work_head, 1u);   // in flight during this item
-    uint32_t lo_l = A.li0, hi_l = A.li1 - 1;     // launch owning the item
-    while (lo_l < hi_l) {
-      const uint32_t mid = (lo_l + hi_l + 1) >> 1;
-      if (A.launches[mid].check_item <= item) lo_l = mid; else hi_l = mid - 1;
-    }
-    const LaunchDev* L = A.launches + lo_l;
+    const LaunchDev* L = A.launches + sh[1];
     const uint32_t first = L->block_base + (item - L->check_item) * L->check_group;
     const uint32_t nb = min(L->check_group, L->block_base + L->grid - first);
     unsigned long long* const log0 = A.log + L->log_base;
     const uint32_t cap = L->log_cap, base = L->block_base, shw = L->shw;
     for (uint32_t b = 0; b < nb; ++b) {
       const uint32_t gb = first + b;
-      const uint32_t n = A.blocks[gb].n_log;
+      const uint32_t n = sh[2 + b];
       if (!n) continue;
       unsigned long long* const region = log0 + (unsigned long long)(gb - base) * cap;
       uint32_t race_out = 0, ep = 0, ivs = 0;
-      uint32_t clo[PER], chi[PER];
-      load_records<PER>(region + cbase, n > cbase ? min(PER, n - cbase) : 0u, clo, chi);
+      // a stage: this thread's records plus three epochs (the stage's first and last
+      // records, and the record before this thread's first), loaded one stage ahead
+      const uint32_t* const hw = reinterpret_cast<const uint32_t*>(region) + 1;   // high word of record i: hw[2i]
+      uint32_t clo[PER], chi[PER], ce0, celast, cebefore;
+      {
+        const uint32_t cnt = min(T, n);
+        load_records<PER>(region + cbase, cnt > cbase ? min(PER, cnt - cbase) : 0u, clo, chi);
+        ce0 = hw[0];
+        celast = hw[2u * (cnt - 1u)];
+        cebefore = cbase ? hw[2u * (min(cbase, cnt) - 1u)] : 0u;
+      }
       for (uint32_t pos = 0; pos < n; pos += T) {
         const uint32_t cnt = min(T, n - pos);
         const uint32_t nval = cnt > cbase ? min(PER, cnt - cbase) : 0u;
         const bool last = pos + T >= n;
-        uint32_t nlo[PER], nhi[PER];
+        uint32_t nlo[PER], nhi[PER], ne0 = 0, nelast = 0, nebefore = 0;
         if (!last) {                              // the next stage's loads go out first
-          const uint32_t rest = n - pos - T;
-          load_records<PER>(region + pos + T + cbase, rest > cbase ? min(PER, rest - cbase) : 0u, nlo, nhi);
+          const uint32_t npos = pos + T, ncnt = min(T, n - npos);
+          load_records<PER>(region + npos + cbase, ncnt > cbase ? min(PER, ncnt - cbase) : 0u, nlo, nhi);
+          ne0 = hw[2u * npos];
+          nelast = hw[2u * (npos + ncnt - 1u)];
+          nebefore = cbase ? hw[2u * (npos + min(cbase, ncnt) - 1u)] : 0u;
+          const uint32_t far = pos + kAheadStages * T;
+          if (tid == 0 && far < n) prefetch_l2(region + far, ((min(T, n - far) + 1u) & ~1u) * 8u);
         }
-        const uint32_t e0 = rec_epoch(region[pos]);
-        const uint32_t elast = rec_epoch(region[pos + cnt - 1]);
-        const uint32_t ebefore = cbase ? rec_epoch(region[pos + min(cbase, cnt) - 1]) : 0u;
+        const uint32_t e0 = ce0 >> 6, elast = celast >> 6, ebefore = cebefore >> 6;
         if (pos == 0) ep = e0;
         const uint32_t how =
             stage_pass<NC, PER>(tab, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, clo, chi, nval,
@@ -728,15 +783,19 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
             clo[j] = nlo[j];
             chi[j] = nhi[j];
           }
+          ce0 = ne0;
+          celast = nelast;
+          cebefore = nebefore;
         }
       }
       if (stop) break;
     }
     if (stop) break;
-    ipar ^= 1u;
-    if (tid == 0) s_item[ipar] = next;
+    // warp 0 prepares the next item (its blocks' records start moving into L2) while
+    // the other warps finish this one
+    if (tid < 32) item_setup(A, __shfl_sync(FULL, next, 0), s_items + (ipar ^ 1u) * C::ITEM_WORDS, kAheadStages * T);
     __syncthreads();
-    item = s_item[ipar];
+    ipar ^= 1u;
   }
   if (bad || stop) atomicOr(A.error_flag, 2u);
 }
