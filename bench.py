@@ -13,6 +13,8 @@ every barrier interval, barrier checks, canonical report ordering.
 
 Other workloads (--workload): ``batched`` = 4096 seed-generated programs (batched and
 plain paths both timed), ``stencil2d`` = the 8192^2, 16-launch log-heavy stencil.
+Kernel shapes (interpreter CTAs per SM or register budget, race-check variant) are picked
+by the autotuner before the timed region unless a shape flag or --no-tune fixes them.
 --impl reference times the CPU oracle on a bounded block sample of the same workload.
 Under torchrun each rank runs its own copy of the workload (seed + rank): weak scaling.
 """
@@ -55,6 +57,10 @@ def parse():
     ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
     ap.add_argument("--interp-variant", type=int, default=0, choices=[0, 1, 2],
                     help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
+    ap.add_argument("--check-variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="race-check kernel shape (0 = default); setting a shape flag skips the autotuner")
+    ap.add_argument("--no-tune", action="store_true", help="library default shapes instead of the autotuner")
+    ap.add_argument("--tune-cache", default=None, help="JSON file caching tuned shapes per workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-blocks", type=int, default=0, help="oracle sample (blocks per launch; 0 = auto)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving trace length (s)")
@@ -193,9 +199,14 @@ def traffic_per_launch(kernel: str, src: str, blocks: int):
     return t["dram_bytes_per_block"] * blocks
 
 
-def measure(binding, torch, progs, mode, variant, steps, warmup, flush, stream):
+def check_kernel(variant: int) -> str:
+    """Kernel name of a race-check shape (variants 1-2: TMA ring, 3-4: register-staged)."""
+    return "k_check" if variant in (1, 2) else "k_check_reg"
+
+
+def measure(binding, torch, progs, opts, steps, warmup, flush, stream):
     """Time `steps` runs of run_and_check on resident programs (L2 flushed between steps)."""
-    ctx = binding.Context(mode=mode, profile=True, interp_variant=variant, use_graph=False)
+    ctx = binding.Context(profile=True, use_graph=False, **opts)
     batch = ctx.load_programs(progs)
     for _ in range(max(3, warmup)):
         batch.run_and_check()
@@ -252,7 +263,7 @@ def run_serving(args):
 def run_native(args):
     import torch
 
-    from paper_1211_6193_gb300 import binding
+    from paper_1211_6193_gb300 import autotune, binding
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
@@ -276,11 +287,21 @@ def run_native(args):
             torch.cuda.synchronize()
 
     mode = "batched" if args.workload == "batched" else args.mode
+
+    def shapes(m):
+        """Kernel shapes for mode m: fixed by the flags, else picked by the autotuner (untimed)."""
+        if args.interp_variant or args.check_variant or args.no_tune:
+            o = {"mode": m, "interp_variant": args.interp_variant, "check_variant": args.check_variant}
+            return o, "flags"
+        sample = progs[::8] if len(progs) >= 64 else progs     # a strided eighth keeps the mix
+        t = autotune.tune(sample, m, cache_path=args.tune_cache)
+        return dict(t.options), ("cache" if t.cached else {"interp_ms": t.interp_ms, "check_ms": t.check_ms})
+
+    opts, tuning = shapes(mode)
     with ClockSampler(local) as clocks:
         barrier()
         t_wall = time.perf_counter()
-        st, n_reports, per_step, stage = measure(binding, torch, progs, mode, args.interp_variant, args.steps,
-                                                 args.warmup, flush, stream)
+        st, n_reports, per_step, stage = measure(binding, torch, progs, opts, args.steps, args.warmup, flush, stream)
         barrier()
         t_wall = time.perf_counter() - t_wall
     clk = clocks.summary()
@@ -294,11 +315,11 @@ def run_native(args):
 
     plain = None
     if args.workload == "batched":     # the same programs through one kernel launch per (program, launch)
-        pst, _, pper, pstage = measure(binding, torch, progs, "plain", args.interp_variant, max(2, args.steps // 2),
-                                       1, flush, stream)
+        popts, _ = shapes("plain")
+        pst, _, pper, pstage = measure(binding, torch, progs, popts, max(2, args.steps // 2), 1, flush, stream)
         pms = sum(pper) / len(pper)
         plain = {"value": pst.shared_accesses / (pms / 1e3), "ms_per_step": pms, "stage_ms": pstage,
-                 "batched_speedup": pms / (dev_ms / args.steps)}
+                 "batched_speedup": pms / (dev_ms / args.steps), "shapes": popts}
 
     # ---- rooflines: the interpreter (dominant) is bound by integer issue, the checker by HBM
     int_peak = 152 * 128 * sm_max * 1e6            # int32 lane-ops/s: 152 SMs x 128 lanes x max clock
@@ -312,10 +333,12 @@ def run_native(args):
                 "traffic": traffic_per_launch("k_interp_plain", isha, nblocks) if mode == "plain" else None,
                 "peak_source": "derived: 152 SMs x 128 int32 lanes x sm_max_mhz (MEASURED_PEAKS.json)",
                 "stage_ms": stage,
-                "checker": {"bound": "hbm", "kernel": "k_check", "achieved": check_gbs, "peak": hbm_peak,
+                "checker": {"bound": "hbm", "kernel": check_kernel(opts.get("check_variant", 0)),
+                            "achieved": check_gbs, "peak": hbm_peak,
                             "unit": "GB/s", "frac": check_gbs / hbm_peak, "peak_source": peak_src,
                             "algorithmic_bytes": "8 B read per logged access + 16 B per race entry",
-                            "traffic": traffic_per_launch("k_check", csha, nblocks)}}
+                            "traffic": traffic_per_launch(check_kernel(opts.get("check_variant", 0)), csha,
+                                                          nblocks)}}
 
     # ---- end to end through the C ABI from pinned host buffers (single-program workloads)
     e2e = None
@@ -328,7 +351,7 @@ def run_native(args):
         h2d = prog.global_init.nbytes + prog.code.nbytes
         d2h = out_arena.nbytes + n_reports * 32
         times = []
-        ctx_e2e = binding.Context(mode=mode, report_cap=max(16, n_reports), interp_variant=args.interp_variant)
+        ctx_e2e = binding.Context(report_cap=max(16, n_reports), **opts)
         for i in range(1 + min(args.steps, 5)):
             barrier()
             t0 = time.perf_counter()
@@ -354,7 +377,8 @@ def run_native(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": workload_label(args), "mode": mode, "blocks": nblocks,
+            "config": {"workload": workload_label(args), "mode": mode, "shapes": opts, "tuning": tuning,
+                       "blocks": nblocks,
                        "programs": len(progs), "parallelism": f"{world} independent replicas" if world > 1
                        else "single GPU", "l2": "flushed between timed steps (256 MB write); logs exceed L2"},
             "sim_thread_instrs_per_s": thread_instr_rate, "shared_accesses_per_step": st.shared_accesses,

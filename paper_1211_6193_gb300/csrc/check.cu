@@ -846,7 +846,7 @@ const VariantEntry kVariants[SR_CHECK_VARIANTS] = {
     entry<CheckVariant<256, 1024, 3, 2>, 2>(),
     entry<CheckVariant<128, 512, 4, 3>, 3>(),
     entry<RegVariant<128, 4, 4>, 4>(),
-    entry<RegVariant<128, 8, 4>, 4>(),
+    entry<RegVariant<256, 4, 2>, 2>(),
 };
 constexpr uint32_t kDefaultVariant = 3;
 
