@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--tune-cache", default=None, help="JSON file caching tuned shapes per workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-blocks", type=int, default=0, help="oracle sample (blocks per launch; 0 = auto)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving trace length (s)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving trace length (s)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving arrival rate (jobs/s)")
     ap.add_argument("--blocks", type=int, default=16384,
                     help="blocks of the reduction (default: the full workload; smaller only for profiling)")
     return ap.parse_args()
@@ -237,7 +238,7 @@ def run_serving(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     pool = serving.job_pool(512, seed=5 + rank)
-    arrivals = serving.poisson_trace(2000.0, args.serve_seconds, seed=5 + rank)
+    arrivals = serving.poisson_trace(args.serve_rate, args.serve_seconds, seed=5 + rank)
     jobs = [serving.Job(k, pool[k % len(pool)], t) for k, t in enumerate(arrivals)]
     warm = serving.Server(log_budget_bytes=120 << 30, max_inflight=4)
     warm.serve([serving.Job(k, pool[k], 0.0) for k in range(16)])      # load kernels, warm the allocator
@@ -253,10 +254,13 @@ def run_serving(args):
             "metric": METRIC, "value": st.accesses_per_s * world, "unit": UNIT, "n_gpus": world, "steps": 1,
             "warmup": 1, "ms_per_step": st.seconds * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["serving"], "trace_seconds": args.serve_seconds, "jobs": st.jobs},
+            "config": {"workload": WORKLOADS["serving"].replace("2000 jobs/s", f"{args.serve_rate:g} jobs/s"),
+                       "trace_seconds": args.serve_seconds, "jobs": st.jobs},
             "serving": {"p50_latency_ms": st.p50_ms, "p99_latency_ms": st.p99_ms, "jobs_per_s": st.jobs_per_s,
                         "batches": st.batches, "mean_batch_jobs": st.mean_batch_jobs,
-                        "max_inflight_batches": st.max_inflight_seen, "peak_log_bytes": st.peak_log_bytes},
+                        "max_inflight_batches": st.max_inflight_seen, "peak_log_bytes": st.peak_log_bytes,
+                        "host_load_s": st.host_load_s, "host_fetch_s": st.host_fetch_s,
+                        "mean_batch_gpu_ms": st.mean_batch_gpu_ms},
             "clocks": clocks.summary()}), flush=True)
 
 

@@ -139,6 +139,23 @@ cudaEvent_t next_event(sr_batch* b) {
 }
 
 // Enqueue the whole pipeline for one run on stream s.
+sr::CompactArgs compact_args(sr_batch* b, const Wave& w) {
+  sr::CompactArgs ka{};
+  ka.launches = (const LaunchDev*)b->launches_d.p;
+  ka.nlaunches = (uint32_t)b->launches.size();
+  ka.gb0 = w.gb0;
+  ka.gb1 = w.gb1;
+  ka.total = (unsigned long long*)b->total.p;
+  ka.log = (const unsigned long long*)b->log.p;
+  ka.blocks = (const sr::BlockRes*)b->blocks.p;
+  ka.offsets = (unsigned long long*)b->offsets.p;
+  ka.partials = (unsigned long long*)b->partials.p;
+  ka.out = (sr_report*)b->out.p;
+  ka.out_cap = b->out_cap;
+  ka.counters = (sr::Counters*)b->counters.p;
+  return ka;
+}
+
 int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
   const sr_opts& o = c->opts;
   b->nevents_used = 0;
@@ -207,19 +224,7 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       if (ctas) CUDA_TRY(c, sr::launch_check(ca, o.check_variant, ctas, s));
     }
     mark();
-    sr::CompactArgs ka{};
-    ka.launches = ra.launches;
-    ka.nlaunches = ra.nlaunches;
-    ka.gb0 = w.gb0;
-    ka.gb1 = w.gb1;
-    ka.total = (unsigned long long*)b->total.p;
-    ka.log = ra.log;
-    ka.blocks = ra.blocks;
-    ka.offsets = (unsigned long long*)b->offsets.p;
-    ka.partials = (unsigned long long*)b->partials.p;
-    ka.out = (sr_report*)b->out.p;
-    ka.out_cap = b->out_cap;
-    ka.counters = ra.counters;
+    const sr::CompactArgs ka = compact_args(b, w);
     CUDA_TRY(c, sr::launch_compact_scan(ka, s));
     CUDA_TRY(c, sr::launch_compact_emit(ka, s));
     mark();
@@ -515,7 +520,10 @@ int fetch_reports(sr_ctx* c, sr_batch* b, sr_report* dst, uint64_t cap, uint64_t
   CUDA_TRY(c, cudaMemcpyAsync(&total, b->total.p, 8, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(c, cudaStreamSynchronize(s));
   if (total > b->out_cap) {
-    // the report buffer was too small: grow it and run again (runs are deterministic)
+    // The report buffer was too small: grow it.  With one wave, that wave's logs, block
+    // results and report offsets are all still on the device, so only the emission runs
+    // again; with several, later waves reused the log pool and the whole run is repeated
+    // (runs are deterministic).
     dev_free(c, b->out, s);
     b->out_cap = total + total / 8 + 1024;
     int rc = alloc_buf(c, b->out, b->out_cap * sizeof(sr_report), s, "reports");
@@ -524,10 +532,14 @@ int fetch_reports(sr_ctx* c, sr_batch* b, sr_report* dst, uint64_t cap, uint64_t
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
     }
-    rc = run_and_check(c, b, s);
-    if (rc) return rc;
-    CUDA_TRY(c, cudaMemcpyAsync(&total, b->total.p, 8, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (b->waves.size() == 1) {
+      CUDA_TRY(c, sr::launch_compact_emit(compact_args(b, b->waves[0]), s));
+    } else {
+      rc = run_and_check(c, b, s);
+      if (rc) return rc;
+      CUDA_TRY(c, cudaMemcpyAsync(&total, b->total.p, 8, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(c, cudaStreamSynchronize(s));
+    }
   }
   uint32_t err = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&err, b->err_flag.p, 4, cudaMemcpyDeviceToHost, s));

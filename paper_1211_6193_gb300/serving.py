@@ -101,7 +101,7 @@ class Job:
 
 @dataclass
 class JobResult:
-    reports: np.ndarray     # REPORT_DTYPE, prog renumbered to 0
+    reports: np.ndarray     # REPORT_DTYPE; `prog` is the job's position in its micro-batch
     arena: np.ndarray
     status: int
     arrival: float
@@ -125,6 +125,9 @@ class ServeStats:
     max_inflight_seen: int
     mean_batch_jobs: float
     peak_log_bytes: int
+    host_load_s: float = 0.0       # host time in load_programs + run_and_check (enqueue)
+    host_fetch_s: float = 0.0      # host time fetching and splitting finished batches
+    mean_batch_gpu_ms: float = 0.0  # enqueue-to-completion time of a batch on its stream
 
 
 def poisson_trace(rate: float, seconds: float, seed: int = 5) -> List[float]:
@@ -151,6 +154,7 @@ class _Flight:
     stream: object
     event: object
     log_bytes: int
+    start: object
 
 
 class Server:
@@ -169,18 +173,21 @@ class Server:
         self.ctx.close()
 
     def _finish(self, f: _Flight, t0: float, emit: Callable[[int, JobResult], None]):
+        tf = time.perf_counter()
+        self._gpu_ms.append(f.start.elapsed_time(f.event))
         # one page-locked copy each for the reports, the arenas and the status words
         reps = f.batch.fetch_reports(pinned=True)
         arenas = f.batch.fetch_all_memory(pinned=True)
         status = f.batch.all_status()
         self._accesses += f.batch.stats().shared_accesses
         now = time.perf_counter() - t0
-        # reports are in canonical order, program first: one slice per job
+        # reports are in canonical order, program first: one slice per job (its `prog`
+        # field stays the job's position in the micro-batch)
         cut = np.searchsorted(reps["prog"], np.arange(len(f.jobs) + 1, dtype=np.uint32))
-        reps["prog"] = 0
         for k, job in enumerate(f.jobs):
             emit(job.jid, JobResult(reps[cut[k]:cut[k + 1]], arenas[k], int(status[k]), job.arrival, now))
         f.batch.free()
+        self._fetch_s += time.perf_counter() - tf
 
     def serve(self, jobs: Sequence[Job], on_result: Optional[Callable[[int, JobResult], None]] = None
               ) -> Tuple[Dict[int, JobResult], ServeStats]:
@@ -204,6 +211,8 @@ class Server:
                 on_result(jid, r)
 
         self._accesses = 0
+        self._fetch_s = load_s = 0.0
+        self._gpu_ms = []
         waiting: collections.deque = collections.deque()
         inflight: List[_Flight] = []
         free_streams = list(range(self.max_inflight))
@@ -233,11 +242,15 @@ class Server:
                     break
                 si = free_streams.pop()
                 stream = self.streams[si]
+                tl = time.perf_counter()
+                start = self.torch.cuda.Event(enable_timing=True)
+                start.record(stream)
                 batch = self.ctx.load_programs([j.program for j in take], stream=stream)
                 batch.run_and_check(stream=stream)
-                ev = self.torch.cuda.Event()
+                ev = self.torch.cuda.Event(enable_timing=True)
                 ev.record(stream)
-                inflight.append(_Flight(take, batch, stream, ev, bytes_))
+                load_s += time.perf_counter() - tl
+                inflight.append(_Flight(take, batch, stream, ev, bytes_, start))
                 used += bytes_
                 peak = max(peak, used)
                 nb += 1
@@ -253,5 +266,6 @@ class Server:
                            float(np.percentile(lat, 50)) if len(lat) else 0.0,
                            float(np.percentile(lat, 99)) if len(lat) else 0.0, self._accesses,
                            self._accesses / elapsed if elapsed else 0.0, nb, max_fl,
-                           float(np.mean(batch_sizes)) if batch_sizes else 0.0, peak)
+                           float(np.mean(batch_sizes)) if batch_sizes else 0.0, peak, load_s, self._fetch_s,
+                           float(np.mean(self._gpu_ms)) if self._gpu_ms else 0.0)
         return results, stats

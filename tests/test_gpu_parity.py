@@ -235,6 +235,20 @@ def test_waves_and_graph_and_repeat(B):
             assert list(st & 3) == list(want.status)
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_report_buffer_grown_after_a_one_wave_run(B, use_graph):
+    """More reports than the initial buffer holds, in one wave: only the emission runs again,
+    and later runs of the same batch use the grown buffer."""
+    progs = families.batch(n_programs=30, seed=21, max_grid=10, bug_rate=0.6)
+    want = oracle.run(progs)
+    assert len(want.report_tuples()) > 64
+    with B.Context(mode="batched", use_graph=use_graph, report_cap=16) as ctx, ctx.load_programs(progs) as b:
+        for _ in range(2):
+            b.run_and_check()
+            assert [tuple(int(x) for x in r) for r in b.fetch_reports()] == want.report_tuples()
+            assert all(np.array_equal(x, w) for x, w in zip(b.fetch_all_memory(), want.arenas))
+
+
 def test_log_overflow_is_reported_not_silent(B):
     a = ir.Asm()
     a.s2r(ir.r2, ir.TID).mov(ir.r3, 50).label("l").sts(ir.r2, ir.r3).sub(ir.r3, ir.r3, 1).brnz(ir.r3, "l").exit()

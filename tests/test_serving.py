@@ -54,6 +54,8 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         if key not in alone:
             alone[key] = binding.check([j.program])
         a, r = alone[key], results[j.jid]
-        assert [tuple(int(x) for x in t) for t in r.reports] == a.report_tuples(), j.jid
+        # every field but `prog` (the job's slot in its micro-batch)
+        assert [tuple(int(x) for x in t)[:1] + tuple(int(x) for x in t)[2:] for t in r.reports] == \
+            [t[:1] + t[2:] for t in a.report_tuples()], j.jid
         assert np.array_equal(r.arena, a.arenas[0]), j.jid
         assert r.status == int(a.status[0]), j.jid
