@@ -35,6 +35,10 @@
  *   MOV d,B | ADD..SNE d,a,B | S2R d,#sreg | LDG d,[a+imm] | STG [a+imm],b
  *   LDS d,[a+imm] | STS [a+imm],b | ATOMS [a+imm],b (add, no return)
  *   BRA #t | BRZ a,#t | BRNZ a,#t (absolute pcs in 0..ncode) | BAR | EXIT
+ *   BARAND d,a | BAROR d,a | BARPOPC d,a: __syncthreads_and/_or/_count (Sec. 3 feature
+ *   list): a barrier like BAR whose thread contributes the predicate a != 0; when the
+ *   barrier releases, d = 1 if every / some released thread's predicate holds, or the
+ *   number that hold (threads released from a plain BAR contribute 0).
  *   At launch r0..r(nparams-1) hold the params, every other register 0; shared memory
  *   starts zeroed; running past the last instruction exits the thread.
  *
@@ -75,7 +79,7 @@ enum {
   SR_OP_MOV = 1, SR_OP_ADD, SR_OP_SUB, SR_OP_MUL, SR_OP_DIV, SR_OP_REM, SR_OP_AND, SR_OP_OR,
   SR_OP_XOR, SR_OP_SHL, SR_OP_SHR, SR_OP_MIN, SR_OP_MAX, SR_OP_SLT, SR_OP_SLE, SR_OP_SEQ,
   SR_OP_SNE, SR_OP_S2R, SR_OP_LDG, SR_OP_STG, SR_OP_LDS, SR_OP_STS, SR_OP_ATOMS, SR_OP_BRA,
-  SR_OP_BRZ, SR_OP_BRNZ, SR_OP_BAR, SR_OP_EXIT
+  SR_OP_BRZ, SR_OP_BRNZ, SR_OP_BAR, SR_OP_EXIT, SR_OP_BARAND, SR_OP_BAROR, SR_OP_BARPOPC
 };
 #define SR_BIMM 0x80u
 #define SR_RZ 0xFFu

@@ -12,7 +12,8 @@
  *   finish_epoch     - race check of the accesses since the last barrier (Sec. 3.1:
  *                      pairwise definition; the history is cleared at the barrier)
  *   resolve          - barrier check at the point where no thread can run
- *                      (Sec. 3 "Barrier synchronization"; Sec. 3.1 deadlock paragraph)
+ *                      (Sec. 3 "Barrier synchronization"; Sec. 3.1 deadlock paragraph),
+ *                      and the results of __syncthreads_and/_or/_count at a release
  */
 #include "simt_oracle.h"
 
@@ -82,6 +83,8 @@ typedef struct {
   launch_ctx* C;
   uint32_t block, n, nwarps, shw;
   uint32_t* pc; uint8_t* st; uint32_t* wpc;
+  uint8_t* bk; uint8_t* bp; uint8_t* bd;   /* waiting thread: barrier kind (0 plain, 1 and,
+                                              2 or, 3 count), its predicate, destination */
   int32_t* regs;                 /* [n][16] */
   int32_t* sh;                   /* shared array of this block */
   uint32_t* err_cnt; uint32_t* err_min;   /* per pc, current epoch */
@@ -151,10 +154,13 @@ static int32_t alu(block_t* B, uint32_t op, int32_t va, int32_t vb, uint32_t pc,
 }
 
 /* which operand fields an opcode reads (unused fields are never decoded) */
-static int uses_d(uint32_t b) { return (b >= ORC_MOV && b <= ORC_SNE) || b == ORC_S2R || b == ORC_LDG || b == ORC_LDS; }
+static int is_rbar(uint32_t b) { return b == ORC_BARAND || b == ORC_BAROR || b == ORC_BARPOPC; }
+static int uses_d(uint32_t b) {
+  return (b >= ORC_MOV && b <= ORC_SNE) || b == ORC_S2R || b == ORC_LDG || b == ORC_LDS || is_rbar(b);
+}
 static int uses_a(uint32_t b) {
   return (b >= ORC_ADD && b <= ORC_SNE) || b == ORC_LDG || b == ORC_STG || b == ORC_LDS ||
-         b == ORC_STS || b == ORC_ATOMS || b == ORC_BRZ || b == ORC_BRNZ;
+         b == ORC_STS || b == ORC_ATOMS || b == ORC_BRZ || b == ORC_BRNZ || is_rbar(b);
 }
 static int uses_b(uint32_t op) {
   uint32_t b = op & 0x7Fu;
@@ -228,7 +234,14 @@ static void exec_one(block_t* B, uint32_t t, uint32_t pc) {
     case ORC_BRA: next = (uint32_t)imm; break;
     case ORC_BRZ: if (va == 0) next = (uint32_t)imm; break;
     case ORC_BRNZ: if (va != 0) next = (uint32_t)imm; break;
-    case ORC_BAR: B->st[t] = ST_WAIT; B->wpc[t] = pc; break;
+    case ORC_BAR: case ORC_BARAND: case ORC_BAROR: case ORC_BARPOPC:
+      /* __syncthreads and its reducing forms (Sec. 3 feature list): wait here; a
+         reducing form also hands in its predicate and names where the result goes */
+      B->st[t] = ST_WAIT; B->wpc[t] = pc;
+      B->bk[t] = (uint8_t)(base == ORC_BAR ? 0 : base - ORC_BARAND + 1);
+      B->bp[t] = base != ORC_BAR && va != 0;
+      B->bd[t] = (uint8_t)d;
+      break;
     case ORC_EXIT: B->st[t] = ST_EXIT; break;
   }
   B->pc[t] = next;
@@ -338,7 +351,17 @@ static int resolve(block_t* B) {
     emit(B, ORC_REP_DIVERGENCE, pmin, pmax, nW << 16);
   finish_epoch(B);
   B->epoch++;
-  for (uint32_t t = 0; t < B->n; ++t) if (B->st[t] == ST_WAIT) B->st[t] = ST_RUN;
+  /* release: the reducing barriers' results, over every released thread's predicate
+     (a thread released from a plain barrier contributes a false one) */
+  uint32_t nP = 0;
+  for (uint32_t t = 0; t < B->n; ++t) if (B->st[t] == ST_WAIT && B->bp[t]) ++nP;
+  for (uint32_t t = 0; t < B->n; ++t) {
+    if (B->st[t] != ST_WAIT) continue;
+    if (B->bk[t] == 1) reg_write(B, t, B->bd[t], nP == nW);
+    else if (B->bk[t] == 2) reg_write(B, t, B->bd[t], nP > 0);
+    else if (B->bk[t] == 3) reg_write(B, t, B->bd[t], (int32_t)nP);
+    B->st[t] = ST_RUN;
+  }
   return 0;
 }
 
@@ -351,6 +374,7 @@ static void run_block(launch_ctx* C, uint32_t block) {
   B.shw = L->shmem_words;
   B.deferred = C->O->schedule == 0;
   B.pc = malloc(B.n * sizeof(uint32_t)); B.st = malloc(B.n); B.wpc = malloc(B.n * sizeof(uint32_t));
+  B.bk = calloc(B.n, 1); B.bp = calloc(B.n, 1); B.bd = calloc(B.n, 1);
   B.regs = calloc((size_t)B.n * 16, sizeof(int32_t));
   B.sh = calloc(B.shw ? B.shw : 1, sizeof(int32_t));          /* shared memory starts at zero */
   B.err_cnt = calloc(P->ncode + 1, sizeof(uint32_t));
@@ -386,7 +410,7 @@ static void run_block(launch_ctx* C, uint32_t block) {
     }
   }
   C->rounds += rounds;
-  free(B.pc); free(B.st); free(B.wpc); free(B.regs); free(B.sh);
+  free(B.pc); free(B.st); free(B.wpc); free(B.bk); free(B.bp); free(B.bd); free(B.regs); free(B.sh);
   free(B.err_cnt); free(B.err_min); free(B.acc.v); free(B.sst.v); free(B.gst.v); free(B.ats.v);
 }
 
@@ -402,7 +426,7 @@ static int validate(const orc_program* P, uint32_t idx) {
     uint32_t d = (w >> 8) & 0xFFu, a = (w >> 16) & 0xFFu, b = (w >> 24) & 0xFFu;
     int32_t imm = P->code[pc].imm;
     int alu_op = base >= ORC_MOV && base <= ORC_SNE;
-    if (base < ORC_MOV || base > ORC_EXIT || (op & 0x40u) || ((op & ORC_BIMM) && !alu_op)) {
+    if (base < ORC_MOV || base > ORC_BARPOPC || (op & 0x40u) || ((op & ORC_BIMM) && !alu_op)) {
       snprintf(g_err, sizeof g_err, "program %u pc %u: bad opcode 0x%x", idx, pc, op); return -1; }
     int need_b = uses_b(op);
     if ((uses_d(base) && d >= 16 && d != ORC_RZ) || (uses_a(base) && a >= 16 && a != ORC_RZ) ||

@@ -47,7 +47,7 @@ enum {
   ORC_MOV = 1, ORC_ADD, ORC_SUB, ORC_MUL, ORC_DIV, ORC_REM, ORC_AND, ORC_OR, ORC_XOR,
   ORC_SHL, ORC_SHR, ORC_MIN, ORC_MAX, ORC_SLT, ORC_SLE, ORC_SEQ, ORC_SNE,
   ORC_S2R, ORC_LDG, ORC_STG, ORC_LDS, ORC_STS, ORC_ATOMS, ORC_BRA, ORC_BRZ, ORC_BRNZ,
-  ORC_BAR, ORC_EXIT
+  ORC_BAR, ORC_EXIT, ORC_BARAND, ORC_BAROR, ORC_BARPOPC
 };
 #define ORC_BIMM 0x80u
 #define ORC_RZ 0xFFu

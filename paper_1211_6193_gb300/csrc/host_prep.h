@@ -12,13 +12,18 @@
 namespace sr {
 namespace host {
 
+// barriers: __syncthreads and its reducing forms _and / _or / _count
+inline bool is_barrier(uint32_t b) { return b == SR_OP_BAR || (b >= SR_OP_BARAND && b <= SR_OP_BARPOPC); }
+inline bool is_reducing_barrier(uint32_t b) { return b >= SR_OP_BARAND && b <= SR_OP_BARPOPC; }
+
 // which operand fields an opcode reads or writes
 inline bool op_writes_d(uint32_t b) {
-  return (b >= SR_OP_MOV && b <= SR_OP_SNE) || b == SR_OP_S2R || b == SR_OP_LDG || b == SR_OP_LDS;
+  return (b >= SR_OP_MOV && b <= SR_OP_SNE) || b == SR_OP_S2R || b == SR_OP_LDG || b == SR_OP_LDS ||
+         is_reducing_barrier(b);
 }
 inline bool op_reads_a(uint32_t b) {
   return (b >= SR_OP_ADD && b <= SR_OP_SNE) || b == SR_OP_LDG || b == SR_OP_STG || b == SR_OP_LDS ||
-         b == SR_OP_STS || b == SR_OP_ATOMS || b == SR_OP_BRZ || b == SR_OP_BRNZ;
+         b == SR_OP_STS || b == SR_OP_ATOMS || b == SR_OP_BRZ || b == SR_OP_BRNZ || is_reducing_barrier(b);
 }
 inline bool op_reads_b(uint32_t op) {
   const uint32_t b = op & 0x7Fu;
@@ -89,7 +94,7 @@ inline KernelBound bound_kernel(const sr_instr* code, uint32_t ncode, uint32_t e
     if (pc < ncode) {
       const uint32_t b = code[pc].op_d_a_b & 0x7Fu;
       a += is_shared_access(b);
-      br += b == SR_OP_BAR;
+      br += is_barrier(b);
       kb.err_pcs += can_err(b);
     }
     w.acc[pc] = a;
@@ -116,7 +121,8 @@ inline int validate(const sr_program* p, char* msg, size_t len) {
     const uint32_t d = (w >> 8) & 0xFFu, ra = (w >> 16) & 0xFFu, rb = (w >> 24) & 0xFFu;
     const int32_t imm = p->code[pc].imm;
     const bool alu = b >= SR_OP_MOV && b <= SR_OP_SNE;
-    if (b < SR_OP_MOV || b > SR_OP_EXIT || (op & 0x40u) || ((op & SR_BIMM) && !alu)) return bad("pc %u: bad opcode 0x%x", pc, op);
+    if (b < SR_OP_MOV || b > SR_OP_BARPOPC || (op & 0x40u) || ((op & SR_BIMM) && !alu))
+      return bad("pc %u: bad opcode 0x%x", pc, op);
     auto reg_ok = [](uint32_t r) { return r < 16 || r == SR_RZ; };
     if ((op_writes_d(b) && !reg_ok(d)) || (op_reads_a(b) && !reg_ok(ra)) || (op_reads_b(op) && !reg_ok(rb)))
       return bad("pc %u: bad register field (op %u)", pc, b);

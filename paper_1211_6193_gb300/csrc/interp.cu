@@ -38,7 +38,8 @@ enum : uint32_t { DEC_RELEASE = 1, DEC_DONE = 2, DEC_STOP = 3 };
 struct BlockVars {
   unsigned long long cursor;   // log records reserved by the block
   uint32_t n_misc, epoch, k0, flags, decision, err_dirty, status;
-  uint32_t pad[7];
+  uint32_t bar_np, bar_nw;     // at a release: true predicates, released threads
+  uint32_t pad[5];
 };
 static_assert(sizeof(BlockVars) <= 64, "block vars");
 
@@ -270,6 +271,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   group_sync(bar_id, nthr);
 
   uint32_t pc = Ls->entry, st = tid < bdim ? ST_RUN : ST_NONE, wpc = 0;
+  // at a barrier: destination row | kind << 5 (0 plain, 1 and, 2 or, 3 count) | predicate << 7
+  uint32_t bst = 0;
   uint32_t k = 0, epoch = 0, front_cap = log_cap, omin = 0;
   // pn: the pc the warp issues next (the lowest pc of its runnable lanes, kInf if none);
   // while every runnable lane sits at pn (conv) it is advanced without a reduction
@@ -414,7 +417,16 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             break;
           }
           case SR_OP_BAR:
-            if (act) { st = ST_WAIT; wpc = p; }
+          case SR_OP_BARAND:
+          case SR_OP_BAROR:
+          case SR_OP_BARPOPC:
+            // __syncthreads and its reducing forms: wait; a reducing form hands in its
+            // predicate and keeps the row its result goes to
+            if (act) {
+              st = ST_WAIT;
+              wpc = p;
+              bst = op == SR_OP_BAR ? 0u : (d | (op - SR_OP_BARAND + 1u) << 5 | (va != 0 ? 1u : 0u) << 7);
+            }
             conv = false;
             break;
           default:  // EXIT, and the EXIT sentinel after the last instruction
@@ -446,11 +458,12 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const uint32_t pmn = __reduce_min_sync(FULL, st == ST_WAIT ? wpc : kInf);
       const uint32_t pmx = __reduce_max_sync(FULL, st == ST_WAIT ? wpc : 0u);
       const uint32_t rpc = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
+      const uint32_t tm = __ballot_sync(FULL, st == ST_WAIT && (bst >> 7));   // true predicates
       if (lane == 0) {
         uint32_t* P = park + w * 8;
         P[0] = __popc(wm); P[1] = __popc(xm); P[2] = __popc(rm);
         P[3] = pmn; P[4] = pmx; P[5] = rpc; P[6] = k;
-        P[7] = (limit ? 1u : 0u) | (timeout ? 2u : 0u);
+        P[7] = (limit ? 1u : 0u) | (timeout ? 2u : 0u) | (uint32_t)__popc(tm) << 8;
         st_release_cta(&clk[w], kInf);
       }
     }
@@ -467,7 +480,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const uint32_t pmx = __reduce_max_sync(FULL, v ? P[4] : 0u);
       const uint32_t rpc = __reduce_min_sync(FULL, v ? P[5] : kInf);
       const uint32_t kmax = __reduce_max_sync(FULL, v ? P[6] : 0u);
-      const uint32_t fl = __reduce_or_sync(FULL, v ? P[7] : 0u);
+      const uint32_t fl = __reduce_or_sync(FULL, v ? P[7] & 0xFFu : 0u);
+      const uint32_t nP = __reduce_add_sync(FULL, v ? P[7] >> 8 : 0u);
       const uint32_t ep = bv->epoch;
       uint32_t dec, kind = 0, a = 0, b = 0, c = 0, stbits = 0;
       if (fl & 2u) {
@@ -489,13 +503,26 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       if (lane == 0) {
         bv->decision = dec;
         bv->status |= stbits;
-        if (dec == DEC_RELEASE) { bv->epoch = ep + 1; bv->k0 = kmax; }
+        if (dec == DEC_RELEASE) {
+          bv->epoch = ep + 1;
+          bv->k0 = kmax;
+          bv->bar_np = nP;
+          bv->bar_nw = nW;
+        }
       }
       if (dec == DEC_RELEASE && v) clk[lane] = 4u * kmax;
     }
     group_sync(bar_id, nthr);
     if (bv->decision != DEC_RELEASE) break;
-    if (st == ST_WAIT) st = ST_RUN;
+    if (st == ST_WAIT) {
+      // a reducing barrier's result, over every released thread's predicate
+      const uint32_t kind = (bst >> 5) & 3u, row = bst & 31u;
+      if (kind && row != kNoDest) {
+        const uint32_t np = bv->bar_np;
+        myregs[row * nthr] = kind == 1 ? (np == bv->bar_nw ? 1u : 0u) : kind == 2 ? (np ? 1u : 0u) : np;
+      }
+      st = ST_RUN;
+    }
     pn = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
     conv = __all_sync(FULL, st != ST_RUN || pc == pn);
     k = bv->k0;

@@ -66,7 +66,7 @@ def _kernel_bound(code: np.ndarray, entry: int):
         if pc < n:
             b = int(ops[pc]) & 0x7F
             a += b in (ir.LDS, ir.STS, ir.ATOMS)
-            br += b == ir.BAR
+            br += b in ir.BAR_OPS
             errs += b in (ir.LDS, ir.STS, ir.ATOMS, ir.LDG, ir.STG, ir.DIV, ir.REM)
         acc[pc], bar[pc], colour[pc] = a, br, 2
         stack.pop()

@@ -30,6 +30,10 @@ Opcodes and operand use::
     BRA #t   BRZ a, #t   BRNZ a, #t           absolute targets (program pc)
     BAR                  __syncthreads()
     EXIT                 thread exits; running past the last instruction also exits
+    BARAND d, a          __syncthreads_and(a): d = 1 if a != 0 in every thread released
+    BAROR d, a           __syncthreads_or(a):  d = 1 if a != 0 in some thread released
+    BARPOPC d, a         __syncthreads_count(a): d = number of released threads with a != 0
+                         (Sec. 3 feature list; threads released from a plain BAR count as 0)
 """
 from __future__ import annotations
 
@@ -41,6 +45,8 @@ import numpy as np
 # ---------------------------------------------------------------- opcode table
 MOV, ADD, SUB, MUL, DIV, REM, AND, OR, XOR, SHL, SHR, MIN, MAX, SLT, SLE, SEQ, SNE = range(1, 18)
 S2R, LDG, STG, LDS, STS, ATOMS, BRA, BRZ, BRNZ, BAR, EXIT = range(18, 29)
+BARAND, BAROR, BARPOPC = range(29, 32)
+BAR_OPS = (BAR, BARAND, BAROR, BARPOPC)
 BIMM = 0x80
 RZ_INDEX = 0xFF
 NREGS = 16
@@ -51,6 +57,7 @@ OP_NAMES = {
     OR: "OR", XOR: "XOR", SHL: "SHL", SHR: "SHR", MIN: "MIN", MAX: "MAX", SLT: "SLT",
     SLE: "SLE", SEQ: "SEQ", SNE: "SNE", S2R: "S2R", LDG: "LDG", STG: "STG", LDS: "LDS",
     STS: "STS", ATOMS: "ATOMS", BRA: "BRA", BRZ: "BRZ", BRNZ: "BRNZ", BAR: "BAR", EXIT: "EXIT",
+    BARAND: "BARAND", BAROR: "BAROR", BARPOPC: "BARPOPC",
 }
 
 # special registers read by S2R (the built-in symbols of Sec. 3; 1-D only)
@@ -169,6 +176,15 @@ class Asm:
     def bar(self) -> "Asm":
         return self._emit(BAR)
 
+    def bar_and(self, d: Reg, a: Reg) -> "Asm":
+        return self._emit(BARAND, d, a)
+
+    def bar_or(self, d: Reg, a: Reg) -> "Asm":
+        return self._emit(BAROR, d, a)
+
+    def bar_count(self, d: Reg, a: Reg) -> "Asm":
+        return self._emit(BARPOPC, d, a)
+
     def exit(self) -> "Asm":
         return self._emit(EXIT)
 
@@ -213,6 +229,8 @@ def disassemble(code: np.ndarray) -> List[str]:
             s = f"BRA ->{imm}"
         elif base in (BRZ, BRNZ):
             s = f"{name} {rn(a)}, ->{imm}"
+        elif base in (BARAND, BAROR, BARPOPC):
+            s = f"{name} {rn(d)}, {rn(a)}"
         else:
             s = name
         lines.append(f"{pc:3d} {s}")

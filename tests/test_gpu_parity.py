@@ -206,6 +206,14 @@ def test_more_racy_words_than_one_summary_round(B, mode):
     assert len(races) == 2 * (8 + 3 + 12) * 1024
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_reducing_barriers(B, mode):
+    """__syncthreads_and/_or/_count: predicates over full and partial warps, reducing and
+    plain barriers meeting, a deadlock at a reducing barrier, reducing barriers in a loop."""
+    from rbar_programs import all_programs
+    assert_parity(B, all_programs(), mode)
+
+
 def test_race_check_disabled_keeps_memory_and_barrier_reports(B):
     progs = families.batch(n_programs=24, seed=8, max_grid=4, bug_rate=0.6)
     want = oracle.run(progs, check_races=False)

@@ -42,6 +42,13 @@ MUTANTS = {
     "shared_bound_off_by_one": (
         "if (addr < 0 || (uint32_t)addr >= B->shw) { note_err(B, pc, t); break; }",
         "if (addr < 0 || (uint32_t)addr >= B->shw + 1) { note_err(B, pc, t); break; }"),
+    "count_barrier_over_last_warp_only": (
+        "for (uint32_t t = 0; t < B->n; ++t) if (B->st[t] == ST_WAIT && B->bp[t]) ++nP;",
+        "for (uint32_t t = (B->n - 1) / 32 * 32; t < B->n; ++t) if (B->st[t] == ST_WAIT && B->bp[t]) ++nP;"),
+    "and_barrier_is_or": ("if (B->bk[t] == 1) reg_write(B, t, B->bd[t], nP == nW);",
+                          "if (B->bk[t] == 1) reg_write(B, t, B->bd[t], nP > 0);"),
+    "plain_barrier_counts_as_true": ("B->bp[t] = base != ORC_BAR && va != 0;",
+                                     "B->bp[t] = base == ORC_BAR || va != 0;"),
     "warps_of_16": (
         "uint32_t lo = 32 * w, hi = lo + 32 < B->n ? lo + 32 : B->n;",
         "uint32_t lo = 16 * w, hi = lo + 16 < B->n ? lo + 16 : B->n; if (lo >= B->n) continue;"),

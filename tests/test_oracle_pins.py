@@ -234,6 +234,97 @@ def test_same_round_store_then_atomic_order():
     assert (rec[0][7] >> 24) == oracle.CLS_WW | oracle.CLS_WA
 
 
+# ------------------------------------------------------------------ __syncthreads_and/_or/_count
+def _rbar_values(bdim, pred_limit):
+    """Every thread: pred = tid < pred_limit; COUNT, AND, OR of it; stores the three results."""
+    a = ir.Asm()
+    a.s2r(ir.r2, ir.TID).slt(ir.r3, ir.r2, pred_limit)
+    a.bar_count(ir.r4, ir.r3).bar_and(ir.r5, ir.r3).bar_or(ir.r6, ir.r3)
+    a.mul(ir.r7, ir.r2, 3).stg(ir.r7, ir.r4).stg(ir.r7, ir.r5, 1).stg(ir.r7, ir.r6, 2).exit()
+    p = ir.Program(a.assemble(), [0], [ir.Launch(0, 1, bdim, 0, ())], np.full(3 * bdim, -1, np.int32))
+    r = oracle.run([p])
+    return r, r.arenas[0].reshape(bdim, 3)
+
+
+@pytest.mark.parametrize("bdim,limit", [(100, 37), (100, 100), (100, 0), (33, 32), (1, 1), (1024, 1000)])
+def test_reducing_barriers_hand_values(bdim, limit):
+    r, got = _rbar_values(bdim, limit)
+    n = min(bdim, limit)
+    assert reports_of(r) == [] and r.status[0] == 0
+    assert (got[:, 0] == n).all()                     # __syncthreads_count
+    assert (got[:, 1] == int(n == bdim)).all()        # __syncthreads_and
+    assert (got[:, 2] == int(n > 0)).all()            # __syncthreads_or
+
+
+@pytest.mark.parametrize("bdim", [33, 100, 512])
+def test_reducing_barrier_count_closed_form(bdim):
+    """Per block, the number of odd inputs, counted by __syncthreads_count and stored by
+    thread 0: numpy's count of the same values."""
+    grid = 5
+    rng = np.random.default_rng(bdim)
+    vals = rng.integers(-1000, 1000, grid * bdim, dtype=np.int32)
+    a = ir.Asm()
+    a.s2r(ir.r2, ir.TID).s2r(ir.r3, ir.BID).mul(ir.r4, ir.r3, bdim).add(ir.r4, ir.r4, ir.r2)
+    a.ldg(ir.r5, ir.r4).and_(ir.r6, ir.r5, 1).bar_count(ir.r7, ir.r6)
+    a.brnz(ir.r2, "x").stg(ir.r3, ir.r7, grid * bdim).label("x").exit()
+    p = ir.Program(a.assemble(), [0], [ir.Launch(0, grid, bdim, 0, ())],
+                   np.concatenate([vals, np.zeros(grid, np.int32)]))
+    r = oracle.run([p])
+    want = (vals.reshape(grid, bdim) & 1).sum(axis=1)
+    assert list(r.arenas[0][grid * bdim:]) == list(want)
+
+
+def test_reducing_barrier_mixed_with_plain_barrier():
+    """Threads 0..39 reach BARAND/BARPOPC with a true predicate, the others a plain BAR:
+    DIVERGENCE is reported, and the plain waiters count as false."""
+    a = ir.Asm()
+    a.s2r(ir.r2, ir.TID).slt(ir.r3, ir.r2, 40).brz(ir.r3, "plain")
+    a.bar_count(ir.r4, ir.r3).bar_and(ir.r5, ir.r3).stg(ir.r2, ir.r4).stg(ir.r2, ir.r5, 100).exit()
+    a.label("plain").bar().bar().exit()
+    p = ir.Program(a.assemble(), [0], [ir.Launch(0, 1, 100, 0, ())], np.full(200, -1, np.int32))
+    r = oracle.run([p])
+    A = r.arenas[0]
+    assert list(A[:40]) == [40] * 40 and list(A[40:100]) == [-1] * 60
+    assert list(A[100:140]) == [0] * 40
+    pc_cnt = find_pc(p.code, lambda op, d, a_, b, imm: op == ir.BARPOPC)[0]
+    pc_and = find_pc(p.code, lambda op, d, a_, b, imm: op == ir.BARAND)[0]
+    pcs_bar = find_pc(p.code, lambda op, d, a_, b, imm: op == ir.BAR)
+    assert reports_of(r) == [(oracle.DIVERGENCE, 0, 0, 0, 0, pc_cnt, pcs_bar[0], 100 << 16),
+                             (oracle.DIVERGENCE, 0, 0, 0, 1, pc_and, pcs_bar[1], 100 << 16)]
+
+
+def test_reducing_barriers_in_a_loop_closed_form():
+    """Threads count down from tid % 7 until __syncthreads_and sees every counter at 0,
+    summing __syncthreads_count of the threads still counting: the total number of
+    decrements, sum(tid % 7), in every thread."""
+    from rbar_programs import loop_until_all_done
+    r = oracle.run([loop_until_all_done(96)])
+    assert reports_of(r) == [] and list(r.arenas[0]) == [sum(t % 7 for t in range(96))] * 96
+
+
+def test_reducing_barrier_deadlock_and_race_interval():
+    """A reducing barrier is a barrier: it ends the race interval; with exited threads it
+    deadlocks like BAR and the block stops before any result is used."""
+    def prog(sync):
+        a = ir.Asm()
+        a.s2r(ir.r2, ir.TID).add(ir.r3, ir.r2, 1).and_(ir.r3, ir.r3, 63).sts(ir.r2, ir.r2)
+        if sync:
+            a.bar_or(ir.r4, ir.r2)
+        a.lds(ir.r5, ir.r3).stg(ir.r2, ir.r5).exit()
+        return ir.Program(a.assemble(), [0], [ir.Launch(0, 1, 64, 64, ())], np.zeros(64, np.int32))
+    assert reports_of(oracle.run([prog(True)])) == []
+    assert len(reports_of(oracle.run([prog(False)]), oracle.RACE)) == 64
+    a = ir.Asm()
+    a.s2r(ir.r2, ir.TID).slt(ir.r3, ir.r2, 5).brnz(ir.r3, "x").bar_count(ir.r4, ir.r3)
+    a.stg(ir.r2, ir.r4).label("x").exit()
+    p = ir.Program(a.assemble(), [0], [ir.Launch(0, 1, 64, 0, ()), ir.Launch(0, 1, 64, 0, ())],
+                   np.full(64, -1, np.int32))
+    r = oracle.run([p])
+    pc = find_pc(p.code, lambda op, d, a_, b, imm: op == ir.BARPOPC)[0]
+    assert reports_of(r) == [(oracle.DEADLOCK, 0, 0, 0, 0, pc, pc, (59 << 16) | 5)]
+    assert r.status[0] & oracle.ST_DEADLOCK and list(r.arenas[0]) == [-1] * 64
+
+
 # ------------------------------------------------------------------ exhaustive interleavings
 @pytest.mark.parametrize("nthreads,nsteps,count,nwords,bar_rate",
                          [(2, 6, 40, 3, 0.25), (3, 4, 40, 3, 0.25), (3, 6, 16, 8, 0.6)])
