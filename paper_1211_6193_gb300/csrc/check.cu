@@ -35,7 +35,6 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr uint32_t NONE = 0xFFFFu;
 constexpr uint32_t NB = kCheckBins;
 constexpr uint32_t NBW = NB / 32;              // words of the racy-address bitmap
-constexpr uint32_t DS = NB / 4;                // exact summaries per round (4 table words each)
 constexpr uint32_t END = 0xFFFFFFFFu;
 
 // table word: tag << 14 | tid << 4 | MULTI | kind bits (1 << K_R, 1 << K_W, 1 << K_A)
@@ -199,10 +198,10 @@ __device__ uint32_t scan_bitmap(const uint32_t* bm, uint32_t* pre, uint32_t nw, 
 
 // One record (low and high words) into the address table, the tag in the high bits of
 // tagw.  An entry that becomes racy marks the interval in *racy.
-__device__ __forceinline__ void table_add(uint32_t* tab, uint32_t lo, uint32_t hi, uint32_t tagw, uint32_t tag,
-                                          volatile uint32_t* racy, bool& bad) {
+__device__ __forceinline__ void table_add(uint32_t* tab, uint32_t ntab, uint32_t lo, uint32_t hi, uint32_t tagw,
+                                          uint32_t tag, volatile uint32_t* racy, bool& bad) {
   const uint32_t a = __funnelshift_r(lo, hi, 24) & 0x3FFFu;   // record bits 24..37
-  if (a >= NB) {
+  if (a >= ntab) {
     bad = true;
     return;
   }
@@ -227,14 +226,14 @@ __device__ __forceinline__ void table_add(uint32_t* tab, uint32_t lo, uint32_t h
 // needed.  A swap that lost a race (another thread, or an earlier record of this same
 // thread, wrote the entry) is redone by table_add.
 template <uint32_t P>
-__device__ __forceinline__ void table_add_set(uint32_t* tab, const uint32_t (&lo)[P], const uint32_t (&hi)[P],
-                                              uint32_t m, uint32_t tagw, uint32_t tag, volatile uint32_t* racy,
-                                              bool& bad) {
+__device__ __forceinline__ void table_add_set(uint32_t* tab, uint32_t ntab, const uint32_t (&lo)[P],
+                                              const uint32_t (&hi)[P], uint32_t m, uint32_t tagw, uint32_t tag,
+                                              volatile uint32_t* racy, bool& bad) {
   uint32_t a[P], x[P], o[P], n[P];
 #pragma unroll
   for (uint32_t j = 0; j < P; ++j) {
     a[j] = __funnelshift_r(lo[j], hi[j], 24) & 0x3FFFu;
-    if (((m >> j) & 1u) && a[j] >= NB) {
+    if (((m >> j) & 1u) && a[j] >= ntab) {
       bad = true;
       m &= ~(1u << j);
     }
@@ -260,7 +259,7 @@ __device__ __forceinline__ void table_add_set(uint32_t* tab, const uint32_t (&lo
   if (retry) {
 #pragma unroll
     for (uint32_t j = 0; j < P; ++j)
-      if ((retry >> j) & 1u) table_add(tab, lo[j], hi[j], tagw, tag, racy, bad);
+      if ((retry >> j) & 1u) table_add(tab, ntab, lo[j], hi[j], tagw, tag, racy, bad);
   }
 }
 
@@ -290,9 +289,11 @@ __device__ __forceinline__ void slot_add(uint32_t* sl, unsigned long long r) {
 // consumers are synchronised on entry and on return).  Returns the number of race
 // entries written at region (as 16-byte entries) + race_out.
 template <uint32_t NC>
-__device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t* bm, uint32_t* pre, uint32_t* wtot,
-                                               uint4* stage_out, unsigned long long* region, uint32_t race_out,
-                                               uint32_t shw, uint32_t tagw, uint32_t epoch, uint32_t s, uint32_t e) {
+__device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t ntab, uint32_t* bm, uint32_t* pre,
+                                               uint32_t* wtot, uint4* stage_out, unsigned long long* region,
+                                               uint32_t race_out, uint32_t shw, uint32_t tagw, uint32_t epoch,
+                                               uint32_t s, uint32_t e) {
+  const uint32_t DS = ntab / 4;                   // exact summaries per round (4 table words each)
   constexpr uint32_t NCW = NC / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t nw = (shw + 31u) >> 5;
@@ -343,17 +344,17 @@ __device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t* bm, uint
 // End of the interval [s, e) with epoch `epoch` (consumers synchronised): races of a
 // racy interval, then the next tag and parity.
 template <uint32_t NC>
-__device__ __forceinline__ void close_interval(uint32_t* tab, uint32_t* bm, uint32_t* pre, uint32_t* wtot,
-                                               uint4* stage_out, volatile uint32_t* s_racy,
+__device__ __forceinline__ void close_interval(uint32_t* tab, uint32_t ntab, uint32_t* bm, uint32_t* pre,
+                                               uint32_t* wtot, uint4* stage_out, volatile uint32_t* s_racy,
                                                unsigned long long* region, uint32_t& race_out, uint32_t shw,
                                                uint32_t& iv, uint32_t& par, uint32_t& tag, uint32_t& tagw,
                                                uint32_t epoch, uint32_t s, uint32_t e) {
   if (s_racy[par] == tag)
-    race_out += racy_interval<NC>(tab, bm, pre, wtot, stage_out, region, race_out, shw, tagw, epoch, s, e);
+    race_out += racy_interval<NC>(tab, ntab, bm, pre, wtot, stage_out, region, race_out, shw, tagw, epoch, s, e);
   par ^= 1u;
   if (++iv % TAG_MOD == 0) {                      // tags wrap: forget every entry
     cbar<NC>();                                   // everyone has read s_racy
-    for (uint32_t i = threadIdx.x; i < NB; i += NC) tab[i] = 0;
+    for (uint32_t i = threadIdx.x; i < ntab; i += NC) tab[i] = 0;
     if (threadIdx.x < 2) s_racy[threadIdx.x] = 0;
     cbar<NC>();
     ++iv;
@@ -370,7 +371,8 @@ __device__ __forceinline__ void close_interval(uint32_t* tab, uint32_t* bm, uint
 // log stopped the pass before the release).
 template <uint32_t NC, uint32_t PER, class Release>
 __device__ __forceinline__ uint32_t stage_pass(
-    uint32_t* tab, uint32_t* bm, uint32_t* pre, uint32_t* wtot, uint4* stage_out, volatile uint32_t* s_racy,
+    uint32_t* tab, uint32_t ntab, uint32_t* bm, uint32_t* pre, uint32_t* wtot, uint4* stage_out,
+    volatile uint32_t* s_racy,
     volatile uint32_t* s_npos, volatile uint32_t* s_nep, BlockRes* blocks, const uint32_t (&lo)[PER],
     const uint32_t (&hi)[PER], uint32_t nval, uint32_t cbase, uint32_t e0, uint32_t ebefore, uint32_t elast,
     bool first, bool last, uint32_t pos, uint32_t cnt, uint32_t n, uint32_t gb, unsigned long long* region,
@@ -393,8 +395,8 @@ __device__ __forceinline__ uint32_t stage_pass(
         }
         end = pos + np;
       }
-      close_interval<NC>(tab, bm, pre, wtot, stage_out, s_racy, region, race_out, shw, iv, par, tag, tagw, ep, ivs,
-                         end);
+      close_interval<NC>(tab, ntab, bm, pre, wtot, stage_out, s_racy, region, race_out, shw, iv, par, tag, tagw, ep,
+                         ivs, end);
       if (why == 3) {
         if (threadIdx.x == 0) blocks[gb].n_race = race_out;
         return 3;
@@ -418,7 +420,7 @@ __device__ __forceinline__ uint32_t stage_pass(
         }
       }
     }
-    if (__any_sync(FULL, m != 0)) table_add_set<PER>(tab, lo, hi, m, tagw, tag, s_racy + par, bad);
+    if (__any_sync(FULL, m != 0)) table_add_set<PER>(tab, ntab, lo, hi, m, tagw, tag, s_racy + par, bad);
     if (elast != ep) {
       why = 2;
       continue;
@@ -613,7 +615,7 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_check(CheckArgs A) {
     const uint32_t elast = rec_epoch(tile[d_cnt - 1]);
     bool bad = false;
     const uint32_t why = stage_pass<NC, C::PER>(
-        tab, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, lo, hi, nval, cbase, e0, ebefore, elast,
+        tab, NB, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, lo, hi, nval, cbase, e0, ebefore, elast,
         d_flags & 1u, d_flags & 2u, d_pos, d_cnt, d_n, gb, region, shw, race_out, ep, ivs, iv, par, tag, tagw, bad,
         [&]() {
           __syncwarp();
@@ -638,13 +640,14 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_check(CheckArgs A) {
 template <uint32_t NC>
 struct RegCfg {
   static constexpr uint32_t NCW = NC / 32;
-  static constexpr uint32_t O_BM = NB * 4;
+  static constexpr uint32_t O_BM = 0;
   static constexpr uint32_t O_PRE = O_BM + NBW * 4;
   static constexpr uint32_t O_ITEM = O_PRE + NBW * 4;          // [2] x {item, launch, n[32]}
   static constexpr uint32_t ITEM_WORDS = 2 + kCheckMaxGroup;
   static constexpr uint32_t O_MISC = O_ITEM + 2 * ITEM_WORDS * 4;
   static constexpr uint32_t MISC_WORDS = 8 + NCW + 1;
-  static constexpr uint32_t SMEM = O_MISC + MISC_WORDS * 4;
+  static constexpr uint32_t O_TABLE = (O_MISC + MISC_WORDS * 4 + 15u) & ~15u;   // table_words entries
+  static constexpr uint32_t smem(uint32_t table_words) { return O_TABLE + table_words * 4; }
 };
 
 // Records [0, nval) of a stage from src (16-byte aligned); the pair that holds the last
@@ -702,7 +705,8 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
   using C = RegCfg<NC>;
   constexpr uint32_t T = NC * PER;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint32_t* tab = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* tab = reinterpret_cast<uint32_t*>(smem + C::O_TABLE);
+  const uint32_t ntab = A.table_words;           // >= every shared array of the wave
   uint32_t* bm = reinterpret_cast<uint32_t*>(smem + C::O_BM);
   uint32_t* pre = reinterpret_cast<uint32_t*>(smem + C::O_PRE);
   volatile uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + C::O_ITEM);
@@ -714,7 +718,7 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
   const uint32_t tid = threadIdx.x, cbase = tid * PER;
   uint4* const stage_out = A.scratch + (size_t)blockIdx.x * kScratchWords;
 
-  for (uint32_t i = tid; i < NB; i += NC) tab[i] = 0;
+  for (uint32_t i = tid; i < ntab; i += NC) tab[i] = 0;
   if (tid < 8) misc[tid] = 0;
   if (tid < 32) {
     uint32_t item = 0;
@@ -770,7 +774,7 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
         const uint32_t e0 = ce0 >> 6, elast = celast >> 6, ebefore = cebefore >> 6;
         if (pos == 0) ep = e0;
         const uint32_t how =
-            stage_pass<NC, PER>(tab, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, clo, chi, nval,
+            stage_pass<NC, PER>(tab, ntab, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, clo, chi, nval,
                                 cbase, e0, ebefore, elast, pos == 0, last, pos, cnt, n, gb, region, shw, race_out, ep,
                                 ivs, iv, par, tag, tagw, bad, []() {});
         if (how == 2) {                           // (uniform) epochs out of order: give up
@@ -802,17 +806,17 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
 
 template <uint32_t NC, uint32_t PER, uint32_t MINB>
 struct RegVariant {
-  static constexpr uint32_t smem() { return RegCfg<NC>::SMEM; }
+  static constexpr uint32_t smem(uint32_t table_words) { return RegCfg<NC>::smem(table_words); }
   static cudaError_t init(uint32_t optin) {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, k_check_reg<NC, PER, MINB>);
     if (e != cudaSuccess) return e;
-    if (smem() + fa.sharedSizeBytes > optin) return cudaErrorInvalidValue;
+    if (smem(NB) + fa.sharedSizeBytes > optin) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(k_check_reg<NC, PER, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem());
+                                (int)smem(NB));
   }
   static cudaError_t launch(const CheckArgs& a, uint32_t ctas, cudaStream_t s) {
-    k_check_reg<NC, PER, MINB><<<ctas, NC, smem(), s>>>(a);
+    k_check_reg<NC, PER, MINB><<<ctas, NC, smem(a.table_words), s>>>(a);
     return cudaGetLastError();
   }
 };
@@ -846,7 +850,7 @@ const VariantEntry kVariants[SR_CHECK_VARIANTS] = {
     entry<CheckVariant<256, 1024, 3, 2>, 2>(),
     entry<CheckVariant<128, 512, 4, 3>, 3>(),
     entry<RegVariant<128, 4, 4>, 4>(),
-    entry<RegVariant<256, 4, 2>, 2>(),
+    entry<RegVariant<64, 4, 8>, 8>(),
 };
 constexpr uint32_t kDefaultVariant = 3;
 

@@ -115,6 +115,7 @@ struct CheckArgs {
   uint32_t* work_head;
   uint32_t* error_flag;
   uint32_t spin_limit;
+  uint32_t table_words;         // address-table entries: >= every shw of the wave, multiple of 32
 };
 // race-check kernel shapes (variant 1..SR_CHECK_VARIANTS; 0 = default)
 uint32_t check_default_variant();
@@ -124,6 +125,15 @@ constexpr uint32_t kCheckBins = 12288;         // address table entries (>= the 
 constexpr uint32_t kScratchWords = 1u << 14;   // race entries per CTA staged in global memory
 constexpr uint32_t kCheckItemRecords = 8192;   // log records a check work item aims at
 constexpr uint32_t kCheckMaxGroup = 32;        // blocks per check work item at most
+
+// address-table entries for a wave's race check: one per word of its largest shared array,
+// and room for the exact summaries (4 entries each) of every word in one round
+inline uint32_t check_table_words(const LaunchDev* L, uint32_t li0, uint32_t li1) {
+  uint32_t m = 8;
+  for (uint32_t i = li0; i < li1; ++i) m = L[i].shw > m ? L[i].shw : m;
+  m = (4u * m + 31u) & ~31u;
+  return m < kCheckBins ? m : kCheckBins;
+}
 
 // blocks per check work item for a launch whose blocks log at most `log_cap` records
 __host__ __device__ inline uint32_t check_group_for(uint32_t log_cap) {

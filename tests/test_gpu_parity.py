@@ -206,6 +206,22 @@ def test_more_racy_words_than_one_summary_round(B, mode):
     assert len(races) == 2 * (8 + 3 + 12) * 1024
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_every_check_variant(B, variant):
+    """Each race-check kernel shape on its own: the table sized to small and large shared
+    arrays, intervals with more racy words than a summary round holds, intervals spanning
+    stages, and a batch of generated programs with planted bugs."""
+    groups = [  # one batch each, so that each sizes the table to its own largest shared array
+        _many_racy_addresses_programs(), _large_interval_programs()[:2],
+        families.batch(n_programs=24, seed=31, max_grid=12, bug_rate=0.5),
+        [fig1.program(race=True)], [families.reduction_plain(n_blocks=20, bdim=256, seed=2, omit_level=2)],
+        [stencil2d.program(log2w=6, steps=3, buggy_launch=1, seed=5)],
+    ]
+    for progs in groups:
+        for mode in MODES:
+            assert_parity(B, progs, mode, check_variant=variant)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_reducing_barriers(B, mode):
     """__syncthreads_and/_or/_count: predicates over full and partial warps, reducing and
