@@ -676,9 +676,13 @@ __device__ __forceinline__ void item_setup(const CheckArgs& A, uint32_t item, vo
   uint32_t li = 0, nb = 0, first = 0;
   if (item < A.item1) {
     uint32_t lo = A.li0, hi = A.li1 - 1;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi + 1) >> 1;
-      if (A.launches[mid].check_item <= item) lo = mid; else hi = mid - 1;
+    if (A.item_launch) {
+      lo = A.item_launch[item];
+    } else {
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (A.launches[mid].check_item <= item) lo = mid; else hi = mid - 1;
+      }
     }
     const LaunchDev* L = A.launches + lo;
     li = lo;

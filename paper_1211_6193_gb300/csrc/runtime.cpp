@@ -53,6 +53,7 @@ struct sr_batch {
   std::vector<LaunchDev> launches;
   std::vector<uint64_t> arena_off, arena_words;
   std::vector<uint2> items;
+  std::vector<uint32_t> item_launch;       // race check: launch of every work item
   std::vector<Wave> waves;
   uint32_t nblocks = 0;
   uint32_t check_items = 0;                // race-check work items of all waves
@@ -60,7 +61,7 @@ struct sr_batch {
   uint32_t batched_smem = 0;
   uint64_t total_code = 0, total_arena = 0, log_records = 0;
   DevBuf code, launches_d, arena_init, arena_work, log, blocks, prog_status, prog_abort, counters, items_d,
-      queue_head, launch_done, scratch, work_head, err_flag, offsets, partials, out, total;
+      queue_head, launch_done, scratch, work_head, err_flag, offsets, partials, out, total, item_launch_d;
   uint64_t out_cap = 0;
   cudaStream_t stream = nullptr;
   bool ran = false;
@@ -125,7 +126,7 @@ void free_batch_buffers(sr_ctx* c, sr_batch* b, cudaStream_t s) {
   DevBuf* all[] = {&b->code, &b->launches_d, &b->arena_init, &b->arena_work, &b->log, &b->blocks,
                    &b->prog_status, &b->prog_abort, &b->counters, &b->items_d, &b->queue_head,
                    &b->launch_done, &b->scratch, &b->work_head, &b->err_flag, &b->offsets, &b->partials,
-                   &b->out, &b->total};
+                   &b->out, &b->total, &b->item_launch_d};
   for (DevBuf* d : all) dev_free(c, *d, s);
 }
 
@@ -220,6 +221,7 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       ca.error_flag = (uint32_t*)b->err_flag.p;
       ca.spin_limit = o.spin_limit;
       ca.table_words = sr::check_table_words(b->launches.data(), w.li0, w.li1);
+      ca.item_launch = (const uint32_t*)b->item_launch_d.p;
       CUDA_TRY(c, cudaMemsetAsync(ca.work_head, 0, 4, s));
       const uint32_t ctas = std::min<uint32_t>(b->check_ctas, ca.item1 - ca.item0);
       if (ctas) CUDA_TRY(c, sr::launch_check(ca, o.check_variant, ctas, s));
@@ -377,6 +379,12 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   }
   b->nblocks = (uint32_t)nblocks;
   b->check_items = (uint32_t)check_items;
+  b->item_launch.resize(check_items);
+  for (uint32_t li = 0; li < b->launches.size(); ++li) {
+    const LaunchDev& d = b->launches[li];
+    const uint32_t n = (d.grid + d.check_group - 1) / d.check_group;
+    std::fill(b->item_launch.begin() + d.check_item, b->item_launch.begin() + d.check_item + n, li);
+  }
   b->total_code = code.size();
   b->total_arena = arena_total;
 
@@ -451,6 +459,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       {&b->partials, sr::compact_partials_count(b->nblocks) * 8, "scan partials"},
       {&b->out, b->out_cap * sizeof(sr_report), "reports"},
       {&b->total, 8, "report total"},
+      {&b->item_launch_d, std::max<size_t>(1, b->item_launch.size()) * 4, "check item table"},
   };
   for (auto& a : allocs) {
     rc = alloc_buf(c, *a.buf, a.bytes, s, a.what);
@@ -466,6 +475,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   cudaError_t e = up(b->code, code.data(), code.size() * 8);
   if (e == cudaSuccess) e = up(b->launches_d, b->launches.data(), nl * sizeof(LaunchDev));
   if (e == cudaSuccess) e = up(b->items_d, b->items.data(), b->items.size() * 8);
+  if (e == cudaSuccess) e = up(b->item_launch_d, b->item_launch.data(), b->item_launch.size() * 4);
   // zero the padding between arenas (each starts on a 16-byte boundary)
   if (e == cudaSuccess && b->total_arena) e = cudaMemsetAsync(b->arena_init.p, 0, b->total_arena * 4, s);
   for (uint32_t i = 0; i < n && e == cudaSuccess; ++i)

@@ -116,6 +116,7 @@ struct CheckArgs {
   uint32_t* error_flag;
   uint32_t spin_limit;
   uint32_t table_words;         // address-table entries: >= every shw of the wave, multiple of 32
+  const uint32_t* item_launch;  // launch index of every work item (NULL: found by binary search)
 };
 // race-check kernel shapes (variant 1..SR_CHECK_VARIANTS; 0 = default)
 uint32_t check_default_variant();
