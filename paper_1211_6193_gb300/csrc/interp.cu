@@ -162,6 +162,11 @@ __device__ __forceinline__ void note_err(uint32_t* err, BlockVars* bv, uint32_t 
   }
 }
 
+// The 8-byte access-log record (layout in sr_internal.h) from its parts.
+__device__ __forceinline__ unsigned long long rec_of(uint32_t epoch_hi, uint32_t low_bits, uint32_t addr) {
+  return (unsigned long long)(epoch_hi | addr >> 8) << 32 | (low_bits | addr << 24);
+}
+
 // Append one record per lane with `me` to the block's access log (warp-aggregated:
 // one shared atomic per warp, consecutive 8-byte slots -> coalesced stores).
 __device__ __forceinline__ void log_access(BlockVars* bv, unsigned long long* region, uint32_t front_cap,
@@ -241,13 +246,13 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   const GroupLayout G = group_layout(nthr, shw, ncode, nrows);
   uint32_t* regs = reinterpret_cast<uint32_t*>(gsm + G.regs);
   int32_t* sh = reinterpret_cast<int32_t*>(gsm + G.sh);
-  uint32_t* clk = reinterpret_cast<uint32_t*>(gsm + G.clk);
-  int32_t* rlo = reinterpret_cast<int32_t*>(gsm + G.rlo);
-  int32_t* rhi = reinterpret_cast<int32_t*>(gsm + G.rhi);
-  uint32_t* rsp = reinterpret_cast<uint32_t*>(gsm + G.rsp);
-  uint32_t* park = reinterpret_cast<uint32_t*>(gsm + G.park);
+  uint32_t* clk = reinterpret_cast<uint32_t*>(gsm + kGroupClk);
+  int32_t* rlo = reinterpret_cast<int32_t*>(gsm + kGroupRlo);
+  int32_t* rhi = reinterpret_cast<int32_t*>(gsm + kGroupRhi);
+  uint32_t* rsp = reinterpret_cast<uint32_t*>(gsm + kGroupRsp);
+  uint32_t* park = reinterpret_cast<uint32_t*>(gsm + kGroupPark);
   uint32_t* err = reinterpret_cast<uint32_t*>(gsm + G.err);
-  BlockVars* bv = reinterpret_cast<BlockVars*>(gsm + G.bv);
+  BlockVars* bv = reinterpret_cast<BlockVars*>(gsm + kGroupBv);
   int32_t* arena = A.arena + Ls->arena_off;
   const uint32_t arena_words = (uint32_t)Ls->arena_words;
   unsigned long long* region = A.log + Ls->log_base + (unsigned long long)block * log_cap;
@@ -279,8 +284,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   bool conv = true;
   uint32_t pn = Ls->entry;
   uint32_t n_instr = 0, n_gacc = 0;              // per lane: executed instructions, global accesses
-  const unsigned long long lane_rec = (unsigned long long)tid << 14;
-  unsigned long long epoch_rec = 0;              // epoch << 38
+  // a log record is built from 32-bit halves: low = addr << 24 | tid << 14 | kind << 12 | pc,
+  // high = epoch << 6 | addr >> 8
+  const uint32_t lane_rec = tid << 14;
+  uint32_t epoch_hi = 0;                         // epoch << 6
 
   for (;;) {  // barrier intervals
     bool limit = false, timeout = false;
@@ -337,7 +344,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (shared) {
               if (logging)
                 log_access(bv, region, front_cap, inb,
-                           epoch_rec | lane_rec | (unsigned long long)(K_R << 12 | p) | (unsigned long long)addr << 24,
+                           rec_of(epoch_hi, lane_rec | K_R << 12 | p, (uint32_t)addr),
                            lane);
             } else {
               n_gacc += act;
@@ -377,7 +384,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (shared) {
               if (logging)
                 log_access(bv, region, front_cap, inb,
-                           epoch_rec | lane_rec | (unsigned long long)(K_W << 12 | p) | (unsigned long long)addr << 24,
+                           rec_of(epoch_hi, lane_rec | K_W << 12 | p, (uint32_t)addr),
                            lane);
             } else {
               n_gacc += act;
@@ -400,7 +407,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (em) note_err(err, bv, p, w, em, lane);
             if (logging)
               log_access(bv, region, front_cap, inb,
-                         epoch_rec | lane_rec | (unsigned long long)(K_A << 12 | p) | (unsigned long long)addr << 24,
+                         rec_of(epoch_hi, lane_rec | K_A << 12 | p, (uint32_t)addr),
                          lane);
             break;
           }
@@ -528,7 +535,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     k = bv->k0;
     omin = 4u * k;                               // every clock was reset to 4 * k0
     epoch = bv->epoch;
-    epoch_rec = (unsigned long long)epoch << 38;
+    epoch_hi = epoch << 6;
     front_cap = log_cap - 2u * bv->n_misc;
   }
 

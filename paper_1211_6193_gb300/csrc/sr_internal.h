@@ -78,18 +78,22 @@ struct GroupLayout {
   uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, total;
 };
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+// The fixed-size arrays come first, at offsets known at compile time; the arrays whose
+// size depends on the launch follow.
+constexpr uint32_t kGroupClk = 0, kGroupRlo = 128, kGroupRhi = 256, kGroupRsp = 384, kGroupPark = 512,
+                   kGroupBv = 512 + 32 * 8 * 4, kGroupFixed = kGroupBv + 64;
 __host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode, uint32_t nrows) {
   GroupLayout g;
-  uint32_t o = 0;
+  g.clk = kGroupClk;
+  g.rlo = kGroupRlo;
+  g.rhi = kGroupRhi;
+  g.rsp = kGroupRsp;
+  g.park = kGroupPark;
+  g.bv = kGroupBv;
+  uint32_t o = kGroupFixed;
   g.regs = o; o += align16(nrows * nthr * 4u);
   g.sh = o;   o += align16(shw * 4u);
-  g.clk = o;  o += 32 * 4;
-  g.rlo = o;  o += 32 * 4;
-  g.rhi = o;  o += 32 * 4;
-  g.rsp = o;  o += 32 * 4;
-  g.park = o; o += 32 * 8 * 4;
   g.err = o;  o += align16(2u * (ncode + 1) * 4u);
-  g.bv = o;   o += 64;
   g.total = o;
   return g;
 }
