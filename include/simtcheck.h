@@ -21,8 +21,8 @@
  *     of a context is returned by sr_last_error().  On SR_E_INVAL nothing was enqueued.
  *   - Host buffers passed in are owned by the caller and only read (or, for fetch_*,
  *     written) during the call.  Device memory is owned by the library: it is obtained
- *     through the allocator given at sr_create (default: cudaMallocAsync on the stream
- *     of the call) and released by sr_free_batch / sr_destroy.
+ *     through the allocator given at sr_create (default: stream-ordered allocation from a
+ *     memory pool owned by the context) and released by sr_free_batch / sr_destroy.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  run_and_check only
  *     enqueues work; fetch_* and sr_batch_status synchronise the batch's stream.
  *   - Races, deadlocks, divergent barriers, out-of-bounds accesses, division by zero and
@@ -156,7 +156,9 @@ typedef struct {
   uint32_t log_budget_mb;    /* device memory for access logs resident at once (launches are
                                 processed in waves that fit); 0 = min(96 GB, half the free memory) */
   uint32_t report_cap;       /* initial report buffer (records); grown on demand; 0 = 1 << 20 */
-  const sr_allocator* allocator;  /* NULL = cudaMallocAsync / cudaFreeAsync */
+  const sr_allocator* allocator;  /* NULL = stream-ordered allocation from a memory pool the
+                                     context owns (freed memory is kept for reuse until
+                                     sr_destroy) */
   uint32_t check_variant;    /* race-check kernel shape, 1..SR_CHECK_VARIANTS (consumer threads,
                                 records per stage, stages, CTAs per SM); 0 = the default */
 } sr_opts;

@@ -46,6 +46,7 @@ struct sr_ctx {
   int device = 0;
   int sms = 0;
   size_t smem_optin = 0;
+  cudaMemPool_t pool = nullptr;   // without a caller allocator: this context's own memory pool
 };
 
 struct sr_batch {
@@ -100,7 +101,7 @@ void* dev_alloc(sr_ctx* c, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
   if (c->custom_alloc) return c->alloc.alloc(c->alloc.user, bytes, s);
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+  if (cudaMallocFromPoolAsync(&p, bytes, c->pool, s) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -269,8 +270,27 @@ int sr_create(sr_ctx** out, const sr_opts* opts) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   c->smem_optin = (size_t)optin;
   if (e == cudaSuccess) e = sr::init_kernel_attributes((uint32_t)optin);
+  if (e == cudaSuccess && !c->custom_alloc) {
+    // a pool of its own that keeps freed memory (batch after batch reuses it instead of
+    // returning it to the driver at every synchronisation)
+    cudaMemPoolProps pp{};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = c->device;
+    e = cudaMemPoolCreate(&c->pool, &pp);
+    if (e == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    // memory freed on one stream is reused on that stream only: reuse across streams would
+    // make batches on different streams wait for each other
+    int no = 0;
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowOpportunistic, &no);
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
     return fail(nullptr, SR_E_CUDA, "device setup failed: %s", cudaGetErrorString(e));
   }
@@ -278,7 +298,11 @@ int sr_create(sr_ctx** out, const sr_opts* opts) {
   return SR_OK;
 }
 
-void sr_destroy(sr_ctx* c) { delete c; }
+void sr_destroy(sr_ctx* c) {
+  if (!c) return;
+  if (c->pool) cudaMemPoolDestroy(c->pool);   // released once frees still in flight complete
+  delete c;
+}
 
 const char* sr_last_error(sr_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 

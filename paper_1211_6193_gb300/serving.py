@@ -165,7 +165,8 @@ class Server:
         self.budget = log_budget_bytes
         self.max_inflight = max_inflight
         self.max_batch_jobs = max_batch_jobs
-        # one context: the server loop is the only host thread using it
+        # one context: the server loop is the only host thread using it (device memory from
+        # PyTorch's caching allocator: a freed micro-batch costs no CUDA call)
         self.ctx = binding.Context(mode=mode, log_budget_mb=max(1, log_budget_bytes >> 20))
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
 

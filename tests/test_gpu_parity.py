@@ -273,6 +273,20 @@ def test_report_buffer_grown_after_a_one_wave_run(B, use_graph):
             assert all(np.array_equal(x, w) for x, w in zip(b.fetch_all_memory(), want.arenas))
 
 
+def test_context_memory_pool(B):
+    """Without a caller allocator the context allocates from its own pool: batch after batch
+    on one context (memory reused), both modes, results as the oracle's."""
+    progs = families.batch(n_programs=12, seed=44, max_grid=10, bug_rate=0.5)
+    want = oracle.run(progs)
+    for mode in MODES:
+        with B.Context(mode=mode, torch_allocator=False) as ctx:
+            for _ in range(3):
+                with ctx.load_programs(progs) as b:
+                    b.run_and_check()
+                    assert [tuple(int(x) for x in r) for r in b.fetch_reports()] == want.report_tuples()
+                    assert all(np.array_equal(x, w) for x, w in zip(b.fetch_all_memory(), want.arenas))
+
+
 def test_log_overflow_is_reported_not_silent(B):
     a = ir.Asm()
     a.s2r(ir.r2, ir.TID).mov(ir.r3, 50).label("l").sts(ir.r2, ir.r3).sub(ir.r3, ir.r3, 1).brnz(ir.r3, "l").exit()
