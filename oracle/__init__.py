@@ -25,7 +25,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 # report kinds / status bits (same numbers as simt_oracle.h)
-RACE, DIVERGENCE, DEADLOCK, STEP_LIMIT, ERR_OOB_SHARED, ERR_OOB_GLOBAL, ERR_DIV0 = range(1, 8)
+RACE, DIVERGENCE, DEADLOCK, STEP_LIMIT, ERR_OOB_SHARED, ERR_OOB_GLOBAL, ERR_DIV0, ERR_UNINIT_SHARED = range(1, 9)
 CLS_WW, CLS_WR, CLS_WA, CLS_AR = 1, 2, 4, 8
 ST_DEADLOCK, ST_STEP_LIMIT = 1, 2
 
@@ -50,7 +50,8 @@ class _Program(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("round_budget", C.c_uint32), ("check_races", C.c_uint32), ("schedule", C.c_uint32),
-                ("nthreads", C.c_uint32), ("check_interblock", C.c_uint32), ("max_blocks", C.c_uint32)]
+                ("nthreads", C.c_uint32), ("check_interblock", C.c_uint32), ("max_blocks", C.c_uint32),
+                ("check_uninit", C.c_uint32)]
 
 
 class _Result(C.Structure):
@@ -104,7 +105,8 @@ class OracleResult:
 
 
 def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, schedule: str = "lockstep",
-        nthreads: int = 1, check_interblock: bool = False, max_blocks: int = 0) -> OracleResult:
+        nthreads: int = 1, check_interblock: bool = False, max_blocks: int = 0,
+        check_uninit: bool = False) -> OracleResult:
     """Run ``programs`` (``workloads.ir.Program``) through the oracle."""
     lib = _load()
     keep = []
@@ -127,7 +129,7 @@ def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, sch
         progs[i].launches, progs[i].nlaunches = C.addressof(ls), len(p.launches)
         progs[i].arena, progs[i].arena_words = (arena.ctypes.data if arena.size else None), arena.size
     opts = _Opts(round_budget, int(check_races), {"lockstep": 0, "sequential": 1}[schedule], nthreads,
-                 int(check_interblock), max_blocks)
+                 int(check_interblock), max_blocks, int(check_uninit))
     res = _Result()
     rc = lib.orc_run(C.addressof(progs), len(programs), C.byref(opts), C.byref(res))
     if rc != 0:

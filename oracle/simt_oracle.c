@@ -89,6 +89,8 @@ typedef struct {
   int32_t* sh;                   /* shared array of this block */
   uint32_t* err_cnt; uint32_t* err_min;   /* per pc, current epoch */
   uint8_t err_any;
+  uint8_t* written;              /* shared words some thread of the block stored or added to */
+  uint32_t* un_cnt; uint32_t* un_min;     /* loads of unwritten words, per pc, current epoch */
   acc_vec acc;                   /* accesses of the current epoch */
   st_vec sst, gst, ats;          /* deferred shared stores, global stores, atomics (round) */
   uint32_t epoch;
@@ -104,6 +106,11 @@ static void reg_write(block_t* B, uint32_t t, uint32_t r, int32_t v) {
 static void note_err(block_t* B, uint32_t pc, uint32_t t) {
   B->err_cnt[pc]++;
   if (t < B->err_min[pc]) B->err_min[pc] = t;
+  B->err_any = 1;
+}
+static void note_uninit(block_t* B, uint32_t pc, uint32_t t) {
+  B->un_cnt[pc]++;
+  if (t < B->un_min[pc]) B->un_min[pc] = t;
   B->err_any = 1;
 }
 static void note_global(block_t* B, int32_t addr, int is_write) {
@@ -202,6 +209,7 @@ static void exec_one(block_t* B, uint32_t t, uint32_t pc) {
       else {
         v = B->sh[addr];                   /* deferred writes: pre-round value */
         acc_push(&B->acc, (access_t){(uint32_t)addr, t, K_R, pc});
+        if (B->C->O->check_uninit && !B->written[addr]) note_uninit(B, pc, t);
       }
       reg_write(B, t, d, v);
       break;
@@ -215,6 +223,7 @@ static void exec_one(block_t* B, uint32_t t, uint32_t pc) {
       } else {
         if (B->deferred) st_push(&B->ats, addr, vb); else B->sh[addr] = add32(B->sh[addr], vb);
       }
+      if (!B->deferred) B->written[addr] = 1;   /* in rounds: when the round's writes apply */
       break;
     }
     case ORC_LDG: {
@@ -264,6 +273,9 @@ static void exec_round(block_t* B) {
   for (uint64_t i = 0; i < B->gst.n; ++i) B->C->P->arena[B->gst.v[i].addr] = B->gst.v[i].val;
   for (uint64_t i = 0; i < B->ats.n; ++i)
     B->sh[B->ats.v[i].addr] = add32(B->sh[B->ats.v[i].addr], B->ats.v[i].val);
+  /* the words this round stored to or added to count as written from the next round on */
+  for (uint64_t i = 0; i < B->sst.n; ++i) B->written[B->sst.v[i].addr] = 1;
+  for (uint64_t i = 0; i < B->ats.n; ++i) B->written[B->ats.v[i].addr] = 1;
 }
 
 static int cmp_access(const void* x, const void* y) {
@@ -326,6 +338,11 @@ static void finish_epoch(block_t* B) {
       emit(B, kind, pc, B->err_min[pc], B->err_cnt[pc]);
       B->err_cnt[pc] = 0; B->err_min[pc] = UINT32_MAX;
     }
+    for (uint32_t pc = 0; pc < P->ncode; ++pc) {
+      if (!B->un_cnt[pc]) continue;
+      emit(B, ORC_REP_ERR_UNINIT_SHARED, pc, B->un_min[pc], B->un_cnt[pc]);
+      B->un_cnt[pc] = 0; B->un_min[pc] = UINT32_MAX;
+    }
     B->err_any = 0;
   }
 }
@@ -379,7 +396,10 @@ static void run_block(launch_ctx* C, uint32_t block) {
   B.sh = calloc(B.shw ? B.shw : 1, sizeof(int32_t));          /* shared memory starts at zero */
   B.err_cnt = calloc(P->ncode + 1, sizeof(uint32_t));
   B.err_min = malloc((P->ncode + 1) * sizeof(uint32_t));
-  for (uint32_t i = 0; i <= P->ncode; ++i) B.err_min[i] = UINT32_MAX;
+  B.un_cnt = calloc(P->ncode + 1, sizeof(uint32_t));
+  B.un_min = malloc((P->ncode + 1) * sizeof(uint32_t));
+  for (uint32_t i = 0; i <= P->ncode; ++i) B.err_min[i] = B.un_min[i] = UINT32_MAX;
+  B.written = calloc(B.shw ? B.shw : 1, 1);
   uint32_t entry = P->kernel_entry[L->kernel];
   for (uint32_t t = 0; t < B.n; ++t) {
     B.pc[t] = entry; B.st[t] = ST_RUN;
@@ -411,7 +431,7 @@ static void run_block(launch_ctx* C, uint32_t block) {
   }
   C->rounds += rounds;
   free(B.pc); free(B.st); free(B.wpc); free(B.bk); free(B.bp); free(B.bd); free(B.regs); free(B.sh);
-  free(B.err_cnt); free(B.err_min); free(B.acc.v); free(B.sst.v); free(B.gst.v); free(B.ats.v);
+  free(B.err_cnt); free(B.err_min); free(B.un_cnt); free(B.un_min); free(B.written); free(B.acc.v); free(B.sst.v); free(B.gst.v); free(B.ats.v);
 }
 
 /* ------------------------------------------------------------ validation */

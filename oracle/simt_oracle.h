@@ -55,7 +55,8 @@ enum {
 /* report kinds (the library's public header defines the same numbers) */
 enum {
   ORC_REP_RACE = 1, ORC_REP_DIVERGENCE = 2, ORC_REP_DEADLOCK = 3, ORC_REP_STEP_LIMIT = 4,
-  ORC_REP_ERR_OOB_SHARED = 5, ORC_REP_ERR_OOB_GLOBAL = 6, ORC_REP_ERR_DIV0 = 7
+  ORC_REP_ERR_OOB_SHARED = 5, ORC_REP_ERR_OOB_GLOBAL = 6, ORC_REP_ERR_DIV0 = 7,
+  ORC_REP_ERR_UNINIT_SHARED = 8
 };
 /* race class bits (field c bits 24..27) */
 enum { ORC_CLS_WW = 1, ORC_CLS_WR = 2, ORC_CLS_WA = 4, ORC_CLS_AR = 8 };
@@ -82,6 +83,7 @@ typedef struct {
   uint32_t nthreads;         /* host threads over blocks of one launch (0/1 = serial) */
   uint32_t check_interblock; /* 1 = flag global words shared between blocks of a launch */
   uint32_t max_blocks;       /* >0: run only blocks [0, max_blocks) of each launch (timing samples) */
+  uint32_t check_uninit;     /* 1 = report shared loads of words no thread of the block wrote */
 } orc_opts;
 
 typedef struct {

@@ -49,6 +49,8 @@ MUTANTS = {
                           "if (B->bk[t] == 1) reg_write(B, t, B->bd[t], nP > 0);"),
     "plain_barrier_counts_as_true": ("B->bp[t] = base != ORC_BAR && va != 0;",
                                      "B->bp[t] = base == ORC_BAR || va != 0;"),
+    "written_marked_at_issue": ("if (!B->deferred) B->written[addr] = 1;", "B->written[addr] = 1;"),
+    "atomics_do_not_initialise": ("  for (uint64_t i = 0; i < B->ats.n; ++i) B->written[B->ats.v[i].addr] = 1;\n", ""),
     "warps_of_16": (
         "uint32_t lo = 32 * w, hi = lo + 32 < B->n ? lo + 32 : B->n;",
         "uint32_t lo = 16 * w, hi = lo + 16 < B->n ? lo + 16 : B->n; if (lo >= B->n) continue;"),

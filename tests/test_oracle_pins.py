@@ -325,6 +325,57 @@ def test_reducing_barrier_deadlock_and_race_interval():
     assert r.status[0] & oracle.ST_DEADLOCK and list(r.arenas[0]) == [-1] * 64
 
 
+# ------------------------------------------------------------------ uninitialised shared reads
+def test_uninitialised_reads_hand_values():
+    """Warp 0 stores sh[tid]; after the barrier every thread loads sh[tid]: the 32 loads of
+    warp 1 read words no thread wrote (one record at the load's pc: min tid 32, count 32).
+    The check is off unless asked for."""
+    a = ir.Asm()
+    a.s2r(ir.r2, ir.TID).shr(ir.r3, ir.r2, 5).brnz(ir.r3, "skip").sts(ir.r2, ir.r2).label("skip").bar()
+    a.lds(ir.r4, ir.r2).stg(ir.r2, ir.r4).exit()
+    p = ir.Program(a.assemble(), [0], [ir.Launch(0, 2, 64, 64, ())], np.zeros(64, np.int32))
+    pc = find_pc(p.code, lambda op, d, a_, b, imm: op == ir.LDS)[0]
+    r = oracle.run([p], check_uninit=True)
+    assert reports_of(r) == [(oracle.ERR_UNINIT_SHARED, 0, 0, blk, 1, pc, 32, 32) for blk in (0, 1)]
+    assert reports_of(oracle.run([p])) == []
+
+
+def test_uninitialised_reads_follow_the_round_rule():
+    """A load sees the writes of earlier rounds only: warp 1 loading sh[0] in the round
+    where warp 0 stores it reads an unwritten word; a round later it does not.  Atomic
+    adds count as writes; a store of a later interval does not help an earlier load."""
+    def prog(delay):
+        a = ir.Asm()
+        a.s2r(ir.r2, ir.TID).shr(ir.r3, ir.r2, 5).mov(ir.r4, 5).brnz(ir.r3, "w1")
+        a.sts(ir.RZ, ir.r4).bra("end")
+        a.label("w1")
+        for _ in range(delay):
+            a.mov(ir.r9, 0)
+        a.lds(ir.r5, ir.RZ).label("end").exit()
+        return ir.Program(a.assemble(), [0], [ir.Launch(0, 1, 64, 1, ())], np.zeros(1, np.int32))
+    r0 = reports_of(oracle.run([prog(0)], check_uninit=True))
+    assert [t[0] for t in r0] == [oracle.RACE, oracle.ERR_UNINIT_SHARED] and r0[1][6:] == (32, 32)
+    assert [t[0] for t in reports_of(oracle.run([prog(1)], check_uninit=True))] == [oracle.RACE]
+    a = ir.Asm()                        # ATOMS initialises; a later-interval store does not count
+    a.s2r(ir.r2, ir.TID).mov(ir.r3, 1).atoms(ir.RZ, ir.r3).bar().lds(ir.r4, ir.RZ).lds(ir.r5, ir.RZ, 1)
+    a.bar().brnz(ir.r2, "x").sts(ir.RZ, ir.r3, 1).label("x").exit()
+    p = ir.Program(a.assemble(), [0], [ir.Launch(0, 1, 40, 2, ())], np.zeros(1, np.int32))
+    pc = find_pc(p.code, lambda op, d, a_, b, imm: op == ir.LDS)[1]
+    assert reports_of(oracle.run([p], check_uninit=True)) == [(oracle.ERR_UNINIT_SHARED, 0, 0, 0, 1, pc, 0, 40)]
+
+
+def test_uninitialised_reads_only_in_planted_bugs():
+    """No bug-free generated program (all families) reads a shared word it did not write;
+    every report comes from a program with a planted off-by-one or missing barrier."""
+    progs = families.batch(n_programs=96, seed=8, max_grid=3, bug_rate=0.4)
+    progs += [families.reduction_plain(n_blocks=3), stencil2d.program(log2w=6, steps=2, buggy_launch=None)]
+    r = oracle.run(progs, check_uninit=True)
+    hit = {t[1] for t in reports_of(r, oracle.ERR_UNINIT_SHARED)}
+    assert hit and all(progs[i].meta.get("bug") in ("off_by_one", "missing_barrier") for i in hit)
+    # and the other reports are exactly those of the run without the check
+    assert [t for t in r.report_tuples() if t[0] != oracle.ERR_UNINIT_SHARED] == oracle.run(progs).report_tuples()
+
+
 # ------------------------------------------------------------------ exhaustive interleavings
 @pytest.mark.parametrize("nthreads,nsteps,count,nwords,bar_rate",
                          [(2, 6, 40, 3, 0.25), (3, 4, 40, 3, 0.25), (3, 6, 16, 8, 0.6)])
