@@ -99,7 +99,9 @@ enum {
   SR_REP_STEP_LIMIT = 4,     /* a = rounds executed, b = runnable threads, c = their lowest pc */
   SR_REP_ERR_OOB_SHARED = 5, /* a = pc, b = lowest tid, c = thread executions in the interval */
   SR_REP_ERR_OOB_GLOBAL = 6, /* same fields */
-  SR_REP_ERR_DIV0 = 7        /* same fields */
+  SR_REP_ERR_DIV0 = 7,       /* same fields */
+  SR_REP_ERR_UNINIT_SHARED = 8 /* (with opts.check_uninit) a shared load of a word no thread of the
+                                  block stored or added to in an earlier round; same fields */
 };
 enum { SR_CLS_WW = 1, SR_CLS_WR = 2, SR_CLS_WA = 4, SR_CLS_AR = 8 };
 
@@ -161,6 +163,8 @@ typedef struct {
                                      sr_destroy) */
   uint32_t check_variant;    /* race-check kernel shape, 1..SR_CHECK_VARIANTS (consumer threads,
                                 records per stage, stages, CTAs per SM); 0 = the default */
+  uint32_t check_uninit;     /* 1 = also report loads of shared words not yet written
+                                (SR_REP_ERR_UNINIT_SHARED); 0 = off */
 } sr_opts;
 
 #define SR_CHECK_VARIANTS 4

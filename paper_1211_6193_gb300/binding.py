@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsimtcheck.so")
 SR_OK, SR_E_INVAL, SR_E_NOMEM, SR_E_CUDA, SR_E_TIMEOUT, SR_E_RANGE = 0, -1, -2, -3, -4, -5
 SR_ALL_PROGRAMS = 0xFFFFFFFF
 MODE_PLAIN, MODE_BATCHED = 0, 1
-RACE, DIVERGENCE, DEADLOCK, STEP_LIMIT, ERR_OOB_SHARED, ERR_OOB_GLOBAL, ERR_DIV0 = range(1, 8)
+RACE, DIVERGENCE, DEADLOCK, STEP_LIMIT, ERR_OOB_SHARED, ERR_OOB_GLOBAL, ERR_DIV0, ERR_UNINIT_SHARED = range(1, 9)
 ST_DEADLOCK, ST_STEP_LIMIT, ST_LOG_OVERFLOW, ST_INTERNAL = 1, 2, 4, 8
 REPORT_DTYPE = np.dtype([(n, "<u4") for n in ("kind", "prog", "launch", "block", "epoch", "a", "b", "c")])
 
@@ -63,7 +63,8 @@ class sr_opts(C.Structure):
                 ("ctas_per_sm", C.c_uint32), ("loop_log_records", C.c_uint32),
                 ("interp_variant", C.c_uint32), ("use_graph", C.c_uint32), ("profile", C.c_uint32),
                 ("spin_limit", C.c_uint32), ("log_budget_mb", C.c_uint32), ("report_cap", C.c_uint32),
-                ("allocator", C.POINTER(sr_allocator)), ("check_variant", C.c_uint32)]
+                ("allocator", C.POINTER(sr_allocator)), ("check_variant", C.c_uint32),
+                ("check_uninit", C.c_uint32)]
 
 
 class sr_stats(C.Structure):
@@ -208,7 +209,7 @@ class Context:
     def __init__(self, check_races: bool = True, round_budget: int = 0, mode: str = "plain", ctas_per_sm: int = 0,
                  loop_log_records: int = 0, interp_variant: int = 0, use_graph: bool = False,
                  profile: bool = False, spin_limit: int = 0, log_budget_mb: int = 0, report_cap: int = 0,
-                 torch_allocator: bool = True, check_variant: int = 0):
+                 torch_allocator: bool = True, check_variant: int = 0, check_uninit: bool = False):
         self.lib = load_library()
         self.allocator = TorchAllocator() if torch_allocator else None
         o = sr_opts()
@@ -218,6 +219,7 @@ class Context:
         o.use_graph, o.profile, o.spin_limit = int(use_graph), int(profile), spin_limit
         o.log_budget_mb, o.report_cap = log_budget_mb, report_cap
         o.check_variant = check_variant
+        o.check_uninit = int(check_uninit)
         if self.allocator is not None:
             o.allocator = C.pointer(self.allocator.struct)
         self.opts = o

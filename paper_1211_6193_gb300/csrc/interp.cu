@@ -200,14 +200,19 @@ __device__ void push_misc(BlockVars* bv, unsigned long long* region, uint32_t lo
 }
 
 // Error records of the interval, ordered by (kind, pc); run by one whole warp.
-__device__ void flush_errors(BlockVars* bv, uint32_t* err, const uint2* ir, uint32_t ncode,
+__device__ void flush_errors(BlockVars* bv, uint32_t* err, uint32_t* un, const uint2* ir, uint32_t ncode,
                              unsigned long long* region, uint32_t log_cap, uint32_t epoch, uint32_t lane) {
-  for (uint32_t kind = SR_REP_ERR_OOB_SHARED; kind <= SR_REP_ERR_DIV0; ++kind) {
+  const uint32_t last = un ? SR_REP_ERR_UNINIT_SHARED : SR_REP_ERR_DIV0;
+  for (uint32_t kind = SR_REP_ERR_OOB_SHARED; kind <= last; ++kind) {
     for (uint32_t base = 0; base < ncode; base += 32) {
       const uint32_t pc = base + lane;
       uint32_t cnt = 0, mt = 0;
       bool hit = false;
-      if (pc < ncode) {
+      if (pc < ncode && kind == SR_REP_ERR_UNINIT_SHARED) {
+        cnt = un[2 * pc];
+        hit = cnt != 0;
+        mt = un[2 * pc + 1];
+      } else if (pc < ncode) {
         cnt = err[2 * pc];
         if (cnt) {
           const uint32_t op = ir[pc].x & 0x3Fu;
@@ -231,6 +236,10 @@ __device__ void flush_errors(BlockVars* bv, uint32_t* err, const uint2* ir, uint
   for (uint32_t pc = lane; pc <= ncode; pc += 32) {
     err[2 * pc] = 0;
     err[2 * pc + 1] = kInf;
+    if (un) {
+      un[2 * pc] = 0;
+      un[2 * pc + 1] = kInf;
+    }
   }
   __syncwarp();
   if (lane == 0) bv->err_dirty = 0;
@@ -243,7 +252,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   const uint32_t nthr = nw * 32;
   const uint32_t tid = w * 32 + lane;
   const uint32_t bdim = Ls->bdim, shw = Ls->shw, ncode = Ls->ncode, log_cap = Ls->log_cap, nrows = Ls->nrows;
-  const GroupLayout G = group_layout(nthr, shw, ncode, nrows);
+  const bool uninit = Ls->uninit != 0;
+  const GroupLayout G = group_layout(nthr, shw, ncode, nrows, Ls->uninit);
   uint32_t* regs = reinterpret_cast<uint32_t*>(gsm + G.regs);
   int32_t* sh = reinterpret_cast<int32_t*>(gsm + G.sh);
   uint32_t* clk = reinterpret_cast<uint32_t*>(gsm + kGroupClk);
@@ -252,6 +262,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   uint32_t* rsp = reinterpret_cast<uint32_t*>(gsm + kGroupRsp);
   uint32_t* park = reinterpret_cast<uint32_t*>(gsm + kGroupPark);
   uint32_t* err = reinterpret_cast<uint32_t*>(gsm + G.err);
+  uint32_t* un = reinterpret_cast<uint32_t*>(gsm + G.un);      // with `uninit` only
+  uint32_t* wb = reinterpret_cast<uint32_t*>(gsm + G.wb);      // with `uninit` only
   BlockVars* bv = reinterpret_cast<BlockVars*>(gsm + kGroupBv);
   int32_t* arena = A.arena + Ls->arena_off;
   const uint32_t arena_words = (uint32_t)Ls->arena_words;
@@ -266,6 +278,13 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   for (uint32_t i = tid; i <= ncode; i += nthr) {
     err[2 * i] = 0;
     err[2 * i + 1] = kInf;
+  }
+  if (uninit) {
+    for (uint32_t i = tid; i <= ncode; i += nthr) {
+      un[2 * i] = 0;
+      un[2 * i + 1] = kInf;
+    }
+    for (uint32_t i = tid; i < (shw + 31u) / 32u; i += nthr) wb[i] = 0;
   }
   if (tid == 0) {
     bv->cursor = 0;
@@ -341,6 +360,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (wr) myregs[d * nthr] = (uint32_t)v;
             const uint32_t em = __ballot_sync(FULL, act && !inb);
             if (em) note_err(err, bv, p, w, em, lane);
+            if (shared && uninit) {                // words no store or atomic of an earlier round wrote
+              const uint32_t um = __ballot_sync(FULL, inb && !((wb[addr >> 5] >> (addr & 31)) & 1u));
+              if (um) note_err(un, bv, p, w, um, lane);
+            }
             if (shared) {
               if (logging)
                 log_access(bv, region, front_cap, inb,
@@ -379,6 +402,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
               else
                 arena[addr] = vb;
             }
+            if (shared && uninit && inb) atomicOr(&wb[addr >> 5], 1u << (addr & 31));
             const uint32_t em = __ballot_sync(FULL, act && !inb);
             if (em) note_err(err, bv, p, w, em, lane);
             if (shared) {
@@ -403,6 +427,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
               }
             }
             if (inb) atomicAdd(&sh[addr], vb);
+            if (uninit && inb) atomicOr(&wb[addr >> 5], 1u << (addr & 31));
             const uint32_t em = __ballot_sync(FULL, act && !inb);
             if (em) note_err(err, bv, p, w, em, lane);
             if (logging)
@@ -506,7 +531,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       }
       if (lane == 0 && kind) push_misc(bv, region, log_cap, kind, ep, a, b, c);
       __syncwarp();
-      if (bv->err_dirty) flush_errors(bv, err, ir, ncode, region, log_cap, ep, lane);
+      if (bv->err_dirty) flush_errors(bv, err, uninit ? un : nullptr, ir, ncode, region, log_cap, ep, lane);
       if (lane == 0) {
         bv->decision = dec;
         bv->status |= stbits;
@@ -650,7 +675,7 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
 
 uint32_t interp_plain_smem(const LaunchDev& L) {
   const uint32_t nthr = ((L.bdim + 31) / 32) * 32;
-  return L.ir_bytes + group_layout(nthr, L.shw, L.ncode, L.nrows).total;
+  return L.ir_bytes + group_layout(nthr, L.shw, L.ncode, L.nrows, L.uninit).total;
 }
 
 // dynamic shared memory may use what the kernel's static shared memory leaves of the opt-in limit

@@ -380,7 +380,8 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       d.ir_bytes = sr::ir_smem_bytes(P.ncode);
       d.nrows = rm.nrows;
       const uint32_t nw = (L.block_dim + 31) / 32;
-      d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode, rm.nrows).total;
+      d.uninit = o.check_uninit ? 1u : 0u;
+      d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode, rm.nrows, d.uninit).total;
       if (d.ir_bytes + d.group_bytes > smem_budget) {
         delete b;
         return fail(c, SR_E_INVAL, "program %u launch %u: %u bytes of shared memory needed, %u available", i, l,

@@ -46,6 +46,7 @@ struct LaunchDev {
   uint32_t groups, group_bytes;          // batched mode: blocks per CTA, smem per block
   uint32_t ir_bytes, nrows;              // smem bytes of the staged code; register rows (zero row last)
   uint32_t check_group, check_item;      // race check: blocks per work item, index of the first item
+  uint32_t uninit, pad0;                 // 1 = report shared loads of words no thread wrote
 };
 
 // Per simulated block, written by the interpreter (n_log, n_misc, flags) and the checker (n_race).
@@ -75,14 +76,16 @@ struct RunArgs {
 
 // Shared-memory footprint of one simulated block in the interpreter.
 struct GroupLayout {
-  uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, total;
+  uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, un, wb, total;
 };
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 // The fixed-size arrays come first, at offsets known at compile time; the arrays whose
 // size depends on the launch follow.
 constexpr uint32_t kGroupClk = 0, kGroupRlo = 128, kGroupRhi = 256, kGroupRsp = 384, kGroupPark = 512,
                    kGroupBv = 512 + 32 * 8 * 4, kGroupFixed = kGroupBv + 64;
-__host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode, uint32_t nrows) {
+// With `uninit`: per-pc counters of loads of unwritten words, and the bitmap of written words.
+__host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode, uint32_t nrows,
+                                                   uint32_t uninit) {
   GroupLayout g;
   g.clk = kGroupClk;
   g.rlo = kGroupRlo;
@@ -94,6 +97,11 @@ __host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw,
   g.regs = o; o += align16(nrows * nthr * 4u);
   g.sh = o;   o += align16(shw * 4u);
   g.err = o;  o += align16(2u * (ncode + 1) * 4u);
+  g.un = g.wb = 0;
+  if (uninit) {
+    g.un = o; o += align16(2u * (ncode + 1) * 4u);
+    g.wb = o; o += align16((shw + 31u) / 32u * 4u);
+  }
   g.total = o;
   return g;
 }

@@ -222,6 +222,37 @@ def test_every_check_variant(B, variant):
             assert_parity(B, progs, mode, check_variant=variant)
 
 
+def _uninit_programs():
+    out = []
+    a = ir.Asm()     # warp 0 writes, everyone reads after the barrier
+    a.s2r(ir.r2, ir.TID).shr(ir.r3, ir.r2, 5).brnz(ir.r3, "skip").sts(ir.r2, ir.r2).label("skip").bar()
+    a.lds(ir.r4, ir.r2).stg(ir.r2, ir.r4).exit()
+    out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 3, 100, 100, ())], np.zeros(100, np.int32)))
+    for delay in (0, 1, 3):   # a load in the same round as the store, one and three rounds later
+        a = ir.Asm()
+        a.s2r(ir.r2, ir.TID).shr(ir.r3, ir.r2, 5).mov(ir.r4, 5).brnz(ir.r3, "w1").sts(ir.RZ, ir.r4).bra("end")
+        a.label("w1")
+        for _ in range(delay):
+            a.mov(ir.r9, 0)
+        a.lds(ir.r5, ir.RZ).label("end").exit()
+        out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 2, 64, 1, ())], np.zeros(1, np.int32)))
+    a = ir.Asm()     # atomics initialise; loads of a word written only in a later interval
+    a.s2r(ir.r2, ir.TID).mov(ir.r3, 1).atoms(ir.RZ, ir.r3).bar().lds(ir.r4, ir.RZ).lds(ir.r5, ir.RZ, 1)
+    a.lds(ir.r6, ir.r2, 2).bar().brnz(ir.r2, "x").sts(ir.RZ, ir.r3, 1).label("x").exit()
+    out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, 2, 40, 64, ())], np.zeros(1, np.int32)))
+    return out
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_uninitialised_shared_reads(B, mode):
+    groups = [_uninit_programs(), families.batch(n_programs=40, seed=8, max_grid=6, bug_rate=0.5),
+              [families.reduction_plain(n_blocks=6, bdim=512, seed=3, omit_level=None)]]
+    for progs in groups:
+        got, _ = assert_parity(B, progs, mode, oracle_kw={"check_uninit": True}, check_uninit=True)
+    assert any(r[0] == oracle.ERR_UNINIT_SHARED for r in assert_parity(
+        B, _uninit_programs(), mode, oracle_kw={"check_uninit": True}, check_uninit=True)[0].report_tuples())
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_reducing_barriers(B, mode):
     """__syncthreads_and/_or/_count: predicates over full and partial warps, reducing and
