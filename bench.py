@@ -8,7 +8,8 @@ every barrier interval, barrier checks, canonical report ordering.
 
   value  : checked shared accesses / s with the programs resident on the device
   e2e    : the same metric through the C ABI from pinned host buffers, per step
-           load_programs (H2D) + run_and_check + fetch_reports + fetch_memory (D2H)
+           load_programs (H2D) + run_and_check + fetch_reports + fetch_memory of every
+           program (D2H)
   roofline, cpu_baseline, clocks: see the design doc (measurement section)
 
 Other workloads (--workload): ``batched`` = 4096 seed-generated programs (batched and
@@ -344,31 +345,35 @@ def run_native(args):
                             "traffic": traffic_per_launch(check_kernel(opts.get("check_variant", 0)), csha,
                                                           nblocks)}}
 
-    # ---- end to end through the C ABI from pinned host buffers (single-program workloads)
-    e2e = None
-    if args.workload != "batched":
-        prog = progs[0]
-        arena_pinned = torch.empty(prog.global_init.size, dtype=torch.int32, pin_memory=True)
-        arena_pinned.numpy()[:] = prog.global_init
-        prog_pinned = type(prog)(prog.code, prog.kernel_entry, prog.launches, arena_pinned.numpy(), prog.name)
-        out_arena = torch.empty(prog.global_init.size, dtype=torch.int32, pin_memory=True).numpy()
-        h2d = prog.global_init.nbytes + prog.code.nbytes
-        d2h = out_arena.nbytes + n_reports * 32
-        times = []
-        ctx_e2e = binding.Context(report_cap=max(16, n_reports), **opts)
-        for i in range(1 + min(args.steps, 5)):
-            barrier()
-            t0 = time.perf_counter()
-            with ctx_e2e.load_programs([prog_pinned]) as b:
-                b.run_and_check()
-                b.fetch_reports()
-                b.fetch_memory(0, out_arena)
-            torch.cuda.synchronize()
-            if i:
-                times.append(time.perf_counter() - t0)
-        ctx_e2e.close()
-        e2e = {"value": world * st.shared_accesses / statistics.mean(times), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    # ---- end to end through the C ABI from pinned host buffers: per step load_programs (the
+    # programs' code and initial arenas host -> device), run_and_check, fetch_reports and one
+    # fetch of every final arena (device -> host)
+    sizes = [p.global_init.size for p in progs]
+    pin = torch.empty(max(1, sum(sizes)), dtype=torch.int32, pin_memory=True).numpy()
+    progs_pinned, off = [], 0
+    for p, n in zip(progs, sizes):
+        v = pin[off:off + n]
+        v[:] = p.global_init
+        progs_pinned.append(type(p)(p.code, p.kernel_entry, p.launches, v, p.name))
+        off += n
+    h2d = sum(p.global_init.nbytes + p.code.nbytes for p in progs)
+    d2h = 4 * sum((n + 3) & ~3 for n in sizes) + 32 * n_reports
+    times = []
+    ctx_e2e = binding.Context(report_cap=max(16, n_reports), **opts)
+    for i in range(1 + min(args.steps, 5)):
+        barrier()
+        t0 = time.perf_counter()
+        with ctx_e2e.load_programs(progs_pinned) as b:
+            b.run_and_check()
+            b.fetch_reports(pinned=True)
+            b.fetch_all_memory(pinned=True)
+        torch.cuda.synchronize()
+        if i:
+            times.append(time.perf_counter() - t0)
+    ctx_e2e.close()
+    del pin, progs_pinned
+    e2e = {"value": world * st.shared_accesses / statistics.mean(times), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
