@@ -10,7 +10,11 @@ every barrier interval, barrier checks, canonical report ordering.
   e2e    : the same metric through the C ABI from pinned host buffers, per step
            load_programs (H2D) + run_and_check + fetch_reports + fetch_memory of every
            program (D2H)
-  roofline, cpu_baseline, clocks: see the design doc (measurement section)
+  roofline     : the interpreter against the int32 lane rate (152 SMs x 128 lanes x clock)
+                 and the race check against the measured HBM bandwidth (8 B per logged
+                 access + 16 B per race entry), each from its own CUDA-event stage time
+  cpu_baseline : the CPU oracle on the host cores, on a bounded block sample
+  clocks       : nvidia-smi samples of the SM clock and throttle reasons while timing
 
 Other workloads (--workload): ``batched`` = 4096 seed-generated programs (batched and
 plain paths both timed), ``stencil2d`` = the 8192^2, 16-launch log-heavy stencil.
