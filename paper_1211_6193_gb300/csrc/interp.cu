@@ -36,10 +36,10 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 enum : uint32_t { DEC_RELEASE = 1, DEC_DONE = 2, DEC_STOP = 3 };
 
 struct BlockVars {
-  unsigned long long cursor;   // log records reserved by the block
+  uint32_t cursor;             // log records reserved by the block (stops growing past the log)
   uint32_t n_misc, epoch, k0, flags, decision, err_dirty, status;
   uint32_t bar_np, bar_nw;     // at a release: true predicates, released threads
-  uint32_t pad[5];
+  uint32_t pad[6];
 };
 static_assert(sizeof(BlockVars) <= 64, "block vars");
 
@@ -168,18 +168,22 @@ __device__ __forceinline__ unsigned long long rec_of(uint32_t epoch_hi, uint32_t
 }
 
 // Append one record per lane with `me` to the block's access log (warp-aggregated:
-// one shared atomic per warp, consecutive 8-byte slots -> coalesced stores).
+// one 32-bit shared atomic per warp, consecutive 8-byte slots -> coalesced stores).
+// Once the log is full nothing more is reserved, so the cursor cannot wrap.
 __device__ __forceinline__ void log_access(BlockVars* bv, unsigned long long* region, uint32_t front_cap,
                                            bool me, unsigned long long rec, uint32_t lane) {
   const uint32_t m = __ballot_sync(FULL, me);
   if (m == 0) return;
   const uint32_t leader = __ffs(m) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(&bv->cursor, (unsigned long long)__popc(m));
+  uint32_t base = 0;
+  if (lane == leader) {
+    base = *reinterpret_cast<volatile uint32_t*>(&bv->cursor);
+    if (base < front_cap) base = atomicAdd(&bv->cursor, (uint32_t)__popc(m));
+  }
   base = __shfl_sync(FULL, base, leader);
   if (me) {
-    const unsigned long long pos = base + __popc(m & lanemask_lt());
-    if (pos < front_cap)
+    const uint32_t pos = base + __popc(m & lanemask_lt());
+    if (base < front_cap && pos < front_cap)
       region[pos] = rec;
     else
       atomicOr(&bv->flags, BF_OVERFLOW);
@@ -190,7 +194,7 @@ __device__ __forceinline__ void log_access(BlockVars* bv, unsigned long long* re
 __device__ void push_misc(BlockVars* bv, unsigned long long* region, uint32_t log_cap, uint32_t kind,
                           uint32_t epoch, uint32_t a, uint32_t b, uint32_t c) {
   const uint32_t i = bv->n_misc;
-  const unsigned long long used = bv->cursor < log_cap ? bv->cursor : log_cap;
+  const uint32_t used = bv->cursor < log_cap ? bv->cursor : log_cap;
   if (2ull * (i + 1) + used > log_cap) {
     bv->flags |= BF_OVERFLOW;
     return;
@@ -573,7 +577,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   if (tid == 0) {
     const uint32_t front = log_cap - 2u * bv->n_misc;
     BlockRes r;
-    r.n_log = bv->cursor < front ? (uint32_t)bv->cursor : front;
+    r.n_log = bv->cursor < front ? bv->cursor : front;
     r.n_race = 0;
     r.n_misc = bv->n_misc;
     r.flags = bv->flags;
