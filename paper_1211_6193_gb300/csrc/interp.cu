@@ -398,9 +398,17 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
                 break;
               }
             }
-            // several lanes of the warp on one word: the highest tid's store is the one kept
-            const uint32_t grp = __match_any_sync(FULL, inb ? (uint32_t)addr : (0x80000000u | lane));
-            if (inb && lane == 31u - __clz(grp)) {
+            // several lanes of the warp on one word: the highest tid's store is the one kept.
+            // Consecutive addresses, one per lane (addr - lane equal across the storing lanes),
+            // cannot collide; any other pattern groups the lanes by address.
+            const uint32_t sm = __ballot_sync(FULL, inb);
+            const int32_t off = __shfl_sync(FULL, addr - (int32_t)lane, sm ? __ffs(sm) - 1 : 0);
+            bool last = inb;
+            if (!__all_sync(FULL, !inb || addr - (int32_t)lane == off)) {
+              const uint32_t grp = __match_any_sync(FULL, inb ? (uint32_t)addr : (0x80000000u | lane));
+              last = inb && lane == 31u - __clz(grp);
+            }
+            if (last) {
               if (shared)
                 sh[addr] = vb;
               else
