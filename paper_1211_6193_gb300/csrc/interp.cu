@@ -495,14 +495,27 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     }
 
     // ---- no runnable lane in this warp: publish its state and park
+    // (`uni`: every waiting lane at one barrier pc and none runnable, the usual case: its
+    // lanes all resume together after that barrier)
+    bool uni = false;
+    uint32_t upc = 0;
     {
       const uint32_t wm = __ballot_sync(FULL, st == ST_WAIT);
       const uint32_t xm = __ballot_sync(FULL, st == ST_EXIT);
       const uint32_t rm = __ballot_sync(FULL, st == ST_RUN);
-      const uint32_t pmn = __reduce_min_sync(FULL, st == ST_WAIT ? wpc : kInf);
-      const uint32_t pmx = __reduce_max_sync(FULL, st == ST_WAIT ? wpc : 0u);
-      const uint32_t rpc = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
       const uint32_t tm = __ballot_sync(FULL, st == ST_WAIT && (bst >> 7));   // true predicates
+      uint32_t pmn = kInf, pmx = 0, rpc = kInf;
+      if (wm) {
+        upc = __shfl_sync(FULL, wpc, __ffs(wm) - 1);
+        uni = rm == 0 && __all_sync(FULL, st != ST_WAIT || wpc == upc);
+        if (uni) {
+          pmn = pmx = upc;
+        } else {
+          pmn = __reduce_min_sync(FULL, st == ST_WAIT ? wpc : kInf);
+          pmx = __reduce_max_sync(FULL, st == ST_WAIT ? wpc : 0u);
+        }
+      }
+      if (rm) rpc = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
       if (lane == 0) {
         uint32_t* P = park + w * 8;
         P[0] = __popc(wm); P[1] = __popc(xm); P[2] = __popc(rm);
@@ -516,16 +529,17 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     // ---- barrier resolution by warp 0 of the block
     if (w == 0) {
       const bool v = lane < nw;
-      const uint32_t* P = park + lane * 8;
-      const uint32_t nW = __reduce_add_sync(FULL, v ? P[0] : 0u);
-      const uint32_t nX = __reduce_add_sync(FULL, v ? P[1] : 0u);
-      const uint32_t nR = __reduce_add_sync(FULL, v ? P[2] : 0u);
-      const uint32_t pmn = __reduce_min_sync(FULL, v ? P[3] : kInf);
-      const uint32_t pmx = __reduce_max_sync(FULL, v ? P[4] : 0u);
-      const uint32_t rpc = __reduce_min_sync(FULL, v ? P[5] : kInf);
-      const uint32_t kmax = __reduce_max_sync(FULL, v ? P[6] : 0u);
-      const uint32_t fl = __reduce_or_sync(FULL, v ? P[7] & 0xFFu : 0u);
-      const uint32_t nP = __reduce_add_sync(FULL, v ? P[7] >> 8 : 0u);
+      const uint4 pa = reinterpret_cast<const uint4*>(park)[2 * lane];      // warp `lane`'s entry
+      const uint4 pb = reinterpret_cast<const uint4*>(park)[2 * lane + 1];
+      const uint32_t nW = __reduce_add_sync(FULL, v ? pa.x : 0u);
+      const uint32_t nX = __reduce_add_sync(FULL, v ? pa.y : 0u);
+      const uint32_t nR = __reduce_add_sync(FULL, v ? pa.z : 0u);
+      const uint32_t pmn = __reduce_min_sync(FULL, v ? pa.w : kInf);
+      const uint32_t pmx = __reduce_max_sync(FULL, v ? pb.x : 0u);
+      const uint32_t rpc = __reduce_min_sync(FULL, v ? pb.y : kInf);
+      const uint32_t kmax = __reduce_max_sync(FULL, v ? pb.z : 0u);
+      const uint32_t fl = __reduce_or_sync(FULL, v ? pb.w & 0xFFu : 0u);
+      const uint32_t nP = __reduce_add_sync(FULL, v ? pb.w >> 8 : 0u);
       const uint32_t ep = bv->epoch;
       uint32_t dec, kind = 0, a = 0, b = 0, c = 0, stbits = 0;
       if (fl & 2u) {
@@ -567,8 +581,13 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       }
       st = ST_RUN;
     }
-    pn = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
-    conv = __all_sync(FULL, st != ST_RUN || pc == pn);
+    if (uni) {                                   // every released lane resumes after its barrier
+      pn = upc + 1;
+      conv = true;
+    } else {
+      pn = __reduce_min_sync(FULL, st == ST_RUN ? pc : kInf);
+      conv = __all_sync(FULL, st != ST_RUN || pc == pn);
+    }
     k = bv->k0;
     omin = 4u * k;                               // every clock was reset to 4 * k0
     epoch = bv->epoch;
