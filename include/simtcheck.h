@@ -165,6 +165,11 @@ typedef struct {
                                 records per stage, stages, CTAs per SM); 0 = the default */
   uint32_t check_uninit;     /* 1 = also report loads of shared words not yet written
                                 (SR_REP_ERR_UNINIT_SHARED); 0 = off */
+  uint32_t fused_check;      /* 1 = the interpreter keeps each shared word's access summary itself
+                                (Sec. 3.1's per-location history, cleared at every barrier) and
+                                writes no access log, for every launch whose summaries fit in
+                                shared memory beside the block; same reports.  0 = access log +
+                                race-check kernel */
 } sr_opts;
 
 #define SR_CHECK_VARIANTS 4

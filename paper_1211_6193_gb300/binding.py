@@ -64,7 +64,7 @@ class sr_opts(C.Structure):
                 ("interp_variant", C.c_uint32), ("use_graph", C.c_uint32), ("profile", C.c_uint32),
                 ("spin_limit", C.c_uint32), ("log_budget_mb", C.c_uint32), ("report_cap", C.c_uint32),
                 ("allocator", C.POINTER(sr_allocator)), ("check_variant", C.c_uint32),
-                ("check_uninit", C.c_uint32)]
+                ("check_uninit", C.c_uint32), ("fused_check", C.c_uint32)]
 
 
 class sr_stats(C.Structure):
@@ -209,7 +209,8 @@ class Context:
     def __init__(self, check_races: bool = True, round_budget: int = 0, mode: str = "plain", ctas_per_sm: int = 0,
                  loop_log_records: int = 0, interp_variant: int = 0, use_graph: bool = False,
                  profile: bool = False, spin_limit: int = 0, log_budget_mb: int = 0, report_cap: int = 0,
-                 torch_allocator: bool = True, check_variant: int = 0, check_uninit: bool = False):
+                 torch_allocator: bool = True, check_variant: int = 0, check_uninit: bool = False,
+                 fused_check: bool = False):
         self.lib = load_library()
         self.allocator = TorchAllocator() if torch_allocator else None
         o = sr_opts()
@@ -220,6 +221,7 @@ class Context:
         o.log_budget_mb, o.report_cap = log_budget_mb, report_cap
         o.check_variant = check_variant
         o.check_uninit = int(check_uninit)
+        o.fused_check = int(fused_check)
         if self.allocator is not None:
             o.allocator = C.pointer(self.allocator.struct)
         self.opts = o

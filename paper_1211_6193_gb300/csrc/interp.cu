@@ -39,7 +39,9 @@ struct BlockVars {
   uint32_t cursor;             // log records reserved by the block (stops growing past the log)
   uint32_t n_misc, epoch, k0, flags, decision, err_dirty, status;
   uint32_t bar_np, bar_nw;     // at a release: true predicates, released threads
-  uint32_t pad[6];
+  uint32_t ntouched;           // fused race check: words touched in the interval
+  uint32_t race_out;           // fused race check: race entries written so far
+  uint32_t pad[4];
 };
 static_assert(sizeof(BlockVars) <= 64, "block vars");
 
@@ -190,6 +192,132 @@ __device__ __forceinline__ void log_access(BlockVars* bv, unsigned long long* re
   }
 }
 
+// ---- fused race check (Sec. 3.1: each shared location keeps the accesses made to it since
+// the last barrier).  The summary of a word: the two smallest distinct tids per access kind
+// and the pc range, enough to decide its races exactly; the first access of an interval to a
+// word lists the word.
+__device__ __forceinline__ void tuple_add(uint32_t* tup, uint16_t* touched, BlockVars* bv, uint32_t addr,
+                                          uint32_t tid, uint32_t kind, uint32_t pc) {
+  uint32_t* T = tup + 4u * addr;
+  uint32_t old = *reinterpret_cast<volatile uint32_t*>(T + kind);
+  for (;;) {
+    const uint32_t m1 = old & 0xFFFFu, m2 = old >> 16;
+    uint32_t nw = old;
+    if (tid != m1 && tid != m2) nw = tid < m1 ? (m1 << 16 | tid) : (tid < m2 ? (tid << 16 | m1) : old);
+    if (nw == old) break;
+    const uint32_t prev = atomicCAS(T + kind, old, nw);
+    if (prev == old) break;
+    old = prev;
+  }
+  old = *reinterpret_cast<volatile uint32_t*>(T + 3);
+  for (;;) {
+    const uint32_t nw = max(old >> 16, pc) << 16 | min(old & 0xFFFFu, pc);
+    if (nw == old) break;
+    const uint32_t prev = atomicCAS(T + 3, old, nw);
+    if (prev == old) {
+      if (old == kTuplePcEmpty) touched[atomicAdd(&bv->ntouched, 1u)] = (uint16_t)addr;
+      break;
+    }
+    old = prev;
+  }
+}
+
+// Conflict classes and the smallest conflicting pair of a word from its summary (two threads
+// conflict when distinct and write-write, write-read, write-atomic or atomic-read); false when
+// the word has no race.
+__device__ __forceinline__ bool tuple_race(const uint32_t* T, uint32_t& bout, uint32_t& cout) {
+  const uint32_t R[2] = {T[0] & 0xFFFFu, T[0] >> 16}, W[2] = {T[1] & 0xFFFFu, T[1] >> 16};
+  const uint32_t A[2] = {T[2] & 0xFFFFu, T[2] >> 16};
+  uint32_t cls = 0, best = 0xFFFFFFFFu;
+  auto pair = [&](uint32_t x, uint32_t y, uint32_t bit) {
+    if (x == 0xFFFFu || y == 0xFFFFu || x == y) return;
+    cls |= bit;
+    best = min(best, min(x, y) << 16 | max(x, y));
+  };
+  pair(W[0], W[1], SR_CLS_WW);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      pair(W[i], R[j], SR_CLS_WR);
+      pair(W[i], A[j], SR_CLS_WA);
+      pair(A[i], R[j], SR_CLS_AR);
+    }
+  if (!cls) return false;
+  bout = best;
+  cout = cls << 24 | (T[3] & 0xFFFu) << 12 | ((T[3] >> 16) & 0xFFFu);
+  return true;
+}
+
+// End of an interval, every warp of the block: its share of the touched words.  A racy word
+// keeps its pair and class|pcs in the first two summary words and is marked in the bitmap;
+// every other word is cleared for the next interval.
+__device__ __forceinline__ void tuples_mark(uint32_t* tup, const uint16_t* touched, uint32_t* rbm, uint32_t n,
+                                            uint32_t tid, uint32_t nthr) {
+  for (uint32_t i = tid; i < n; i += nthr) {
+    const uint32_t a = touched[i];
+    uint32_t* T = tup + 4u * a;
+    uint32_t b, c;
+    if (tuple_race(T, b, c)) {
+      T[0] = b;
+      T[1] = c;
+      atomicOr(&rbm[a >> 5], 1u << (a & 31u));
+    } else {
+      T[0] = T[1] = T[2] = kTupleEmpty;
+      T[3] = kTuplePcEmpty;
+    }
+  }
+}
+
+// Warp 0: race entries of the interval's racy words in address order at the front of the
+// block's region (16 bytes each, after the entries of earlier intervals), then the words are
+// cleared.  A racy word had at least two accesses, so the entries fit wherever the region is
+// sized by the accesses on a path; past `front_cap` record slots (a loop kernel's fixed
+// region) entries are dropped and the block is flagged, as the access log would be.
+__device__ void tuples_emit(uint32_t* tup, uint32_t* rbm, uint32_t shw, BlockVars* bv, unsigned long long* region,
+                            uint32_t front_cap, uint32_t epoch, uint32_t lane) {
+  const uint32_t nbw = (shw + 31u) / 32u;
+  const uint32_t cap = front_cap / 2u;           // entries that fit
+  uint32_t ro = bv->race_out;
+  bool over = false;
+  uint4* out = reinterpret_cast<uint4*>(region);
+  for (uint32_t base = 0; base < nbw; base += 32) {
+    const uint32_t wd = base + lane;
+    uint32_t word = wd < nbw ? rbm[wd] : 0u;
+    const uint32_t cnt = __popc(word);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    uint32_t pos = ro + inc - cnt;
+    while (word) {
+      const uint32_t a = wd * 32u + (__ffs(word) - 1);
+      word &= word - 1;
+      uint32_t* T = tup + 4u * a;
+      if (pos < cap)
+        out[pos] = make_uint4(epoch, a, T[0], T[1]);
+      else
+        over = true;
+      ++pos;
+      T[0] = T[1] = T[2] = kTupleEmpty;
+      T[3] = kTuplePcEmpty;
+    }
+    if (wd < nbw) rbm[wd] = 0;
+    ro += __shfl_sync(FULL, inc, 31);
+  }
+  ro = min(ro, cap);
+  if (__any_sync(FULL, over) && lane == 0) bv->flags |= BF_OVERFLOW;
+  __syncwarp();
+  if (lane == 0) {
+    bv->race_out = ro;
+    bv->ntouched = 0;
+    bv->cursor = 2u * ro;                        // record slots the entries occupy
+  }
+  __syncwarp();
+}
+
 // Barrier/error records grow down from the end of the block's log region (16 B each).
 __device__ void push_misc(BlockVars* bv, unsigned long long* region, uint32_t log_cap, uint32_t kind,
                           uint32_t epoch, uint32_t a, uint32_t b, uint32_t c) {
@@ -257,7 +385,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   const uint32_t tid = w * 32 + lane;
   const uint32_t bdim = Ls->bdim, shw = Ls->shw, ncode = Ls->ncode, log_cap = Ls->log_cap, nrows = Ls->nrows;
   const bool uninit = Ls->uninit != 0;
-  const GroupLayout G = group_layout(nthr, shw, ncode, nrows, Ls->uninit);
+  const bool fused = Ls->fused != 0 && A.check_races != 0;
+  const GroupLayout G = group_layout(nthr, shw, ncode, nrows, Ls->uninit, Ls->fused);
   uint32_t* regs = reinterpret_cast<uint32_t*>(gsm + G.regs);
   int32_t* sh = reinterpret_cast<int32_t*>(gsm + G.sh);
   uint32_t* clk = reinterpret_cast<uint32_t*>(gsm + kGroupClk);
@@ -268,6 +397,9 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   uint32_t* err = reinterpret_cast<uint32_t*>(gsm + G.err);
   uint32_t* un = reinterpret_cast<uint32_t*>(gsm + G.un);      // with `uninit` only
   uint32_t* wb = reinterpret_cast<uint32_t*>(gsm + G.wb);      // with `uninit` only
+  uint32_t* tup = reinterpret_cast<uint32_t*>(gsm + G.tup);    // with `fused` only
+  uint16_t* touched = reinterpret_cast<uint16_t*>(gsm + G.touched);
+  uint32_t* rbm = reinterpret_cast<uint32_t*>(gsm + G.rbm);
   BlockVars* bv = reinterpret_cast<BlockVars*>(gsm + kGroupBv);
   int32_t* arena = A.arena + Ls->arena_off;
   const uint32_t arena_words = (uint32_t)Ls->arena_words;
@@ -290,10 +422,16 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     }
     for (uint32_t i = tid; i < (shw + 31u) / 32u; i += nthr) wb[i] = 0;
   }
+  if (fused) {
+    for (uint32_t i = tid; i < shw; i += nthr)
+      reinterpret_cast<uint4*>(tup)[i] = make_uint4(kTupleEmpty, kTupleEmpty, kTupleEmpty, kTuplePcEmpty);
+    for (uint32_t i = tid; i < (shw + 31u) / 32u; i += nthr) rbm[i] = 0;
+  }
   if (tid == 0) {
     bv->cursor = 0;
     bv->n_misc = 0; bv->epoch = 0; bv->k0 = 0; bv->flags = 0;
     bv->decision = 0; bv->err_dirty = 0; bv->status = 0;
+    bv->ntouched = 0; bv->race_out = 0;
   }
   if (lane == 0) clk[w] = 0;
   group_sync(bar_id, nthr);
@@ -307,6 +445,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   bool conv = true;
   uint32_t pn = Ls->entry;
   uint32_t n_instr = 0, n_gacc = 0;              // per lane: executed instructions, global accesses
+  uint32_t n_sacc = 0;                           // per lane, fused race check: shared accesses
   // a log record is built from 32-bit halves: low = addr << 24 | tid << 14 | kind << 12 | pc,
   // high = epoch << 6 | addr >> 8
   const uint32_t lane_rec = tid << 14;
@@ -369,10 +508,16 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
               if (um) note_err(un, bv, p, w, um, lane);
             }
             if (shared) {
-              if (logging)
-                log_access(bv, region, front_cap, inb,
+              if (logging) {
+                if (fused) {
+                  if (inb) tuple_add(tup, touched, bv, (uint32_t)addr, tid, K_R, p);
+                  n_sacc += inb;
+                } else {
+                  log_access(bv, region, front_cap, inb,
                            rec_of(epoch_hi, lane_rec | K_R << 12 | p, (uint32_t)addr),
                            lane);
+                }
+              }
             } else {
               n_gacc += act;
             }
@@ -418,10 +563,16 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             const uint32_t em = __ballot_sync(FULL, act && !inb);
             if (em) note_err(err, bv, p, w, em, lane);
             if (shared) {
-              if (logging)
-                log_access(bv, region, front_cap, inb,
+              if (logging) {
+                if (fused) {
+                  if (inb) tuple_add(tup, touched, bv, (uint32_t)addr, tid, K_W, p);
+                  n_sacc += inb;
+                } else {
+                  log_access(bv, region, front_cap, inb,
                            rec_of(epoch_hi, lane_rec | K_W << 12 | p, (uint32_t)addr),
                            lane);
+                }
+              }
             } else {
               n_gacc += act;
             }
@@ -442,10 +593,16 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (uninit && inb) atomicOr(&wb[addr >> 5], 1u << (addr & 31));
             const uint32_t em = __ballot_sync(FULL, act && !inb);
             if (em) note_err(err, bv, p, w, em, lane);
-            if (logging)
-              log_access(bv, region, front_cap, inb,
+            if (logging) {
+                if (fused) {
+                  if (inb) tuple_add(tup, touched, bv, (uint32_t)addr, tid, K_A, p);
+                  n_sacc += inb;
+                } else {
+                  log_access(bv, region, front_cap, inb,
                          rec_of(epoch_hi, lane_rec | K_A << 12 | p, (uint32_t)addr),
                          lane);
+                }
+              }
             break;
           }
           case SR_OP_BRA: npc = cn = (uint32_t)imm; break;
@@ -525,6 +682,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       }
     }
     group_sync(bar_id, nthr);
+    if (fused) {                                 // the interval's touched words, all warps
+      tuples_mark(tup, touched, rbm, bv->ntouched, tid, nthr);
+      group_sync(bar_id, nthr);
+    }
 
     // ---- barrier resolution by warp 0 of the block
     if (w == 0) {
@@ -541,6 +702,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const uint32_t fl = __reduce_or_sync(FULL, v ? pb.w & 0xFFu : 0u);
       const uint32_t nP = __reduce_add_sync(FULL, v ? pb.w >> 8 : 0u);
       const uint32_t ep = bv->epoch;
+      if (fused) tuples_emit(tup, rbm, shw, bv, region, log_cap - 2u * bv->n_misc, ep, lane);
       uint32_t dec, kind = 0, a = 0, b = 0, c = 0, stbits = 0;
       if (fl & 2u) {
         dec = DEC_STOP;
@@ -597,15 +759,17 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
 
   // ---- block finished
   const uint32_t wi = __reduce_add_sync(FULL, n_instr), wg = __reduce_add_sync(FULL, n_gacc);
+  const uint32_t ws = __reduce_add_sync(FULL, n_sacc);
   if (lane == 0) {
     atomicAdd(&A.counters->thread_instrs, (unsigned long long)wi);
     if (wg) atomicAdd(&A.counters->global_accesses, (unsigned long long)wg);
+    if (ws) atomicAdd(&A.counters->shared_accesses, (unsigned long long)ws);
   }
   if (tid == 0) {
     const uint32_t front = log_cap - 2u * bv->n_misc;
     BlockRes r;
-    r.n_log = bv->cursor < front ? bv->cursor : front;
-    r.n_race = 0;
+    r.n_log = fused ? 0u : (bv->cursor < front ? bv->cursor : front);   // fused: no records to check
+    r.n_race = fused ? bv->race_out : 0u;
     r.n_misc = bv->n_misc;
     r.flags = bv->flags;
     A.blocks[Ls->block_base + block] = r;
@@ -706,7 +870,7 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
 
 uint32_t interp_plain_smem(const LaunchDev& L) {
   const uint32_t nthr = ((L.bdim + 31) / 32) * 32;
-  return L.ir_bytes + group_layout(nthr, L.shw, L.ncode, L.nrows, L.uninit).total;
+  return L.ir_bytes + group_layout(nthr, L.shw, L.ncode, L.nrows, L.uninit, L.fused).total;
 }
 
 // dynamic shared memory may use what the kernel's static shared memory leaves of the opt-in limit

@@ -107,7 +107,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     d.ir_bytes = sr::ir_smem_bytes(ncode);
     d.nrows = rm.nrows;
     const uint32_t nw = (pl.block_dim + 31) / 32;
-    d.group_bytes = sr::group_layout(nw * 32, pl.shmem_words, ncode, rm.nrows, 0).total;
+    d.group_bytes = sr::group_layout(nw * 32, pl.shmem_words, ncode, rm.nrows, 0, 0).total;
     d.groups = 1;
     d.check_group = sr::check_group_for(d.log_cap);
     d.check_item = (uint32_t)check_items;

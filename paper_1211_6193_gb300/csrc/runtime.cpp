@@ -381,7 +381,13 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       d.nrows = rm.nrows;
       const uint32_t nw = (L.block_dim + 31) / 32;
       d.uninit = o.check_uninit ? 1u : 0u;
-      d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode, rm.nrows, d.uninit).total;
+      // the fused race check where its summaries fit beside the block, else the access log
+      d.fused = (o.fused_check && o.check_races && L.shmem_words) ? 1u : 0u;
+      d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode, rm.nrows, d.uninit, d.fused).total;
+      if (d.fused && d.ir_bytes + d.group_bytes > smem_budget) {
+        d.fused = 0;
+        d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode, rm.nrows, d.uninit, 0).total;
+      }
       if (d.ir_bytes + d.group_bytes > smem_budget) {
         delete b;
         return fail(c, SR_E_INVAL, "program %u launch %u: %u bytes of shared memory needed, %u available", i, l,

@@ -46,7 +46,8 @@ struct LaunchDev {
   uint32_t groups, group_bytes;          // batched mode: blocks per CTA, smem per block
   uint32_t ir_bytes, nrows;              // smem bytes of the staged code; register rows (zero row last)
   uint32_t check_group, check_item;      // race check: blocks per work item, index of the first item
-  uint32_t uninit, pad0;                 // 1 = report shared loads of words no thread wrote
+  uint32_t uninit;                       // 1 = report shared loads of words no thread wrote
+  uint32_t fused;                        // 1 = race summaries kept by the interpreter (no log)
 };
 
 // Per simulated block, written by the interpreter (n_log, n_misc, flags) and the checker (n_race).
@@ -76,16 +77,22 @@ struct RunArgs {
 
 // Shared-memory footprint of one simulated block in the interpreter.
 struct GroupLayout {
-  uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, un, wb, total;
+  uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, un, wb, tup, touched, rbm, total;
 };
+// the summary of one shared word in the fused race check: the two smallest distinct tids
+// of each access kind (low 16 bits the smaller, 0xFFFF none) and the pc range (low 16 bits
+// the lowest pc, high 16 bits the highest)
+constexpr uint32_t kTupleEmpty = 0xFFFFFFFFu, kTuplePcEmpty = 0x0000FFFFu;
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 // The fixed-size arrays come first, at offsets known at compile time; the arrays whose
 // size depends on the launch follow.
 constexpr uint32_t kGroupClk = 0, kGroupRlo = 128, kGroupRhi = 256, kGroupRsp = 384, kGroupPark = 512,
                    kGroupBv = 512 + 32 * 8 * 4, kGroupFixed = kGroupBv + 64;
 // With `uninit`: per-pc counters of loads of unwritten words, and the bitmap of written words.
+// With `fused`: a 4-word summary per shared word, the words touched in the interval, and a
+// bitmap of its racy words.
 __host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode, uint32_t nrows,
-                                                   uint32_t uninit) {
+                                                   uint32_t uninit, uint32_t fused) {
   GroupLayout g;
   g.clk = kGroupClk;
   g.rlo = kGroupRlo;
@@ -101,6 +108,12 @@ __host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw,
   if (uninit) {
     g.un = o; o += align16(2u * (ncode + 1) * 4u);
     g.wb = o; o += align16((shw + 31u) / 32u * 4u);
+  }
+  g.tup = g.touched = g.rbm = 0;
+  if (fused) {
+    g.tup = o;     o += align16(shw * 16u);
+    g.touched = o; o += align16(shw * 2u);
+    g.rbm = o;     o += align16((shw + 31u) / 32u * 4u);
   }
   g.total = o;
   return g;

@@ -254,6 +254,29 @@ def test_uninitialised_shared_reads(B, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_fused_race_check(B, mode):
+    """The interpreter keeping each word's summary itself (no access log): the same reports
+    as the oracle on Figure 1, interleaving programs, generated batches with planted bugs,
+    reductions, the 2-D stencil, reducing barriers, loops with barriers, deadlocks, more racy
+    words than one round holds, shared arrays too large to fuse (they keep the log), and with
+    the uninitialised-read check on."""
+    from rbar_programs import all_programs
+    groups = [
+        [fig1.program(), fig1.program(race=True), fig1.program(deadlock=True)],
+        tiny.tiny_batch(5, 40),
+        families.batch(n_programs=40, seed=17, max_grid=10, bug_rate=0.5),
+        [families.reduction_plain(n_blocks=12, bdim=1024, seed=2, omit_level=3)],
+        [stencil2d.program(log2w=6, steps=3, buggy_launch=1, seed=5)],
+        all_programs(),
+        _many_racy_addresses_programs(),
+    ]
+    for progs in groups:
+        assert_parity(B, progs, mode, fused_check=True)
+    assert_parity(B, _uninit_programs(), mode, oracle_kw={"check_uninit": True}, check_uninit=True,
+                  fused_check=True)
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_reducing_barriers(B, mode):
     """__syncthreads_and/_or/_count: predicates over full and partial warps, reducing and
     plain barriers meeting, a deadlock at a reducing barrier, reducing barriers in a loop."""
