@@ -195,39 +195,53 @@ __device__ __forceinline__ void log_access(BlockVars* bv, unsigned long long* re
 // ---- fused race check (Sec. 3.1: each shared location keeps the accesses made to it since
 // the last barrier).  The summary of a word: the two smallest distinct tids per access kind
 // and the pc range, enough to decide its races exactly; the first access of an interval to a
-// word lists the word.
-__device__ __forceinline__ void tuple_add(uint32_t* tup, uint16_t* touched, BlockVars* bv, uint32_t addr,
-                                          uint32_t tid, uint32_t kind, uint32_t pc) {
-  uint32_t* T = tup + 4u * addr;
-  uint32_t old = *reinterpret_cast<volatile uint32_t*>(T + kind);
-  for (;;) {
-    const uint32_t m1 = old & 0xFFFFu, m2 = old >> 16;
-    uint32_t nw = old;
-    if (tid != m1 && tid != m2) nw = tid < m1 ? (m1 << 16 | tid) : (tid < m2 ? (tid << 16 | m1) : old);
-    if (nw == old) break;
-    const uint32_t prev = atomicCAS(T + kind, old, nw);
-    if (prev == old) break;
-    old = prev;
-  }
-  old = *reinterpret_cast<volatile uint32_t*>(T + 3);
-  for (;;) {
-    const uint32_t nw = max(old >> 16, pc) << 16 | min(old & 0xFFFFu, pc);
-    if (nw == old) break;
-    const uint32_t prev = atomicCAS(T + 3, old, nw);
-    if (prev == old) {
-      if (old == kTuplePcEmpty) touched[atomicAdd(&bv->ntouched, 1u)] = (uint16_t)addr;
-      break;
+// word lists the word.  Plane k of the summaries starts at tup + k * tps.
+//
+// Whole warp (converged): lanes with `inb` add their access to word `addr`.
+__device__ __forceinline__ void tuple_add(uint32_t* tup, uint32_t tps, uint16_t* touched, BlockVars* bv, bool inb,
+                                          uint32_t addr, uint32_t tid, uint32_t kind, uint32_t pc, uint32_t lane) {
+  bool first = false;
+  if (inb) {
+    uint32_t* T = tup + kind * tps + addr;
+    uint32_t old = *reinterpret_cast<volatile uint32_t*>(T);
+    for (;;) {
+      const uint32_t m1 = old & 0xFFFFu, m2 = old >> 16;
+      uint32_t nw = old;
+      if (tid != m1 && tid != m2) nw = tid < m1 ? (m1 << 16 | tid) : (tid < m2 ? (tid << 16 | m1) : old);
+      if (nw == old) break;
+      const uint32_t prev = atomicCAS(T, old, nw);
+      if (prev == old) break;
+      old = prev;
     }
-    old = prev;
+    uint32_t* P = tup + 3u * tps + addr;
+    old = *reinterpret_cast<volatile uint32_t*>(P);
+    for (;;) {
+      const uint32_t nw = max(old >> 16, pc) << 16 | min(old & 0xFFFFu, pc);
+      if (nw == old) break;
+      const uint32_t prev = atomicCAS(P, old, nw);
+      if (prev == old) {
+        first = old == kTuplePcEmpty;
+        break;
+      }
+      old = prev;
+    }
+  }
+  const uint32_t fm = __ballot_sync(FULL, first);
+  if (fm) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&bv->ntouched, (uint32_t)__popc(fm));
+    base = __shfl_sync(FULL, base, 0);
+    if (first) touched[base + __popc(fm & ((1u << lane) - 1u))] = (uint16_t)addr;
   }
 }
 
 // Conflict classes and the smallest conflicting pair of a word from its summary (two threads
 // conflict when distinct and write-write, write-read, write-atomic or atomic-read); false when
 // the word has no race.
-__device__ __forceinline__ bool tuple_race(const uint32_t* T, uint32_t& bout, uint32_t& cout) {
-  const uint32_t R[2] = {T[0] & 0xFFFFu, T[0] >> 16}, W[2] = {T[1] & 0xFFFFu, T[1] >> 16};
-  const uint32_t A[2] = {T[2] & 0xFFFFu, T[2] >> 16};
+__device__ __forceinline__ bool tuple_race(uint32_t r, uint32_t w, uint32_t a, uint32_t pcr, uint32_t& bout,
+                                           uint32_t& cout) {
+  const uint32_t R[2] = {r & 0xFFFFu, r >> 16}, W[2] = {w & 0xFFFFu, w >> 16};
+  const uint32_t A[2] = {a & 0xFFFFu, a >> 16};
   uint32_t cls = 0, best = 0xFFFFFFFFu;
   auto pair = [&](uint32_t x, uint32_t y, uint32_t bit) {
     if (x == 0xFFFFu || y == 0xFFFFu || x == y) return;
@@ -245,26 +259,26 @@ __device__ __forceinline__ bool tuple_race(const uint32_t* T, uint32_t& bout, ui
     }
   if (!cls) return false;
   bout = best;
-  cout = cls << 24 | (T[3] & 0xFFFu) << 12 | ((T[3] >> 16) & 0xFFFu);
+  cout = cls << 24 | (pcr & 0xFFFu) << 12 | ((pcr >> 16) & 0xFFFu);
   return true;
 }
 
 // End of an interval, every warp of the block: its share of the touched words.  A racy word
-// keeps its pair and class|pcs in the first two summary words and is marked in the bitmap;
+// keeps its pair and class|pcs in its read and write summaries and is marked in the bitmap;
 // every other word is cleared for the next interval.
-__device__ __forceinline__ void tuples_mark(uint32_t* tup, const uint16_t* touched, uint32_t* rbm, uint32_t n,
-                                            uint32_t tid, uint32_t nthr) {
+__device__ __forceinline__ void tuples_mark(uint32_t* tup, uint32_t tps, const uint16_t* touched, uint32_t* rbm,
+                                            uint32_t n, uint32_t tid, uint32_t nthr) {
   for (uint32_t i = tid; i < n; i += nthr) {
     const uint32_t a = touched[i];
-    uint32_t* T = tup + 4u * a;
+    uint32_t* T = tup + a;
     uint32_t b, c;
-    if (tuple_race(T, b, c)) {
+    if (tuple_race(T[0], T[tps], T[2u * tps], T[3u * tps], b, c)) {
       T[0] = b;
-      T[1] = c;
+      T[tps] = c;
       atomicOr(&rbm[a >> 5], 1u << (a & 31u));
     } else {
-      T[0] = T[1] = T[2] = kTupleEmpty;
-      T[3] = kTuplePcEmpty;
+      T[0] = T[tps] = T[2u * tps] = kTupleEmpty;
+      T[3u * tps] = kTuplePcEmpty;
     }
   }
 }
@@ -274,8 +288,8 @@ __device__ __forceinline__ void tuples_mark(uint32_t* tup, const uint16_t* touch
 // cleared.  A racy word had at least two accesses, so the entries fit wherever the region is
 // sized by the accesses on a path; past `front_cap` record slots (a loop kernel's fixed
 // region) entries are dropped and the block is flagged, as the access log would be.
-__device__ void tuples_emit(uint32_t* tup, uint32_t* rbm, uint32_t shw, BlockVars* bv, unsigned long long* region,
-                            uint32_t front_cap, uint32_t epoch, uint32_t lane) {
+__device__ void tuples_emit(uint32_t* tup, uint32_t tps, uint32_t* rbm, uint32_t shw, BlockVars* bv,
+                            unsigned long long* region, uint32_t front_cap, uint32_t epoch, uint32_t lane) {
   const uint32_t nbw = (shw + 31u) / 32u;
   const uint32_t cap = front_cap / 2u;           // entries that fit
   uint32_t ro = bv->race_out;
@@ -295,14 +309,14 @@ __device__ void tuples_emit(uint32_t* tup, uint32_t* rbm, uint32_t shw, BlockVar
     while (word) {
       const uint32_t a = wd * 32u + (__ffs(word) - 1);
       word &= word - 1;
-      uint32_t* T = tup + 4u * a;
+      uint32_t* T = tup + a;
       if (pos < cap)
-        out[pos] = make_uint4(epoch, a, T[0], T[1]);
+        out[pos] = make_uint4(epoch, a, T[0], T[tps]);
       else
         over = true;
       ++pos;
-      T[0] = T[1] = T[2] = kTupleEmpty;
-      T[3] = kTuplePcEmpty;
+      T[0] = T[tps] = T[2u * tps] = kTupleEmpty;
+      T[3u * tps] = kTuplePcEmpty;
     }
     if (wd < nbw) rbm[wd] = 0;
     ro += __shfl_sync(FULL, inc, 31);
@@ -377,7 +391,10 @@ __device__ void flush_errors(BlockVars* bv, uint32_t* err, uint32_t* un, const u
   if (lane == 0) bv->err_dirty = 0;
 }
 
-// Run one simulated block on warps [0, nw) of a group (bar_id = its named barrier).
+// Run one simulated block on warps [0, nw) of a group (bar_id = its named barrier).  The
+// fused race check is compiled in only where Fused is set, so that the kernels without it
+// keep their register budget.
+template <bool Fused>
 __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block, const uint2* __restrict__ ir,
                           unsigned char* gsm, uint32_t w, uint32_t nw, uint32_t bar_id) {
   const uint32_t lane = threadIdx.x & 31;
@@ -385,7 +402,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   const uint32_t tid = w * 32 + lane;
   const uint32_t bdim = Ls->bdim, shw = Ls->shw, ncode = Ls->ncode, log_cap = Ls->log_cap, nrows = Ls->nrows;
   const bool uninit = Ls->uninit != 0;
-  const bool fused = Ls->fused != 0 && A.check_races != 0;
+  const bool fused = Fused && Ls->fused != 0 && A.check_races != 0;
   const GroupLayout G = group_layout(nthr, shw, ncode, nrows, Ls->uninit, Ls->fused);
   uint32_t* regs = reinterpret_cast<uint32_t*>(gsm + G.regs);
   int32_t* sh = reinterpret_cast<int32_t*>(gsm + G.sh);
@@ -398,6 +415,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   uint32_t* un = reinterpret_cast<uint32_t*>(gsm + G.un);      // with `uninit` only
   uint32_t* wb = reinterpret_cast<uint32_t*>(gsm + G.wb);      // with `uninit` only
   uint32_t* tup = reinterpret_cast<uint32_t*>(gsm + G.tup);    // with `fused` only
+  const uint32_t tps = tuple_plane_words(shw);
   uint16_t* touched = reinterpret_cast<uint16_t*>(gsm + G.touched);
   uint32_t* rbm = reinterpret_cast<uint32_t*>(gsm + G.rbm);
   BlockVars* bv = reinterpret_cast<BlockVars*>(gsm + kGroupBv);
@@ -423,8 +441,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     for (uint32_t i = tid; i < (shw + 31u) / 32u; i += nthr) wb[i] = 0;
   }
   if (fused) {
-    for (uint32_t i = tid; i < shw; i += nthr)
-      reinterpret_cast<uint4*>(tup)[i] = make_uint4(kTupleEmpty, kTupleEmpty, kTupleEmpty, kTuplePcEmpty);
+    for (uint32_t i = tid; i < 4u * tps; i += nthr) tup[i] = i < 3u * tps ? kTupleEmpty : kTuplePcEmpty;
     for (uint32_t i = tid; i < (shw + 31u) / 32u; i += nthr) rbm[i] = 0;
   }
   if (tid == 0) {
@@ -510,7 +527,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (shared) {
               if (logging) {
                 if (fused) {
-                  if (inb) tuple_add(tup, touched, bv, (uint32_t)addr, tid, K_R, p);
+                  tuple_add(tup, tps, touched, bv, inb, (uint32_t)addr, tid, K_R, p, lane);
                   n_sacc += inb;
                 } else {
                   log_access(bv, region, front_cap, inb,
@@ -565,7 +582,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (shared) {
               if (logging) {
                 if (fused) {
-                  if (inb) tuple_add(tup, touched, bv, (uint32_t)addr, tid, K_W, p);
+                  tuple_add(tup, tps, touched, bv, inb, (uint32_t)addr, tid, K_W, p, lane);
                   n_sacc += inb;
                 } else {
                   log_access(bv, region, front_cap, inb,
@@ -595,7 +612,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (em) note_err(err, bv, p, w, em, lane);
             if (logging) {
                 if (fused) {
-                  if (inb) tuple_add(tup, touched, bv, (uint32_t)addr, tid, K_A, p);
+                  tuple_add(tup, tps, touched, bv, inb, (uint32_t)addr, tid, K_A, p, lane);
                   n_sacc += inb;
                 } else {
                   log_access(bv, region, front_cap, inb,
@@ -683,7 +700,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     }
     group_sync(bar_id, nthr);
     if (fused) {                                 // the interval's touched words, all warps
-      tuples_mark(tup, touched, rbm, bv->ntouched, tid, nthr);
+      tuples_mark(tup, tps, touched, rbm, bv->ntouched, tid, nthr);
       group_sync(bar_id, nthr);
     }
 
@@ -702,7 +719,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const uint32_t fl = __reduce_or_sync(FULL, v ? pb.w & 0xFFu : 0u);
       const uint32_t nP = __reduce_add_sync(FULL, v ? pb.w >> 8 : 0u);
       const uint32_t ep = bv->epoch;
-      if (fused) tuples_emit(tup, rbm, shw, bv, region, log_cap - 2u * bv->n_misc, ep, lane);
+      if (fused) tuples_emit(tup, tps, rbm, shw, bv, region, log_cap - 2u * bv->n_misc, ep, lane);
       uint32_t dec, kind = 0, a = 0, b = 0, c = 0, stbits = 0;
       if (fl & 2u) {
         dec = DEC_STOP;
@@ -783,7 +800,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
 
 // One CTA per simulated block; one kernel launch per (program, launch).  MINB = 2 caps
 // registers so that two 1024-thread CTAs fit an SM.
-template <int MINB>
+template <int MINB, bool Fused>
 __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t li) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LaunchDev Ls;
@@ -805,7 +822,7 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
     if (threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
     return;
   }
-  run_block(A, &Ls, blockIdx.x, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes, threadIdx.x >> 5,
+  run_block<Fused>(A, &Ls, blockIdx.x, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes, threadIdx.x >> 5,
             blockDim.x >> 5, 1);
 }
 
@@ -813,6 +830,7 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
 // `groups` simulated blocks side by side, each on its own warps and named barrier.
 // Items are ordered launch-wave by launch-wave, and an item of launch l waits (bounded)
 // until every block of launch l-1 of the same program has completed.
+template <bool Fused>
 __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LaunchDev Ls;
@@ -854,7 +872,7 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
       const uint32_t nw = (Ls.bdim + 31) >> 5;
       const uint32_t wid = threadIdx.x >> 5, g = wid / nw;
       if (ok && g < nblk)
-        run_block(A, &Ls, it.y + g, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes + g * Ls.group_bytes,
+        run_block<Fused>(A, &Ls, it.y + g, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes + g * Ls.group_bytes,
                   wid - g * nw, nw, 1 + g);
       if (!ok && threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
     }
@@ -884,9 +902,12 @@ static cudaError_t allow_dynamic_smem(K kernel, uint32_t smem_optin) {
 }
 
 cudaError_t init_interp_attributes(uint32_t smem_optin) {
-  cudaError_t e = allow_dynamic_smem(k_interp_plain<1>, smem_optin);
-  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2>, smem_optin);
-  return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched, smem_optin) : e;
+  cudaError_t e = allow_dynamic_smem(k_interp_plain<1, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<1, true>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, true>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<false>, smem_optin);
+  return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched<true>, smem_optin) : e;
 }
 
 // variant: 1 = one CTA per SM budget (no register cap), 2 = two CTAs per SM, 0 = the one
@@ -894,21 +915,24 @@ cudaError_t init_interp_attributes(uint32_t smem_optin) {
 cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, uint32_t variant, cudaStream_t s) {
   const uint32_t threads = ((L.bdim + 31) / 32) * 32;
   const uint32_t smem = interp_plain_smem(L);
+  const bool fused = L.fused != 0;
   if (variant == 0) {
     int b1 = 0, b2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_interp_plain<1>, (int)threads, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_interp_plain<2>, (int)threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fused ? k_interp_plain<1, true> : k_interp_plain<1, false>,
+                                                  (int)threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fused ? k_interp_plain<2, true> : k_interp_plain<2, false>,
+                                                  (int)threads, smem);
     variant = b2 > b1 ? 2 : 1;
   }
   if (variant == 2)
-    k_interp_plain<2><<<L.grid, threads, smem, s>>>(a, li);
+    (fused ? k_interp_plain<2, true> : k_interp_plain<2, false>)<<<L.grid, threads, smem, s>>>(a, li);
   else
-    k_interp_plain<1><<<L.grid, threads, smem, s>>>(a, li);
+    (fused ? k_interp_plain<1, true> : k_interp_plain<1, false>)<<<L.grid, threads, smem, s>>>(a, li);
   return cudaGetLastError();
 }
 
-cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, cudaStream_t s) {
-  k_interp_batched<<<ctas, 1024, smem, s>>>(a);
+cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, cudaStream_t s) {
+  (fused ? k_interp_batched<true> : k_interp_batched<false>)<<<ctas, 1024, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -202,7 +202,7 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       ra.queue_head = (uint32_t*)b->queue_head.p + wi;
       CUDA_TRY(c, cudaMemsetAsync(ra.queue_head, 0, 4, s));
       const uint32_t ctas = std::min<uint32_t>(ra.nitems, (uint32_t)c->sms * std::max(1u, o.ctas_per_sm));
-      if (ctas) CUDA_TRY(c, sr::launch_interp_batched(ra, ctas, b->batched_smem, s));
+      if (ctas) CUDA_TRY(c, sr::launch_interp_batched(ra, ctas, b->batched_smem, o.fused_check && o.check_races, s));
     } else {
       for (uint32_t li = w.li0; li < w.li1; ++li)
         CUDA_TRY(c, sr::launch_interp_plain(ra, li, b->launches[li], o.interp_variant, s));

@@ -83,14 +83,17 @@ struct GroupLayout {
 // of each access kind (low 16 bits the smaller, 0xFFFF none) and the pc range (low 16 bits
 // the lowest pc, high 16 bits the highest)
 constexpr uint32_t kTupleEmpty = 0xFFFFFFFFu, kTuplePcEmpty = 0x0000FFFFu;
+// The summaries are kept as four planes (reads, writes, atomics, pc range) of this many words
+// each, so that the lanes of a warp on consecutive words touch consecutive banks.
+__host__ __device__ inline uint32_t tuple_plane_words(uint32_t shw) { return (shw + 31u) & ~31u; }
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 // The fixed-size arrays come first, at offsets known at compile time; the arrays whose
 // size depends on the launch follow.
 constexpr uint32_t kGroupClk = 0, kGroupRlo = 128, kGroupRhi = 256, kGroupRsp = 384, kGroupPark = 512,
                    kGroupBv = 512 + 32 * 8 * 4, kGroupFixed = kGroupBv + 64;
 // With `uninit`: per-pc counters of loads of unwritten words, and the bitmap of written words.
-// With `fused`: a 4-word summary per shared word, the words touched in the interval, and a
-// bitmap of its racy words.
+// With `fused`: the four summary planes, the words touched in the interval, and a bitmap of
+// its racy words.
 __host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode, uint32_t nrows,
                                                    uint32_t uninit, uint32_t fused) {
   GroupLayout g;
@@ -111,7 +114,7 @@ __host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw,
   }
   g.tup = g.touched = g.rbm = 0;
   if (fused) {
-    g.tup = o;     o += align16(shw * 16u);
+    g.tup = o;     o += 16u * tuple_plane_words(shw);
     g.touched = o; o += align16(shw * 2u);
     g.rbm = o;     o += align16((shw + 31u) / 32u * 4u);
   }
@@ -127,7 +130,9 @@ cudaError_t init_kernel_attributes(uint32_t smem_optin);
 cudaError_t init_interp_attributes(uint32_t smem_optin);
 cudaError_t init_check_attributes(uint32_t smem_optin);
 cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, uint32_t variant, cudaStream_t s);
-cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, cudaStream_t s);
+// fused: run the instantiation with the fused race check (launches whose `fused` is 0 still
+// log their accesses in it)
+cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, cudaStream_t s);
 uint32_t interp_plain_smem(const LaunchDev& L);
 
 struct CheckArgs {
