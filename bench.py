@@ -64,6 +64,8 @@ def parse():
                     help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
     ap.add_argument("--check-variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="race-check kernel shape (0 = default); setting a shape flag skips the autotuner")
+    ap.add_argument("--fused-check", action="store_true",
+                    help="race check inside the interpreter on per-word summaries (no access log)")
     ap.add_argument("--no-tune", action="store_true", help="library default shapes instead of the autotuner")
     ap.add_argument("--tune-cache", default=None, help="JSON file caching tuned shapes per workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -299,12 +301,15 @@ def run_native(args):
 
     def shapes(m):
         """Kernel shapes for mode m: fixed by the flags, else picked by the autotuner (untimed)."""
-        if args.interp_variant or args.check_variant or args.no_tune:
+        if args.interp_variant or args.check_variant or args.no_tune or args.fused_check:
             o = {"mode": m, "interp_variant": args.interp_variant, "check_variant": args.check_variant}
+            if args.fused_check:
+                o["fused_check"] = 1
             return o, "flags"
         sample = progs[::8] if len(progs) >= 64 else progs     # a strided eighth keeps the mix
         t = autotune.tune(sample, m, cache_path=args.tune_cache)
-        return dict(t.options), ("cache" if t.cached else {"interp_ms": t.interp_ms, "check_ms": t.check_ms})
+        return dict(t.options), ("cache" if t.cached else {"interp_ms": t.interp_ms, "check_ms": t.check_ms,
+                                                           "fused_ms": t.fused_ms})
 
     opts, tuning = shapes(mode)
     with ClockSampler(local) as clocks:
@@ -336,10 +341,12 @@ def run_native(args):
     check_bytes = 8 * st.shared_accesses + 16 * n_reports
     check_gbs = check_bytes / (stage["check"] / 1e3) / 1e9 if stage["check"] > 0 else 0.0
     isha, csha = src_sha("interp.cu", "sr_internal.h"), src_sha("check.cu", "sr_internal.h")
+    fused = bool(opts.get("fused_check"))
     roofline = {"bound": "alu", "kernel": "k_interp_plain" if mode == "plain" else "k_interp_batched",
                 "achieved": interp_rate, "peak": int_peak, "unit": "int32 ops/s", "frac": interp_rate / int_peak,
                 "algorithmic_unit": "simulated thread-instruction",
-                "traffic": traffic_per_launch("k_interp_plain", isha, nblocks) if mode == "plain" else None,
+                "traffic": traffic_per_launch("k_interp_plain", isha, nblocks)
+                if mode == "plain" and not fused else None,
                 "peak_source": "derived: 152 SMs x 128 int32 lanes x sm_max_mhz (MEASURED_PEAKS.json)",
                 "stage_ms": stage,
                 "checker": {"bound": "hbm", "kernel": check_kernel(opts.get("check_variant", 0)),
@@ -348,6 +355,9 @@ def run_native(args):
                             "algorithmic_bytes": "8 B read per logged access + 16 B per race entry",
                             "traffic": traffic_per_launch(check_kernel(opts.get("check_variant", 0)), csha,
                                                           nblocks)}}
+    if fused:      # races decided inside the interpreter: no log is written, the check stage only skips
+        roofline["checker"] = {"bound": None, "kernel": None, "stage_ms": stage["check"],
+                               "note": "fused race check: no access log written or read"}
 
     # ---- end to end through the C ABI from pinned host buffers: per step load_programs (the
     # programs' code and initial arenas host -> device), run_and_check, fetch_reports and one

@@ -1,20 +1,24 @@
 """Autotuner: kernel shapes of a workload picked by measurement.
 
-Three knobs of the library decide how the hot path maps onto the GPU, and the best
+Four knobs of the library decide how the hot path maps onto the GPU, and the best
 setting depends on the workload's block sizes, barrier-interval lengths and shared-array
 sizes:
 
   * interpreter CTAs per SM (``ctas_per_sm``, batched mode) or the register budget of the
     plain interpreter (``interp_variant``): how many simulated blocks share an SM;
   * the race-check kernel shape (``check_variant``): consumer threads per CTA, records per
-    stage, staging (TMA ring or registers) and CTAs per SM -- the log-tile width.
+    stage, staging (TMA ring or registers) and CTAs per SM -- the log-tile width;
+  * where the race check runs (``fused_check``): over the access log after the interpreter,
+    or inside the interpreter on per-word summaries with no log.
 
 (The race check groups records by their whole 14-bit address in one direct-indexed
 table, a one-digit counting sort, so there is no digit width left to choose.)
 
 The stages are separable, so each is tuned on its own time from the library's per-stage
 CUDA events: interpreter candidates with the default checker, then every checker
-variant behind the fastest interpreter.  Every candidate must produce the same reports
+variant behind the fastest interpreter, then the fused check behind that interpreter
+shape, kept only if its whole run beats interpreter plus checker.  Every candidate must
+produce the same reports
 (any difference is a bug, not a tuning outcome).  Choices are cached per workload
 signature (device, mode, program shapes) in a JSON file.
 """
@@ -50,12 +54,13 @@ class Tuned:
     options: Dict[str, int]                       # keyword options for binding.Context
     interp_ms: Dict[str, float] = field(default_factory=dict)
     check_ms: Dict[str, float] = field(default_factory=dict)
+    fused_ms: Optional[float] = None              # interpreter with the fused check, if tried
     cached: bool = False
 
 
-def signature(programs: Sequence[Program], mode: str, device: str) -> str:
+def signature(programs: Sequence[Program], mode: str, device: str, fused: bool = True) -> str:
     """Digest of what the choice depends on: device, mode and every launch's shape."""
-    h = hashlib.sha256(f"{device}|{mode}".encode())
+    h = hashlib.sha256(f"{device}|{mode}|{fused}".encode())
     for p in programs:
         h.update(np.int64(p.ncode).tobytes())
         for l in p.launches:
@@ -96,14 +101,15 @@ def _key(opts: Dict[str, int]) -> str:
 
 
 def tune(programs: Sequence[Program], mode: str = "plain", measure: Optional[Measure] = None,
-         cache_path: Optional[str] = None, device: Optional[str] = None) -> Tuned:
-    """Pick interpreter and checker shapes for `programs` in `mode` ('plain' or 'batched')."""
+         cache_path: Optional[str] = None, device: Optional[str] = None, fused: bool = True) -> Tuned:
+    """Pick interpreter and checker shapes for `programs` in `mode` ('plain' or 'batched');
+    `fused` also tries the fused race check."""
     if mode not in INTERP_CANDIDATES:
         raise ValueError(f"unknown mode {mode!r}")
     if device is None:
         import torch
         device = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
-    sig = signature(programs, mode, device)
+    sig = signature(programs, mode, device, fused)
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
@@ -138,6 +144,16 @@ def tune(programs: Sequence[Program], mode: str = "plain", measure: Optional[Mea
     if len(digests) != 1:
         raise RuntimeError("kernel variants disagree on the reports: a parity bug, not a tuning outcome")
     out.options = dict(best_i, mode=mode, check_variant=best_v)
+    if fused:
+        try:
+            ti, tc, dg = measure(programs, dict(best_i, mode=mode, fused_check=1))
+        except NotApplicable:
+            ti = None
+        if ti is not None:
+            digests.add(dg)
+            out.fused_ms = ti + tc
+            if out.fused_ms < best_t + best_c:
+                out.options = dict(best_i, mode=mode, fused_check=1)
     if cache_path:
         cache[sig] = out.options
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)

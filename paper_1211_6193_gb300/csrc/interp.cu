@@ -39,9 +39,8 @@ struct BlockVars {
   uint32_t cursor;             // log records reserved by the block (stops growing past the log)
   uint32_t n_misc, epoch, k0, flags, decision, err_dirty, status;
   uint32_t bar_np, bar_nw;     // at a release: true predicates, released threads
-  uint32_t ntouched;           // fused race check: words touched in the interval
   uint32_t race_out;           // fused race check: race entries written so far
-  uint32_t pad[4];
+  uint32_t pad[5];
 };
 static_assert(sizeof(BlockVars) <= 64, "block vars");
 
@@ -194,57 +193,33 @@ __device__ __forceinline__ void log_access(BlockVars* bv, unsigned long long* re
 
 // ---- fused race check (Sec. 3.1: each shared location keeps the accesses made to it since
 // the last barrier).  The summary of a word: the two smallest distinct tids per access kind
-// and the pc range, enough to decide its races exactly; the first access of an interval to a
-// word lists the word.  Plane k of the summaries starts at tup + k * tps.
+// and the lowest and highest pc, enough to decide its races exactly.  Plane q of the
+// summaries starts at tup + q * tps: planes 2k and 2k+1 hold the smallest and second
+// smallest tid of kind k, planes 6 and 7 the pc range.  Every field is updated by one
+// atomic min or max, so an access waits on at most one returned value.
 //
-// Whole warp (converged): lanes with `inb` add their access to word `addr`.
-__device__ __forceinline__ void tuple_add(uint32_t* tup, uint32_t tps, uint16_t* touched, BlockVars* bv, bool inb,
-                                          uint32_t addr, uint32_t tid, uint32_t kind, uint32_t pc, uint32_t lane) {
-  bool first = false;
-  if (inb) {
-    uint32_t* T = tup + kind * tps + addr;
-    uint32_t old = *reinterpret_cast<volatile uint32_t*>(T);
-    for (;;) {
-      const uint32_t m1 = old & 0xFFFFu, m2 = old >> 16;
-      uint32_t nw = old;
-      if (tid != m1 && tid != m2) nw = tid < m1 ? (m1 << 16 | tid) : (tid < m2 ? (tid << 16 | m1) : old);
-      if (nw == old) break;
-      const uint32_t prev = atomicCAS(T, old, nw);
-      if (prev == old) break;
-      old = prev;
-    }
-    uint32_t* P = tup + 3u * tps + addr;
-    old = *reinterpret_cast<volatile uint32_t*>(P);
-    for (;;) {
-      const uint32_t nw = max(old >> 16, pc) << 16 | min(old & 0xFFFFu, pc);
-      if (nw == old) break;
-      const uint32_t prev = atomicCAS(P, old, nw);
-      if (prev == old) {
-        first = old == kTuplePcEmpty;
-        break;
-      }
-      old = prev;
-    }
-  }
-  const uint32_t fm = __ballot_sync(FULL, first);
-  if (fm) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&bv->ntouched, (uint32_t)__popc(fm));
-    base = __shfl_sync(FULL, base, 0);
-    if (first) touched[base + __popc(fm & ((1u << lane) - 1u))] = (uint16_t)addr;
-  }
+// Lanes with `inb` add their access to word `addr`.  Inserting tid into (m1, m2): the min
+// into m1 returns the old m1, and the larger of the two (unless equal or empty) is the
+// candidate for m2; every value that leaves or misses m1 reaches m2, so m2 ends as the
+// smallest tid different from m1.
+__device__ __forceinline__ void tuple_add(uint32_t* tup, uint32_t tps, bool inb, uint32_t addr, uint32_t tid,
+                                          uint32_t kind, uint32_t pc) {
+  if (!inb) return;
+  uint32_t* T = tup + addr;
+  atomicMin(T + 6u * tps, pc);
+  atomicMax(T + 7u * tps, pc);
+  const uint32_t o = atomicMin(T + 2u * kind * tps, tid);
+  if (o != tid && o != kTupleEmpty) atomicMin(T + (2u * kind + 1u) * tps, max(o, tid));
 }
 
 // Conflict classes and the smallest conflicting pair of a word from its summary (two threads
 // conflict when distinct and write-write, write-read, write-atomic or atomic-read); false when
 // the word has no race.
-__device__ __forceinline__ bool tuple_race(uint32_t r, uint32_t w, uint32_t a, uint32_t pcr, uint32_t& bout,
-                                           uint32_t& cout) {
-  const uint32_t R[2] = {r & 0xFFFFu, r >> 16}, W[2] = {w & 0xFFFFu, w >> 16};
-  const uint32_t A[2] = {a & 0xFFFFu, a >> 16};
+__device__ __forceinline__ bool tuple_race(const uint32_t* T, uint32_t tps, uint32_t& bout, uint32_t& cout) {
+  const uint32_t R[2] = {T[0], T[tps]}, W[2] = {T[2u * tps], T[3u * tps]}, A[2] = {T[4u * tps], T[5u * tps]};
   uint32_t cls = 0, best = 0xFFFFFFFFu;
   auto pair = [&](uint32_t x, uint32_t y, uint32_t bit) {
-    if (x == 0xFFFFu || y == 0xFFFFu || x == y) return;
+    if (x == kTupleEmpty || y == kTupleEmpty || x == y) return;
     cls |= bit;
     best = min(best, min(x, y) << 16 | max(x, y));
   };
@@ -259,27 +234,36 @@ __device__ __forceinline__ bool tuple_race(uint32_t r, uint32_t w, uint32_t a, u
     }
   if (!cls) return false;
   bout = best;
-  cout = cls << 24 | (pcr & 0xFFFu) << 12 | ((pcr >> 16) & 0xFFFu);
+  cout = cls << 24 | (T[6u * tps] & 0xFFFu) << 12 | (T[7u * tps] & 0xFFFu);
   return true;
 }
 
-// End of an interval, every warp of the block: its share of the touched words.  A racy word
-// keeps its pair and class|pcs in its read and write summaries and is marked in the bitmap;
-// every other word is cleared for the next interval.
-__device__ __forceinline__ void tuples_mark(uint32_t* tup, uint32_t tps, const uint16_t* touched, uint32_t* rbm,
-                                            uint32_t n, uint32_t tid, uint32_t nthr) {
-  for (uint32_t i = tid; i < n; i += nthr) {
-    const uint32_t a = touched[i];
-    uint32_t* T = tup + a;
-    uint32_t b, c;
-    if (tuple_race(T[0], T[tps], T[2u * tps], T[3u * tps], b, c)) {
-      T[0] = b;
-      T[tps] = c;
-      atomicOr(&rbm[a >> 5], 1u << (a & 31u));
-    } else {
-      T[0] = T[tps] = T[2u * tps] = kTupleEmpty;
-      T[3u * tps] = kTuplePcEmpty;
+__device__ __forceinline__ void tuple_clear(uint32_t* T, uint32_t tps) {
+#pragma unroll
+  for (uint32_t q = 0; q < 7; ++q) T[q * tps] = kTupleEmpty;
+  T[7u * tps] = 0;
+}
+
+// End of an interval, every warp of the block: words 32 j .. 32 j + 31 for its share of j.
+// A racy word keeps its pair and class|pcs in planes 0 and 1 and is marked in the bitmap;
+// every other touched word is cleared for the next interval.
+__device__ __forceinline__ void tuples_mark(uint32_t* tup, uint32_t tps, uint32_t* rbm, uint32_t w, uint32_t nw,
+                                            uint32_t lane) {
+  for (uint32_t j = w; j < tps / 32u; j += nw) {
+    uint32_t* T = tup + 32u * j + lane;
+    bool racy = false;
+    if (T[6u * tps] != kTupleEmpty) {
+      uint32_t b, c;
+      racy = tuple_race(T, tps, b, c);
+      if (racy) {
+        T[0] = b;
+        T[tps] = c;
+      } else {
+        tuple_clear(T, tps);
+      }
     }
+    const uint32_t m = __ballot_sync(FULL, racy);
+    if (lane == 0) rbm[j] = m;
   }
 }
 
@@ -288,9 +272,9 @@ __device__ __forceinline__ void tuples_mark(uint32_t* tup, uint32_t tps, const u
 // cleared.  A racy word had at least two accesses, so the entries fit wherever the region is
 // sized by the accesses on a path; past `front_cap` record slots (a loop kernel's fixed
 // region) entries are dropped and the block is flagged, as the access log would be.
-__device__ void tuples_emit(uint32_t* tup, uint32_t tps, uint32_t* rbm, uint32_t shw, BlockVars* bv,
+__device__ void tuples_emit(uint32_t* tup, uint32_t tps, const uint32_t* rbm, BlockVars* bv,
                             unsigned long long* region, uint32_t front_cap, uint32_t epoch, uint32_t lane) {
-  const uint32_t nbw = (shw + 31u) / 32u;
+  const uint32_t nbw = tps / 32u;
   const uint32_t cap = front_cap / 2u;           // entries that fit
   uint32_t ro = bv->race_out;
   bool over = false;
@@ -315,10 +299,8 @@ __device__ void tuples_emit(uint32_t* tup, uint32_t tps, uint32_t* rbm, uint32_t
       else
         over = true;
       ++pos;
-      T[0] = T[tps] = T[2u * tps] = kTupleEmpty;
-      T[3u * tps] = kTuplePcEmpty;
+      tuple_clear(T, tps);
     }
-    if (wd < nbw) rbm[wd] = 0;
     ro += __shfl_sync(FULL, inc, 31);
   }
   ro = min(ro, cap);
@@ -326,7 +308,6 @@ __device__ void tuples_emit(uint32_t* tup, uint32_t tps, uint32_t* rbm, uint32_t
   __syncwarp();
   if (lane == 0) {
     bv->race_out = ro;
-    bv->ntouched = 0;
     bv->cursor = 2u * ro;                        // record slots the entries occupy
   }
   __syncwarp();
@@ -416,7 +397,6 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   uint32_t* wb = reinterpret_cast<uint32_t*>(gsm + G.wb);      // with `uninit` only
   uint32_t* tup = reinterpret_cast<uint32_t*>(gsm + G.tup);    // with `fused` only
   const uint32_t tps = tuple_plane_words(shw);
-  uint16_t* touched = reinterpret_cast<uint16_t*>(gsm + G.touched);
   uint32_t* rbm = reinterpret_cast<uint32_t*>(gsm + G.rbm);
   BlockVars* bv = reinterpret_cast<BlockVars*>(gsm + kGroupBv);
   int32_t* arena = A.arena + Ls->arena_off;
@@ -441,14 +421,14 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     for (uint32_t i = tid; i < (shw + 31u) / 32u; i += nthr) wb[i] = 0;
   }
   if (fused) {
-    for (uint32_t i = tid; i < 4u * tps; i += nthr) tup[i] = i < 3u * tps ? kTupleEmpty : kTuplePcEmpty;
+    for (uint32_t i = tid; i < 8u * tps; i += nthr) tup[i] = i < 7u * tps ? kTupleEmpty : 0u;
     for (uint32_t i = tid; i < (shw + 31u) / 32u; i += nthr) rbm[i] = 0;
   }
   if (tid == 0) {
     bv->cursor = 0;
     bv->n_misc = 0; bv->epoch = 0; bv->k0 = 0; bv->flags = 0;
     bv->decision = 0; bv->err_dirty = 0; bv->status = 0;
-    bv->ntouched = 0; bv->race_out = 0;
+    bv->race_out = 0;
   }
   if (lane == 0) clk[w] = 0;
   group_sync(bar_id, nthr);
@@ -527,7 +507,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (shared) {
               if (logging) {
                 if (fused) {
-                  tuple_add(tup, tps, touched, bv, inb, (uint32_t)addr, tid, K_R, p, lane);
+                  tuple_add(tup, tps, inb, (uint32_t)addr, tid, K_R, p);
                   n_sacc += inb;
                 } else {
                   log_access(bv, region, front_cap, inb,
@@ -582,7 +562,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (shared) {
               if (logging) {
                 if (fused) {
-                  tuple_add(tup, tps, touched, bv, inb, (uint32_t)addr, tid, K_W, p, lane);
+                  tuple_add(tup, tps, inb, (uint32_t)addr, tid, K_W, p);
                   n_sacc += inb;
                 } else {
                   log_access(bv, region, front_cap, inb,
@@ -612,7 +592,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
             if (em) note_err(err, bv, p, w, em, lane);
             if (logging) {
                 if (fused) {
-                  tuple_add(tup, tps, touched, bv, inb, (uint32_t)addr, tid, K_A, p, lane);
+                  tuple_add(tup, tps, inb, (uint32_t)addr, tid, K_A, p);
                   n_sacc += inb;
                 } else {
                   log_access(bv, region, front_cap, inb,
@@ -700,7 +680,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     }
     group_sync(bar_id, nthr);
     if (fused) {                                 // the interval's touched words, all warps
-      tuples_mark(tup, tps, touched, rbm, bv->ntouched, tid, nthr);
+      tuples_mark(tup, tps, rbm, w, nw, lane);
       group_sync(bar_id, nthr);
     }
 
@@ -719,7 +699,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const uint32_t fl = __reduce_or_sync(FULL, v ? pb.w & 0xFFu : 0u);
       const uint32_t nP = __reduce_add_sync(FULL, v ? pb.w >> 8 : 0u);
       const uint32_t ep = bv->epoch;
-      if (fused) tuples_emit(tup, tps, rbm, shw, bv, region, log_cap - 2u * bv->n_misc, ep, lane);
+      if (fused) tuples_emit(tup, tps, rbm, bv, region, log_cap - 2u * bv->n_misc, ep, lane);
       uint32_t dec, kind = 0, a = 0, b = 0, c = 0, stbits = 0;
       if (fl & 2u) {
         dec = DEC_STOP;

@@ -77,14 +77,12 @@ struct RunArgs {
 
 // Shared-memory footprint of one simulated block in the interpreter.
 struct GroupLayout {
-  uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, un, wb, tup, touched, rbm, total;
+  uint32_t regs, sh, clk, rlo, rhi, rsp, park, err, bv, un, wb, tup, rbm, total;
 };
-// the summary of one shared word in the fused race check: the two smallest distinct tids
-// of each access kind (low 16 bits the smaller, 0xFFFF none) and the pc range (low 16 bits
-// the lowest pc, high 16 bits the highest)
-constexpr uint32_t kTupleEmpty = 0xFFFFFFFFu, kTuplePcEmpty = 0x0000FFFFu;
-// The summaries are kept as four planes (reads, writes, atomics, pc range) of this many words
-// each, so that the lanes of a warp on consecutive words touch consecutive banks.
+// The summary of one shared word in the fused race check: the two smallest distinct tids of
+// each access kind (kTupleEmpty none) and the lowest and highest pc, eight planes of this
+// many words each, so that the lanes of a warp on consecutive words touch consecutive banks.
+constexpr uint32_t kTupleEmpty = 0xFFFFFFFFu;
 __host__ __device__ inline uint32_t tuple_plane_words(uint32_t shw) { return (shw + 31u) & ~31u; }
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 // The fixed-size arrays come first, at offsets known at compile time; the arrays whose
@@ -92,8 +90,7 @@ __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15
 constexpr uint32_t kGroupClk = 0, kGroupRlo = 128, kGroupRhi = 256, kGroupRsp = 384, kGroupPark = 512,
                    kGroupBv = 512 + 32 * 8 * 4, kGroupFixed = kGroupBv + 64;
 // With `uninit`: per-pc counters of loads of unwritten words, and the bitmap of written words.
-// With `fused`: the four summary planes, the words touched in the interval, and a bitmap of
-// its racy words.
+// With `fused`: the eight summary planes and a bitmap of the interval's racy words.
 __host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw, uint32_t ncode, uint32_t nrows,
                                                    uint32_t uninit, uint32_t fused) {
   GroupLayout g;
@@ -112,11 +109,10 @@ __host__ __device__ inline GroupLayout group_layout(uint32_t nthr, uint32_t shw,
     g.un = o; o += align16(2u * (ncode + 1) * 4u);
     g.wb = o; o += align16((shw + 31u) / 32u * 4u);
   }
-  g.tup = g.touched = g.rbm = 0;
+  g.tup = g.rbm = 0;
   if (fused) {
-    g.tup = o;     o += 16u * tuple_plane_words(shw);
-    g.touched = o; o += align16(shw * 2u);
-    g.rbm = o;     o += align16((shw + 31u) / 32u * 4u);
+    g.tup = o;     o += 32u * tuple_plane_words(shw);
+    g.rbm = o;     o += align16(tuple_plane_words(shw) / 8u);
   }
   g.total = o;
   return g;
