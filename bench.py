@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
     ap.add_argument("--interp-variant", type=int, default=0, choices=[0, 1, 2],
                     help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
-    ap.add_argument("--check-variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--check-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="race-check kernel shape (0 = default); setting a shape flag skips the autotuner")
     ap.add_argument("--fused-check", action="store_true",
                     help="race check inside the interpreter on per-word summaries (no access log)")

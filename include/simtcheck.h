@@ -162,7 +162,8 @@ typedef struct {
                                      context owns (freed memory is kept for reuse until
                                      sr_destroy) */
   uint32_t check_variant;    /* race-check kernel shape, 1..SR_CHECK_VARIANTS (consumer threads,
-                                records per stage, stages, CTAs per SM); 0 = the default */
+                                records per stage, staging, CTAs per SM, address-table size);
+                                0 = the default */
   uint32_t check_uninit;     /* 1 = also report loads of shared words not yet written
                                 (SR_REP_ERR_UNINIT_SHARED); 0 = off */
   uint32_t fused_check;      /* 1 = the interpreter keeps each shared word's access summary itself
@@ -172,7 +173,7 @@ typedef struct {
                                 race-check kernel */
 } sr_opts;
 
-#define SR_CHECK_VARIANTS 4
+#define SR_CHECK_VARIANTS 5
 
 typedef struct {
   uint64_t thread_instrs;    /* simulated thread-instructions executed */

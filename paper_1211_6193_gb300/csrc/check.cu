@@ -197,12 +197,13 @@ __device__ uint32_t scan_bitmap(const uint32_t* bm, uint32_t* pre, uint32_t nw, 
 }
 
 // One record (low and high words) into the address table, the tag in the high bits of
-// tagw.  An entry that becomes racy marks the interval in *racy.
+// tagw.  An entry that becomes racy marks the interval in *racy; an address past the table
+// sets `oor` and is left out.
 __device__ __forceinline__ void table_add(uint32_t* tab, uint32_t ntab, uint32_t lo, uint32_t hi, uint32_t tagw,
-                                          uint32_t tag, volatile uint32_t* racy, bool& bad) {
+                                          uint32_t tag, volatile uint32_t* racy, bool& oor) {
   const uint32_t a = __funnelshift_r(lo, hi, 24) & 0x3FFFu;   // record bits 24..37
   if (a >= ntab) {
-    bad = true;
+    oor = true;
     return;
   }
   const uint32_t t4 = (lo >> 10) & 0x3FF0u;                   // tid << 4
@@ -228,13 +229,13 @@ __device__ __forceinline__ void table_add(uint32_t* tab, uint32_t ntab, uint32_t
 template <uint32_t P>
 __device__ __forceinline__ void table_add_set(uint32_t* tab, uint32_t ntab, const uint32_t (&lo)[P],
                                               const uint32_t (&hi)[P], uint32_t m, uint32_t tagw, uint32_t tag,
-                                              volatile uint32_t* racy, bool& bad) {
+                                              volatile uint32_t* racy, bool& oor) {
   uint32_t a[P], x[P], o[P], n[P];
 #pragma unroll
   for (uint32_t j = 0; j < P; ++j) {
     a[j] = __funnelshift_r(lo[j], hi[j], 24) & 0x3FFFu;
     if (((m >> j) & 1u) && a[j] >= ntab) {
-      bad = true;
+      oor = true;
       m &= ~(1u << j);
     }
     x[j] = ((lo[j] >> 10) & 0x3FF0u) | 1u << ((lo[j] >> 12) & 3u);
@@ -259,7 +260,7 @@ __device__ __forceinline__ void table_add_set(uint32_t* tab, uint32_t ntab, cons
   if (retry) {
 #pragma unroll
     for (uint32_t j = 0; j < P; ++j)
-      if ((retry >> j) & 1u) table_add(tab, ntab, lo[j], hi[j], tagw, tag, racy, bad);
+      if ((retry >> j) & 1u) table_add(tab, ntab, lo[j], hi[j], tagw, tag, racy, oor);
   }
 }
 
@@ -296,11 +297,12 @@ __device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t ntab, uin
   const uint32_t DS = ntab / 4;                   // exact summaries per round (4 table words each)
   constexpr uint32_t NCW = NC / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const uint32_t nw = (shw + 31u) >> 5;
+  const uint32_t lim = min(shw, ntab);            // every address of the interval is below both
+  const uint32_t nw = (lim + 31u) >> 5;
   for (uint32_t wd = warp; wd < nw; wd += NCW) {
     const uint32_t a = wd * 32u + lane;
-    const uint32_t x = a < shw ? tab[a] : 0u;
-    const uint32_t bits = __ballot_sync(FULL, a < shw && (x & ~0x3FFFu) == tagw && entry_racy(x));
+    const uint32_t x = a < lim ? tab[a] : 0u;
+    const uint32_t bits = __ballot_sync(FULL, a < lim && (x & ~0x3FFFu) == tagw && entry_racy(x));
     if (lane == 0) bm[wd] = bits;
   }
   cbar<NC>();
@@ -313,7 +315,7 @@ __device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t ntab, uin
     for (uint32_t i = s + tid; i < e; i += NC) {
       const unsigned long long r = region[i];
       const uint32_t a = rec_addr(r);
-      if (a >= shw) continue;                     // (a logged address is always below shw)
+      if (a >= lim) continue;                     // (a logged address is always below lim)
       const uint32_t word = bm[a >> 5], bit = 1u << (a & 31u);
       if (!(word & bit)) continue;
       const uint32_t rank = pre[a >> 5] + __popc(word & (bit - 1u)) - r0;
@@ -341,21 +343,46 @@ __device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t ntab, uin
   return M;
 }
 
-// End of the interval [s, e) with epoch `epoch` (consumers synchronised): races of a
-// racy interval, then the next tag and parity.
+// An interval with an address past the shared-memory table (a launch whose shared array is
+// larger than the table): its records, still intact in the log, go into the CTA's spill
+// table in global memory (kCheckBins entries, zeroed on first use), under the same tag.  An
+// address past the shared array there is a corrupt record.  Consumers synchronised on
+// entry and on return.
 template <uint32_t NC>
-__device__ __forceinline__ void close_interval(uint32_t* tab, uint32_t ntab, uint32_t* bm, uint32_t* pre,
+__device__ __noinline__ void spill_interval(uint32_t* gtab, uint32_t shw, const unsigned long long* region,
+                                            uint32_t s, uint32_t e, uint32_t tagw, uint32_t tag,
+                                            volatile uint32_t* racy, bool& bad, bool& g_ready) {
+  if (!g_ready) {
+    for (uint32_t i = threadIdx.x; i < kCheckBins; i += NC) gtab[i] = 0;
+    g_ready = true;
+    cbar<NC>();
+  }
+  for (uint32_t i = s + threadIdx.x; i < e; i += NC) {
+    const unsigned long long r = region[i];
+    table_add(gtab, shw, (uint32_t)r, (uint32_t)(r >> 32), tagw, tag, racy, bad);
+  }
+  cbar<NC>();
+}
+
+// End of the interval [s, e) with epoch `epoch` (consumers synchronised): races of a
+// racy interval, from the spill table if the interval went there, then the next tag and
+// parity.
+template <uint32_t NC>
+__device__ __forceinline__ void close_interval(uint32_t* tab, uint32_t ntab, uint32_t* gtab, bool spilled,
+                                               bool& g_ready, uint32_t* bm, uint32_t* pre,
                                                uint32_t* wtot, uint4* stage_out, volatile uint32_t* s_racy,
                                                unsigned long long* region, uint32_t& race_out, uint32_t shw,
                                                uint32_t& iv, uint32_t& par, uint32_t& tag, uint32_t& tagw,
                                                uint32_t epoch, uint32_t s, uint32_t e) {
   if (s_racy[par] == tag)
-    race_out += racy_interval<NC>(tab, ntab, bm, pre, wtot, stage_out, region, race_out, shw, tagw, epoch, s, e);
+    race_out += racy_interval<NC>(spilled ? gtab : tab, spilled ? kCheckBins : ntab, bm, pre, wtot, stage_out, region,
+                                  race_out, shw, tagw, epoch, s, e);
   par ^= 1u;
   if (++iv % TAG_MOD == 0) {                      // tags wrap: forget every entry
     cbar<NC>();                                   // everyone has read s_racy
     for (uint32_t i = threadIdx.x; i < ntab; i += NC) tab[i] = 0;
     if (threadIdx.x < 2) s_racy[threadIdx.x] = 0;
+    g_ready = false;                              // the spill table is zeroed again before its next use
     cbar<NC>();
     ++iv;
   }
@@ -377,11 +404,12 @@ __device__ __forceinline__ uint32_t stage_pass(
     const uint32_t (&hi)[PER], uint32_t nval, uint32_t cbase, uint32_t e0, uint32_t ebefore, uint32_t elast,
     bool first, bool last, uint32_t pos, uint32_t cnt, uint32_t n, uint32_t gb, unsigned long long* region,
     uint32_t shw, uint32_t& race_out, uint32_t& ep, uint32_t& ivs, uint32_t& iv, uint32_t& par, uint32_t& tag,
-    uint32_t& tagw, bool& bad, Release release) {
+    uint32_t& tagw, bool& bad, uint32_t* gtab, bool& ovf, bool& g_ready, Release release) {
   uint32_t why = (!first && e0 != ep) ? 1u : 0u;
   for (;;) {
     if (why) {
-      cbar<NC>();
+      const bool spill = cbar_or<NC>(ovf);        // some record of the interval was past the table
+      ovf = false;
       uint32_t end = n, nep = ep;
       if (why == 1) {
         end = pos;
@@ -395,8 +423,9 @@ __device__ __forceinline__ uint32_t stage_pass(
         }
         end = pos + np;
       }
-      close_interval<NC>(tab, ntab, bm, pre, wtot, stage_out, s_racy, region, race_out, shw, iv, par, tag, tagw, ep,
-                         ivs, end);
+      if (spill) spill_interval<NC>(gtab, shw, region, ivs, end, tagw, tag, s_racy + par, bad, g_ready);
+      close_interval<NC>(tab, ntab, gtab, spill, g_ready, bm, pre, wtot, stage_out, s_racy, region, race_out, shw, iv,
+                         par, tag, tagw, ep, ivs, end);
       if (why == 3) {
         if (threadIdx.x == 0) blocks[gb].n_race = race_out;
         return 3;
@@ -420,7 +449,7 @@ __device__ __forceinline__ uint32_t stage_pass(
         }
       }
     }
-    if (__any_sync(FULL, m != 0)) table_add_set<PER>(tab, ntab, lo, hi, m, tagw, tag, s_racy + par, bad);
+    if (__any_sync(FULL, m != 0)) table_add_set<PER>(tab, ntab, lo, hi, m, tagw, tag, s_racy + par, ovf);
     if (elast != ep) {
       why = 2;
       continue;
@@ -571,6 +600,8 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_check(CheckArgs A) {
   // -------------------------------------------------------------- consumer warps
   const uint32_t cbase = tid * C::PER;
   uint4* const stage_out = A.scratch + (size_t)blockIdx.x * kScratchWords;
+  uint32_t* const gtab = reinterpret_cast<uint32_t*>(stage_out + kCheckBins);
+  bool ovf = false, g_ready = false;
   uint32_t iv = 1, par = 0, tag = 1, tagw = 1u << 14;
   // per block
   unsigned long long* region = nullptr;
@@ -617,7 +648,7 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_check(CheckArgs A) {
     const uint32_t why = stage_pass<NC, C::PER>(
         tab, NB, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, lo, hi, nval, cbase, e0, ebefore, elast,
         d_flags & 1u, d_flags & 2u, d_pos, d_cnt, d_n, gb, region, shw, race_out, ep, ivs, iv, par, tag, tagw, bad,
-        [&]() {
+        gtab, ovf, g_ready, [&]() {
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[buf]);   // the stage may be refilled
         });
@@ -721,6 +752,8 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
   uint32_t* wtot = misc + 8;
   const uint32_t tid = threadIdx.x, cbase = tid * PER;
   uint4* const stage_out = A.scratch + (size_t)blockIdx.x * kScratchWords;
+  uint32_t* const gtab = reinterpret_cast<uint32_t*>(stage_out + kCheckBins);
+  bool ovf = false, g_ready = false;
 
   for (uint32_t i = tid; i < ntab; i += NC) tab[i] = 0;
   if (tid < 8) misc[tid] = 0;
@@ -780,7 +813,7 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
         const uint32_t how =
             stage_pass<NC, PER>(tab, ntab, bm, pre, wtot, stage_out, s_racy, s_npos, s_nep, A.blocks, clo, chi, nval,
                                 cbase, e0, ebefore, elast, pos == 0, last, pos, cnt, n, gb, region, shw, race_out, ep,
-                                ivs, iv, par, tag, tagw, bad, []() {});
+                                ivs, iv, par, tag, tagw, bad, gtab, ovf, g_ready, []() {});
         if (how == 2) {                           // (uniform) epochs out of order: give up
           stop = true;
           break;
@@ -846,17 +879,22 @@ struct VariantEntry {
   cudaError_t (*init)(uint32_t);
   cudaError_t (*launch)(const CheckArgs&, uint32_t, cudaStream_t);
   uint32_t ctas_per_sm;
+  uint32_t table_cap;           // shared-memory address table entries at most
 };
-template <class V, uint32_t MINB>
-constexpr VariantEntry entry() { return VariantEntry{&V::init, &V::launch, MINB}; }
+template <class V, uint32_t MINB, uint32_t CAP>
+constexpr VariantEntry entry() { return VariantEntry{&V::init, &V::launch, MINB, CAP}; }
 
+// The TMA-ring kernels always hold the whole table.  The register-staged ones size it to
+// the wave; one-warp CTAs take a smaller cap so that sixteen fit an SM, each checking its
+// own simulated block.
 const VariantEntry kVariants[SR_CHECK_VARIANTS] = {
-    entry<CheckVariant<256, 1024, 3, 2>, 2>(),
-    entry<CheckVariant<128, 512, 4, 3>, 3>(),
-    entry<RegVariant<128, 4, 4>, 4>(),
-    entry<RegVariant<64, 4, 8>, 8>(),
+    entry<CheckVariant<256, 1024, 3, 2>, 2, kCheckBins>(),
+    entry<CheckVariant<128, 512, 4, 3>, 3, kCheckBins>(),
+    entry<RegVariant<128, 4, 4>, 4, kCheckTableCap>(),
+    entry<RegVariant<64, 4, 8>, 8, kCheckTableCap>(),
+    entry<RegVariant<32, 4, 16>, 16, kCheckTableCap / 2>(),
 };
-constexpr uint32_t kDefaultVariant = 3;
+constexpr uint32_t kDefaultVariant = 4;
 
 const VariantEntry& variant_entry(uint32_t v) {
   return kVariants[(v >= 1 && v <= SR_CHECK_VARIANTS ? v : kDefaultVariant) - 1];
@@ -866,6 +904,7 @@ const VariantEntry& variant_entry(uint32_t v) {
 
 uint32_t check_default_variant() { return kDefaultVariant; }
 uint32_t check_ctas_per_sm(uint32_t variant) { return variant_entry(variant).ctas_per_sm; }
+uint32_t check_table_cap(uint32_t variant) { return variant_entry(variant).table_cap; }
 
 cudaError_t init_check_attributes(uint32_t smem_optin) {
   for (const VariantEntry& v : kVariants) {

@@ -204,7 +204,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     ca.work_head = heads + wi;
     ca.error_flag = heads + kMaxWaves;
     ca.spin_limit = ra.spin_limit;
-    ca.table_words = sr::check_table_words(L, w.li0, w.li1);
+    ca.table_words = sr::check_table_words(L, w.li0, w.li1, sr::check_table_cap(0));
     const uint32_t ctas = std::min<uint32_t>(cctas, ca.item1 - ca.item0);
     if (ctas) NA_TRY(sr::launch_check(ca, 0, ctas, s));
     sr::CompactArgs ka{};

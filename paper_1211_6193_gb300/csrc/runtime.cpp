@@ -221,7 +221,7 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       ca.work_head = (uint32_t*)b->work_head.p + wi;
       ca.error_flag = (uint32_t*)b->err_flag.p;
       ca.spin_limit = o.spin_limit;
-      ca.table_words = sr::check_table_words(b->launches.data(), w.li0, w.li1);
+      ca.table_words = sr::check_table_words(b->launches.data(), w.li0, w.li1, sr::check_table_cap(o.check_variant));
       ca.item_launch = (const uint32_t*)b->item_launch_d.p;
       CUDA_TRY(c, cudaMemsetAsync(ca.work_head, 0, 4, s));
       const uint32_t ctas = std::min<uint32_t>(b->check_ctas, ca.item1 - ca.item0);

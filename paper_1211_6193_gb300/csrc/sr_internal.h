@@ -147,19 +147,27 @@ struct CheckArgs {
 // race-check kernel shapes (variant 1..SR_CHECK_VARIANTS; 0 = default)
 uint32_t check_default_variant();
 uint32_t check_ctas_per_sm(uint32_t variant);
+uint32_t check_table_cap(uint32_t variant);
 cudaError_t launch_check(const CheckArgs& a, uint32_t variant, uint32_t ctas, cudaStream_t s);
-constexpr uint32_t kCheckBins = 12288;         // address table entries (>= the largest shared array)
-constexpr uint32_t kScratchWords = 1u << 14;   // race entries per CTA staged in global memory
+constexpr uint32_t kCheckBins = 12288;         // the largest shared array (words)
+constexpr uint32_t kCheckTableCap = 4096;      // shared-memory address table entries at most (per variant)
+// per checker CTA in global memory: race entries of an interval staged while its summaries
+// take several rounds (at most kCheckBins), then the spill table (kCheckBins words) for the
+// intervals that touch words past the shared-memory table
+constexpr uint32_t kScratchWords = 1u << 14;
+static_assert(kScratchWords >= kCheckBins + kCheckBins / 4, "spill table must fit behind the staged entries");
 constexpr uint32_t kCheckItemRecords = 8192;   // log records a check work item aims at
 constexpr uint32_t kCheckMaxGroup = 32;        // blocks per check work item at most
 
 // address-table entries for a wave's race check: one per word of its largest shared array,
-// and room for the exact summaries (4 entries each) of every word in one round
-inline uint32_t check_table_words(const LaunchDev* L, uint32_t li0, uint32_t li1) {
+// and room for the exact summaries (4 entries each) of every word in one round, at most
+// `cap` (the kernel shape's), so that small tables keep more CTAs on an SM.  Intervals
+// touching words past the table are checked in the CTA's spill table instead.
+inline uint32_t check_table_words(const LaunchDev* L, uint32_t li0, uint32_t li1, uint32_t cap) {
   uint32_t m = 8;
   for (uint32_t i = li0; i < li1; ++i) m = L[i].shw > m ? L[i].shw : m;
   m = (4u * m + 31u) & ~31u;
-  return m < kCheckBins ? m : kCheckBins;
+  return m < cap ? m : cap;
 }
 
 // blocks per check work item for a launch whose blocks log at most `log_cap` records

@@ -174,6 +174,36 @@ def _large_interval_programs():
     return out
 
 
+def _uneven_block_logs_programs():
+    """Blocks whose logs differ in length from block to block: block b has (389 b) mod
+    (bdim + 7) active threads (none when b is a multiple of 5), each making three stores, a
+    load and, in blocks with b mod 3 = 1 where the second barrier is skipped, a racing store.
+    Record counts are odd and even, some blocks log nothing, and with 96-thread blocks a work
+    item of the race check holds many blocks, so staged copies run across block ends."""
+    out = []
+    for bdim, grid in ((96, 200), (1024, 24)):
+        a = ir.Asm()
+        a.s2r(ir.r2, ir.TID).s2r(ir.r3, ir.BID)
+        a.mul(ir.r4, ir.r3, 389).rem(ir.r4, ir.r4, bdim + 7)
+        a.rem(ir.r5, ir.r3, 5).sne(ir.r5, ir.r5, 0).mul(ir.r4, ir.r4, ir.r5)
+        a.slt(ir.r7, ir.r2, ir.r4).brz(ir.r7, "skip")
+        for j in range(3):
+            a.sts(ir.r2, ir.r2, bdim * j)
+        a.label("skip").bar().brz(ir.r7, "skip2")
+        a.add(ir.r8, ir.r2, 1).rem(ir.r8, ir.r8, ir.r4).lds(ir.r9, ir.r8)
+        a.label("skip2").rem(ir.r10, ir.r3, 3).seq(ir.r10, ir.r10, 1).brnz(ir.r10, "nobar").bar()
+        a.label("nobar").brz(ir.r7, "out").sts(ir.r2, ir.r9)
+        a.label("out").mul(ir.r11, ir.r3, bdim).add(ir.r11, ir.r11, ir.r2).stg(ir.r11, ir.r9).exit()
+        out.append(ir.Program(a.assemble(), [0], [ir.Launch(0, grid, bdim, 3 * bdim, ())],
+                              np.zeros(grid * bdim, np.int32)))
+    return out
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_blocks_with_uneven_logs(B, mode):
+    assert_parity(B, _uneven_block_logs_programs(), mode)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_intervals_larger_than_a_staged_tile(B, mode):
     assert_parity(B, _large_interval_programs(), mode)
@@ -206,13 +236,14 @@ def test_more_racy_words_than_one_summary_round(B, mode):
     assert len(races) == 2 * (8 + 3 + 12) * 1024
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", range(1, 6))
 def test_every_check_variant(B, variant):
     """Each race-check kernel shape on its own: the table sized to small and large shared
     arrays, intervals with more racy words than a summary round holds, intervals spanning
-    stages, and a batch of generated programs with planted bugs."""
+    stages, blocks of uneven (and empty) logs in one work item, and a batch of generated
+    programs with planted bugs."""
     groups = [  # one batch each, so that each sizes the table to its own largest shared array
-        _many_racy_addresses_programs(), _large_interval_programs()[:2],
+        _many_racy_addresses_programs(), _large_interval_programs()[:2], _uneven_block_logs_programs(),
         families.batch(n_programs=24, seed=31, max_grid=12, bug_rate=0.5),
         [fig1.program(race=True)], [families.reduction_plain(n_blocks=20, bdim=256, seed=2, omit_level=2)],
         [stencil2d.program(log2w=6, steps=3, buggy_launch=1, seed=5)],
