@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving arrival rate (jobs/s)")
     ap.add_argument("--blocks", type=int, default=16384,
                     help="blocks of the reduction (default: the full workload; smaller only for profiling)")
+    ap.add_argument("--programs", type=int, default=4096,
+                    help="programs of the batched workload, the first N of the same seeded batch "
+                         "(default: the full workload; smaller only for profiling)")
     return ap.parse_args()
 
 
@@ -82,12 +85,12 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def workload(name: str, rank: int, blocks: int = 16384):
+def workload(name: str, rank: int, blocks: int = 16384, programs: int = 4096):
     from paper_1211_6193_gb300.workloads import families, stencil2d
     if name == "reduction":
         return [families.reduction_plain(n_blocks=blocks, bdim=1024, seed=1 + rank, omit_level=3)]
     if name == "batched":
-        return families.batch(n_programs=4096, seed=3 + rank)
+        return families.batch(n_programs=programs, seed=3 + rank)
     if name == "serving":
         return families.batch(n_programs=512, seed=5 + rank)
     return [stencil2d.program(log2w=13, steps=16, buggy_launch=8, seed=4 + rank)]
@@ -96,6 +99,8 @@ def workload(name: str, rank: int, blocks: int = 16384):
 def workload_label(args):
     if args.workload == "reduction" and args.blocks != 16384:
         return f"reduction, {args.blocks} blocks x 1024 threads (profiling size)"
+    if args.workload == "batched" and args.programs != 4096:
+        return f"batched, the first {args.programs} of the 4096 seed-generated programs (profiling size)"
     return WORKLOADS[args.workload]
 
 
@@ -166,7 +171,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    progs = workload(args.workload, 0, args.blocks)
+    progs = workload(args.workload, 0, args.blocks, args.programs)
     sample = args.cpu_sample_blocks or default_sample(args.workload)
     for _ in range(args.warmup):
         oracle_rate(progs, 1)
@@ -208,7 +213,7 @@ def traffic_per_launch(kernel: str, src: str, blocks: int):
 
 
 def check_kernel(variant: int) -> str:
-    """Kernel name of a race-check shape (variants 1-2: TMA ring, 3-4: register-staged)."""
+    """Kernel name of a race-check shape (variants 1-2: TMA ring, 3-5: register-staged)."""
     return "k_check" if variant in (1, 2) else "k_check_reg"
 
 
@@ -282,7 +287,7 @@ def run_native(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    progs = workload(args.workload, rank, args.blocks)
+    progs = workload(args.workload, rank, args.blocks, args.programs)
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(pk)) if os.path.exists(pk) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
