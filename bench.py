@@ -201,15 +201,17 @@ def src_sha(*names):
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(kernel: str, src: str, blocks: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+def traffic_per_launch(workload: str, kernel: str, src: str, units: dict):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu capture (taken
+    on a smaller case of the same workload and scaled by its unit, blocks or logged records),
+    if one was taken on this source; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    t = json.load(open(path)).get(kernel)
-    if not t or t.get("src_sha1") != src:
-        return None
-    return t["dram_bytes_per_block"] * blocks
+    for t in json.load(open(path)).get("captures", []):
+        if t["workload"] == workload and t["kernel"] == kernel and t["src_sha1"] == src:
+            return (t["dram_read"] + t["dram_write"]) / t["units"] * units[t["unit"]]
+    return None
 
 
 def check_kernel(variant: int) -> str:
@@ -347,10 +349,11 @@ def run_native(args):
     check_gbs = check_bytes / (stage["check"] / 1e3) / 1e9 if stage["check"] > 0 else 0.0
     isha, csha = src_sha("interp.cu", "sr_internal.h"), src_sha("check.cu", "sr_internal.h")
     fused = bool(opts.get("fused_check"))
+    units = {"block": nblocks, "record": st.shared_accesses}
     roofline = {"bound": "alu", "kernel": "k_interp_plain" if mode == "plain" else "k_interp_batched",
                 "achieved": interp_rate, "peak": int_peak, "unit": "int32 ops/s", "frac": interp_rate / int_peak,
                 "algorithmic_unit": "simulated thread-instruction",
-                "traffic": traffic_per_launch("k_interp_plain", isha, nblocks)
+                "traffic": traffic_per_launch(args.workload, "k_interp_plain", isha, units)
                 if mode == "plain" and not fused else None,
                 "peak_source": "derived: 152 SMs x 128 int32 lanes x sm_max_mhz (MEASURED_PEAKS.json)",
                 "stage_ms": stage,
@@ -358,8 +361,8 @@ def run_native(args):
                             "achieved": check_gbs, "peak": hbm_peak,
                             "unit": "GB/s", "frac": check_gbs / hbm_peak, "peak_source": peak_src,
                             "algorithmic_bytes": "8 B read per logged access + 16 B per race entry",
-                            "traffic": traffic_per_launch(check_kernel(opts.get("check_variant", 0)), csha,
-                                                          nblocks)}}
+                            "traffic": traffic_per_launch(args.workload, check_kernel(opts.get("check_variant", 0)),
+                                                          csha, units)}}
     if fused:      # races decided inside the interpreter: no log is written, the check stage only skips
         roofline["checker"] = {"bound": None, "kernel": None, "stage_ms": stage["check"],
                                "note": "fused race check: no access log written or read"}
