@@ -507,12 +507,18 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   if (e == cudaSuccess) e = up(b->launches_d, b->launches.data(), nl * sizeof(LaunchDev));
   if (e == cudaSuccess) e = up(b->items_d, b->items.data(), b->items.size() * 8);
   if (e == cudaSuccess) e = up(b->item_launch_d, b->item_launch.data(), b->item_launch.size() * 4);
-  // zero the padding between arenas (each starts on a 16-byte boundary)
-  if (e == cudaSuccess && b->total_arena) e = cudaMemsetAsync(b->arena_init.p, 0, b->total_arena * 4, s);
-  for (uint32_t i = 0; i < n && e == cudaSuccess; ++i)
+  // every arena starts on a 16-byte boundary; the up to three padding words after it are
+  // zeroed by copies too, not by a memset: a memset is a kernel, which would wait for SMs that
+  // other batches' kernels hold, and the synchronisation below would wait with it
+  static const int32_t kZeros[4] = {0, 0, 0, 0};
+  for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+    int32_t* dst = (int32_t*)b->arena_init.p + b->arena_off[i];
     if (progs[i].global_words)
-      e = cudaMemcpyAsync((int32_t*)b->arena_init.p + b->arena_off[i], progs[i].global_init,
-                          progs[i].global_words * 4, cudaMemcpyHostToDevice, s);
+      e = cudaMemcpyAsync(dst, progs[i].global_init, progs[i].global_words * 4, cudaMemcpyHostToDevice, s);
+    const uint64_t pad = ((b->arena_words[i] + 3) & ~3ull) - b->arena_words[i];
+    if (pad && e == cudaSuccess)
+      e = cudaMemcpyAsync(dst + b->arena_words[i], kZeros, pad * 4, cudaMemcpyHostToDevice, s);
+  }
   // host buffers are caller-owned: the copies must finish before we return
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {

@@ -159,15 +159,18 @@ class _Flight:
 
 class Server:
     def __init__(self, log_budget_bytes: int = 120 << 30, max_inflight: int = 4, max_batch_jobs: int = 512,
-                 mode: str = "batched"):
+                 mode: str = "batched", **ctx_opts):
         import torch
         self.torch = torch
         self.budget = log_budget_bytes
         self.max_inflight = max_inflight
         self.max_batch_jobs = max_batch_jobs
-        # one context: the server loop is the only host thread using it (device memory from
-        # PyTorch's caching allocator: a freed micro-batch costs no CUDA call)
-        self.ctx = binding.Context(mode=mode, log_budget_mb=max(1, log_budget_bytes >> 20))
+        # one context: the server loop is the only host thread using it.  Device memory comes
+        # from the context's stream-ordered pool by default: a micro-batch then costs no
+        # Python allocator callbacks, which at two jobs per batch were a third of its host
+        # time.  (ctx_opts: further binding.Context options, e.g. kernel shapes.)
+        ctx_opts.setdefault("torch_allocator", False)
+        self.ctx = binding.Context(mode=mode, log_budget_mb=max(1, log_budget_bytes >> 20), **ctx_opts)
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
 
     def close(self):
