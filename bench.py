@@ -366,8 +366,8 @@ def run_native(args):
     roofline = {"bound": "alu", "kernel": "k_interp_plain" if mode == "plain" else "k_interp_batched",
                 "achieved": interp_rate, "peak": int_peak, "unit": "int32 ops/s", "frac": interp_rate / int_peak,
                 "algorithmic_unit": "simulated thread-instruction",
-                "traffic": traffic_per_launch(args.workload, "k_interp_plain", isha, units)
-                if mode == "plain" and not fused else None,
+                "traffic": None if fused else traffic_per_launch(
+                    args.workload, "k_interp_plain" if mode == "plain" else "k_interp_batched", isha, units),
                 "peak_source": "derived: 152 SMs x 128 int32 lanes x sm_max_mhz (MEASURED_PEAKS.json)",
                 "stage_ms": stage,
                 "checker": {"bound": "hbm", "kernel": check_kernel(opts.get("check_variant", 0)),
