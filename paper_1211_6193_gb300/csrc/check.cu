@@ -21,11 +21,20 @@
 // region; every entry consumes at least two records of its interval, so the writes
 // never reach records not yet read.
 //
-// One producer warp per CTA claims groups of blocks and streams their records into a
-// ring of shared-memory stages with TMA bulk copies (cp.async.bulk + mbarrier); the
-// consumer warps take stage after stage and meet at a named barrier only where an
-// interval ends.  Every wait is bounded: a wait that gives up sets the error flag, and
-// the producer drains its copies in flight before the CTA exits.
+// The table is sized to the wave's shared arrays but capped per kernel shape, because a
+// CTA checks one simulated block at a time and the speed follows the blocks in flight
+// per SM; an interval that touches a word past the table is read again into a larger
+// table the CTA keeps in global memory (the spill table) and closed the same way.
+//
+// Two families of kernels share the per-stage logic (stage_pass):
+//   k_check      one producer warp per CTA claims groups of blocks and streams their
+//                records into a ring of shared-memory stages with TMA bulk copies
+//                (cp.async.bulk + mbarrier); every wait is bounded: a wait that gives up
+//                sets the error flag, and the producer drains its copies before exiting;
+//   k_check_reg  every thread loads its own records of the next stage into registers,
+//                with the blocks' first stages pulled into L2 ahead of time; no flag is
+//                waited on.  The one-warp form runs sixteen CTAs per SM.
+// In both, the consumers meet at a named barrier only where an interval ends.
 #include "sr_internal.h"
 
 namespace sr {
