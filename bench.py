@@ -55,7 +55,9 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200 for the native reduction, whose step takes ~4 ms, so "
+                         "that the clock samples, taken every 200 ms, fall inside the timed region; else 10)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="reduction", choices=sorted(WORKLOADS))
@@ -77,7 +79,10 @@ def parse():
     ap.add_argument("--programs", type=int, default=4096,
                     help="programs of the batched workload, the first N of the same seeded batch "
                          "(default: the full workload; smaller only for profiling)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 200 if args.impl == "native" and args.workload == "reduction" else 10
+    return args
 
 
 def dist_env():
