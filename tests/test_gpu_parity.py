@@ -307,6 +307,19 @@ def test_fused_race_check(B, mode):
                   fused_check=True)
 
 
+def test_fused_race_check_matches_the_log_path_on_a_larger_batch(B):
+    """128 generated programs (the first of the batched workload's seeded batch, every family
+    and planted bug kind, shared arrays up to 48 KB, some too large to fuse): the fused check
+    and the access log + race-check kernel give the same reports, arenas and status."""
+    progs = families.batch(n_programs=128, seed=3)
+    log = B.check(progs, mode="batched")
+    fused = B.check(progs, mode="batched", fused_check=True)
+    assert fused.report_tuples() == log.report_tuples()
+    assert len(log.reports) > 0
+    assert all(np.array_equal(a, b) for a, b in zip(fused.arenas, log.arenas))
+    assert list(fused.status) == list(log.status)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_reducing_barriers(B, mode):
     """__syncthreads_and/_or/_count: predicates over full and partial warps, reducing and
