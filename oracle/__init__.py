@@ -38,7 +38,8 @@ class _Instr(C.Structure):
 
 class _Launch(C.Structure):
     _fields_ = [("kernel", C.c_uint32), ("grid", C.c_uint32), ("block_dim", C.c_uint32),
-                ("shmem_words", C.c_uint32), ("nparams", C.c_uint32), ("params", C.c_int32 * 4)]
+                ("shmem_words", C.c_uint32), ("nparams", C.c_uint32), ("params", C.c_int32 * 4),
+                ("stream", C.c_uint32), ("wait", C.c_uint32)]
 
 
 class _Program(C.Structure):
@@ -51,13 +52,13 @@ class _Program(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("round_budget", C.c_uint32), ("check_races", C.c_uint32), ("schedule", C.c_uint32),
                 ("nthreads", C.c_uint32), ("check_interblock", C.c_uint32), ("max_blocks", C.c_uint32),
-                ("check_uninit", C.c_uint32)]
+                ("check_uninit", C.c_uint32), ("check_streams", C.c_uint32)]
 
 
 class _Result(C.Structure):
     _fields_ = [("reports", C.c_void_p), ("nreports", C.c_uint64), ("status", C.POINTER(C.c_uint32)),
                 ("thread_instrs", C.c_uint64), ("shared_accesses", C.c_uint64), ("rounds", C.c_uint64),
-                ("interblock_conflicts", C.c_uint64)]
+                ("interblock_conflicts", C.c_uint64), ("stream_conflicts", C.c_uint64)]
 
 
 _lock = threading.Lock()
@@ -99,6 +100,7 @@ class OracleResult:
     shared_accesses: int
     rounds: int
     interblock_conflicts: int
+    stream_conflicts: int = 0    # check_streams: global words two unordered launches share, one writing
 
     def report_tuples(self):
         return [tuple(int(x) for x in r) for r in self.reports]
@@ -106,7 +108,7 @@ class OracleResult:
 
 def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, schedule: str = "lockstep",
         nthreads: int = 1, check_interblock: bool = False, max_blocks: int = 0,
-        check_uninit: bool = False) -> OracleResult:
+        check_uninit: bool = False, check_streams: bool = False) -> OracleResult:
     """Run ``programs`` (``workloads.ir.Program``) through the oracle."""
     lib = _load()
     keep = []
@@ -121,6 +123,7 @@ def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, sch
             ls[j].shmem_words, ls[j].nparams = l.shmem_words, len(l.params)
             for k, v in enumerate(l.params):
                 ls[j].params[k] = int(v)
+            ls[j].stream, ls[j].wait = getattr(l, "stream", 0), getattr(l, "wait", -1) + 1
         arena = np.array(p.global_init, dtype=np.int32, copy=True)
         arenas.append(arena)
         keep += [code, entries, ls]
@@ -129,7 +132,7 @@ def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, sch
         progs[i].launches, progs[i].nlaunches = C.addressof(ls), len(p.launches)
         progs[i].arena, progs[i].arena_words = (arena.ctypes.data if arena.size else None), arena.size
     opts = _Opts(round_budget, int(check_races), {"lockstep": 0, "sequential": 1}[schedule], nthreads,
-                 int(check_interblock), max_blocks, int(check_uninit))
+                 int(check_interblock), max_blocks, int(check_uninit), int(check_streams))
     res = _Result()
     rc = lib.orc_run(C.addressof(progs), len(programs), C.byref(opts), C.byref(res))
     if rc != 0:
@@ -141,7 +144,7 @@ def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, sch
             C.memmove(reps.ctypes.data, res.reports, n * REPORT_DTYPE.itemsize)
         status = np.array([res.status[i] for i in range(len(programs))], dtype=np.uint32)
         out = OracleResult(arenas, status, reps, int(res.thread_instrs), int(res.shared_accesses),
-                           int(res.rounds), int(res.interblock_conflicts))
+                           int(res.rounds), int(res.interblock_conflicts), int(res.stream_conflicts))
     finally:
         lib.orc_free(C.byref(res))
     return out

@@ -77,6 +77,8 @@ typedef struct {
   uint32_t status;               /* ORC_ST_* seen in this launch */
   /* inter-block conflict bookkeeping (serial mode only) */
   int32_t* writer; int32_t* reader; uint64_t conflicts;
+  /* check_streams: per global word of this launch, 1 = read, 2 = written (serial mode only) */
+  uint8_t* acc;
 } launch_ctx;
 
 typedef struct {
@@ -115,6 +117,7 @@ static void note_uninit(block_t* B, uint32_t pc, uint32_t t) {
 }
 static void note_global(block_t* B, int32_t addr, int is_write) {
   launch_ctx* C = B->C;
+  if (C->acc) C->acc[addr] |= is_write ? 2u : 1u;
   if (!C->writer) return;
   int32_t me = (int32_t)B->block;
   if (is_write) {
@@ -462,6 +465,9 @@ static int validate(const orc_program* P, uint32_t idx) {
     if (L->kernel >= P->nkernels || L->block_dim == 0 || L->block_dim > ORC_MAX_BDIM || L->grid == 0 ||
         L->shmem_words > ORC_MAX_SHMEM || L->nparams > 4) {
       snprintf(g_err, sizeof g_err, "program %u launch %u: bad configuration", idx, l); return -1; }
+    if (L->wait > l) {
+      snprintf(g_err, sizeof g_err, "program %u launch %u: waits for a launch that is not earlier", idx, l);
+      return -1; }
   }
   if (P->arena_words > 0x7FFFFFFFull || (P->arena_words && !P->arena)) {
     snprintf(g_err, sizeof g_err, "program %u: bad arena", idx); return -1; }
@@ -502,8 +508,24 @@ int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc
       writer = malloc(P->arena_words * sizeof(int32_t));
       reader = malloc(P->arena_words * sizeof(int32_t));
     }
-    for (uint32_t l = 0; l < P->nlaunches; ++l) {
+    const uint32_t nl = P->nlaunches;
+    /* the launches each launch follows: the previous one of its stream, the one it waits for */
+    int32_t* dep_prev = malloc((nl ? nl : 1) * sizeof(int32_t));
+    int32_t* dep_wait = malloc((nl ? nl : 1) * sizeof(int32_t));
+    uint8_t* dead = calloc(nl ? nl : 1, 1);   /* stopped (deadlock, step limit) or skipped */
+    uint8_t** acc = (O.check_streams && nth == 1 && P->arena_words) ? calloc(nl ? nl : 1, sizeof(uint8_t*)) : NULL;
+    for (uint32_t l = 0; l < nl; ++l) {
+      dep_prev[l] = -1;
+      for (uint32_t m = l; m-- > 0;)
+        if (P->launches[m].stream == P->launches[l].stream) { dep_prev[l] = (int32_t)m; break; }
+      dep_wait[l] = P->launches[l].wait ? (int32_t)P->launches[l].wait - 1 : -1;
+    }
+    for (uint32_t l = 0; l < nl; ++l) {
       const orc_launch* L = &P->launches[l];
+      if ((dep_prev[l] >= 0 && dead[dep_prev[l]]) || (dep_wait[l] >= 0 && dead[dep_wait[l]])) {
+        dead[l] = 1;                                            /* skipped */
+        continue;
+      }
       uint32_t nblocks = L->grid;
       if (O.max_blocks && O.max_blocks < nblocks) nblocks = O.max_blocks;
       if (writer) {
@@ -517,6 +539,7 @@ int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc
         ctx[i].P = P; ctx[i].prog_idx = p; ctx[i].launch_idx = l; ctx[i].L = L; ctx[i].O = &O;
         ctx[i].budget = budget; ctx[i].reps = &reps[i]; ctx[i].writer = writer; ctx[i].reader = reader;
       }
+      if (acc) ctx[0].acc = acc[l] = calloc(P->arena_words, 1);
       if (nw == 1) {
         for (uint32_t b = 0; b < nblocks; ++b) run_block(&ctx[0], b);
       } else {
@@ -543,8 +566,31 @@ int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc
       }
       free(reps); free(ctx);
       res->status[p] |= st;
-      if (st & (ORC_ST_DEADLOCK | ORC_ST_STEP_LIMIT)) break;   /* later launches skipped */
+      if (st & (ORC_ST_DEADLOCK | ORC_ST_STEP_LIMIT)) dead[l] = 1;   /* launches after it are skipped */
     }
+    if (acc) {
+      /* pairs of launches that no chain of stream order and event waits orders: any global
+         word that both touch, one of them writing, makes the result depend on timing */
+      uint8_t* before = calloc((size_t)(nl ? nl : 1) * (nl ? nl : 1), 1);   /* before[l*nl+m]: m precedes l */
+      for (uint32_t l = 0; l < nl; ++l) {
+        int32_t d[2] = {dep_prev[l], dep_wait[l]};
+        for (int k = 0; k < 2; ++k) {
+          if (d[k] < 0) continue;
+          before[(size_t)l * nl + (uint32_t)d[k]] = 1;
+          for (uint32_t m = 0; m < nl; ++m)
+            if (before[(size_t)(uint32_t)d[k] * nl + m]) before[(size_t)l * nl + m] = 1;
+        }
+      }
+      for (uint32_t l = 0; l < nl; ++l)
+        for (uint32_t m = 0; m < l; ++m) {
+          if (before[(size_t)l * nl + m] || !acc[l] || !acc[m]) continue;
+          for (uint64_t w = 0; w < P->arena_words; ++w)
+            if (((acc[l][w] & 2u) && acc[m][w]) || ((acc[m][w] & 2u) && acc[l][w])) res->stream_conflicts++;
+        }
+      for (uint32_t l = 0; l < nl; ++l) free(acc[l]);
+      free(acc); free(before);
+    }
+    free(dep_prev); free(dep_wait); free(dead);
     free(writer); free(reader);
   }
   qsort(all.v, all.n, sizeof(orc_report), cmp_report);

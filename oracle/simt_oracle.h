@@ -64,9 +64,14 @@ enum { ORC_CLS_WW = 1, ORC_CLS_WR = 2, ORC_CLS_WA = 4, ORC_CLS_AR = 8 };
 enum { ORC_ST_DEADLOCK = 1, ORC_ST_STEP_LIMIT = 2 };
 
 typedef struct { uint32_t op_d_a_b; int32_t imm; } orc_instr;
+/* Sec. 2 and Sec. 3 "Streams and events": launches of one stream run in order; launches of
+ * different streams may run in parallel; a launch may also wait for an event recorded after an
+ * earlier launch (wait = 1 + that launch's index, 0 = none).  A launch is skipped when the
+ * launch before it in its stream, or the one it waits for, stopped or was skipped. */
 typedef struct {
   uint32_t kernel, grid, block_dim, shmem_words, nparams;
   int32_t params[4];
+  uint32_t stream, wait;
 } orc_launch;
 typedef struct {
   const orc_instr* code; uint32_t ncode;
@@ -84,6 +89,8 @@ typedef struct {
   uint32_t check_interblock; /* 1 = flag global words shared between blocks of a launch */
   uint32_t max_blocks;       /* >0: run only blocks [0, max_blocks) of each launch (timing samples) */
   uint32_t check_uninit;     /* 1 = report shared loads of words no thread of the block wrote */
+  uint32_t check_streams;    /* 1 = count global words that two launches no stream or event orders
+                                both touch, one writing (serial mode only) */
 } orc_opts;
 
 typedef struct {
@@ -93,6 +100,7 @@ typedef struct {
   uint64_t shared_accesses;                  /* shared accesses seen by the race check */
   uint64_t rounds;                           /* rounds executed, all blocks */
   uint64_t interblock_conflicts;             /* diagnostic (check_interblock) */
+  uint64_t stream_conflicts;                 /* diagnostic (check_streams) */
 } orc_result;
 
 /* returns 0, or a negative code for an invalid program (nothing is run) */

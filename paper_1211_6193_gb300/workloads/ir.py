@@ -239,21 +239,27 @@ def disassemble(code: np.ndarray) -> List[str]:
 
 @dataclass
 class Launch:
-    """One ``kernel<<<grid, block_dim, shmem>>>(params...)`` call (Sec. 2, kernel configuration)."""
+    """One ``kernel<<<grid, block_dim, shmem, stream>>>(params...)`` call (Sec. 2, kernel
+    configuration).  Launches of one stream run in order; launches of different streams may
+    run in parallel; ``wait`` >= 0 makes the launch also wait for an event recorded right after
+    launch ``wait`` of the same program (an earlier one), as ``cudaStreamWaitEvent`` would
+    (Sec. 3, streams and events).  The defaults put every launch in one stream."""
 
     kernel: int
     grid: int
     block_dim: int
     shmem_words: int
     params: Tuple[int, ...] = ()
+    stream: int = 0
+    wait: int = -1
 
 
 @dataclass
 class Program:
     """A simulated CUDA program: code, kernels, launch list and initial global arena.
 
-    Launches run in order over the one global arena, with the implicit grid-wide
-    synchronisation between kernel calls (Sec. 2).
+    Launches run in stream order over the one global arena, with the implicit grid-wide
+    synchronisation between kernel calls of a stream (Sec. 2).
     """
 
     code: np.ndarray

@@ -35,7 +35,12 @@ MUTANTS = {
     "floor_division": (
         "return va / vb;                          /* C99: truncation toward zero */",
         "return (va % vb && ((va < 0) != (vb < 0))) ? va / vb - 1 : va / vb;"),
-    "no_abort_after_deadlock": ("if (st & (ORC_ST_DEADLOCK | ORC_ST_STEP_LIMIT)) break;", ""),
+    "no_abort_after_deadlock": ("if (st & (ORC_ST_DEADLOCK | ORC_ST_STEP_LIMIT)) dead[l] = 1;", ""),
+    "event_wait_ignored": ("dep_wait[l] = P->launches[l].wait ? (int32_t)P->launches[l].wait - 1 : -1;",
+                           "dep_wait[l] = -1;"),
+    "streams_ignored": ("if (P->launches[m].stream == P->launches[l].stream) { dep_prev[l] = (int32_t)m; break; }",
+                        "{ dep_prev[l] = (int32_t)m; break; }"),
+    "skip_not_propagated": ("dead[l] = 1;                                            /* skipped */", ""),
     "divergence_unchecked": ("if (pmin != pmax)        /* all threads wait", "if (0)        /* all threads wait"),
     "logical_right_shift": ("return va < 0 ? ~((~va) >> s) : (va >> s);", "return as_i32((uint32_t)va >> s);"),
     "pc_range_not_recorded": ("if (p->pc < pclo) pclo = p->pc;\n        if (p->pc > pchi) pchi = p->pc;", ""),

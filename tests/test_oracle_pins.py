@@ -636,3 +636,36 @@ def test_opcode_numbers_agree_with_ir_module():
     names = ["MOV"] + [n.strip()[4:] for n in body.replace("\n", " ").split(",") if n.strip()]
     for i, nm in enumerate(names, start=1):
         assert getattr(ir, nm) == i, nm
+
+
+# ---------------------------------------------------------------- streams and events
+def test_streams_fork_join_hand_values():
+    """Sec. 3, streams and events: a deadlock stops its own stream and what waits on it, not
+    the other streams.  Expected arenas are derived by hand in tests/stream_programs.py."""
+    import stream_programs as sp
+    for streams in (True, False):
+        res = oracle.run([sp.fork_join(streams)], check_streams=True)
+        assert np.array_equal(res.arenas[0], sp.fork_join_expected(streams)), res.arenas[0]
+        assert list(res.status) == [oracle.ST_DEADLOCK]
+        # the one report: launch 0's block 0 deadlocks (thread 0 exited, three wait at pc 3)
+        assert [(r[0], r[2], r[3]) for r in res.report_tuples()] == [(oracle.DEADLOCK, 0, 0)]
+        assert res.stream_conflicts == 0
+
+
+def test_stream_conflict_diagnostic():
+    """Launches no stream order or event wait orders must not share a written global word
+    (the result would depend on timing); the diagnostic counts such words."""
+    import stream_programs as sp
+    assert oracle.run([sp.conflicting("ww")], check_streams=True).stream_conflicts == 4
+    assert oracle.run([sp.conflicting("rw")], check_streams=True).stream_conflicts == 4
+    assert oracle.run([sp.conflicting("ordered")], check_streams=True).stream_conflicts == 0
+    # every generated workload is one stream, hence conflict-free by construction
+    assert oracle.run(families.batch(n_programs=12, seed=3, max_grid=4), check_streams=True).stream_conflicts == 0
+
+
+def test_stream_waits_must_name_an_earlier_launch():
+    import stream_programs as sp
+    p = sp.fork_join(True)
+    p.launches[2] = ir.Launch(0, 1, 4, 0, (4, 20), stream=0, wait=5)
+    with pytest.raises(ValueError):
+        oracle.run([p])
