@@ -122,12 +122,21 @@ typedef struct {
   uint32_t shmem_words;      /* dynamic shared words per block, 0..SR_MAX_SHMEM_WORDS */
   uint32_t nparams;          /* 0..4, loaded into r0.. */
   int32_t params[4];
+  /* Sec. 2 and Sec. 3 "Streams and events": launches of one stream run in order, launches of
+   * different streams may run at the same time.  `wait` = 1 + the index of an earlier launch
+   * of the program that this one also waits for (an event recorded after that launch and
+   * waited for by this launch's stream); 0 = none.  All zero: one in-order stream.  A launch
+   * is skipped when the previous launch of its stream, or the one it waits for, stopped
+   * (deadlock, step limit) or was skipped.  Launches that nothing orders must not share a
+   * global word that one of them writes (the result would depend on timing; not checked). */
+  uint32_t stream;
+  uint32_t wait;             /* 0..index of this launch; SR_E_INVAL otherwise */
 } sr_launch;
 
 typedef struct {
   const sr_instr* code; uint32_t ncode;           /* 1..SR_MAX_CODE instructions */
   const uint32_t* kernel_entry; uint32_t nkernels;
-  const sr_launch* launches; uint32_t nlaunches;  /* run in order */
+  const sr_launch* launches; uint32_t nlaunches;  /* run in stream order (sr_launch) */
   const int32_t* global_init; uint64_t global_words;  /* initial global arena (< 2^31 words) */
 } sr_program;
 

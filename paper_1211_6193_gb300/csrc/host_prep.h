@@ -138,6 +138,7 @@ inline int validate(const sr_program* p, char* msg, size_t len) {
     if (L.block_dim == 0 || L.block_dim > SR_MAX_BLOCK_DIM) return bad("launch %u: block_dim %u", l, L.block_dim);
     if (L.shmem_words > SR_MAX_SHMEM_WORDS) return bad("launch %u: shmem_words %u", l, L.shmem_words);
     if (L.nparams > 4) return bad("launch %u: nparams %u", l, L.nparams);
+    if (L.wait > l) return bad("launch %u: waits for launch %u, which is not an earlier one", l, L.wait - 1);
   }
   if (p->global_words >= (1ull << 31)) return bad("global arena too large (%u)", (uint32_t)(p->global_words >> 20), 0);
   if (p->global_words && !p->global_init) return bad("global_init missing (%u words)", (uint32_t)p->global_words, 0);

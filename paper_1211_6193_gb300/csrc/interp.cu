@@ -774,12 +774,20 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     const uint32_t bits = bv->status | ((bv->flags & BF_OVERFLOW) ? (uint32_t)SR_ST_LOG_OVERFLOW : 0u) |
                           ((bv->flags & BF_INTERNAL) ? (uint32_t)SR_ST_INTERNAL : 0u);
     if (bits) atomicOr(&A.prog_status[Ls->prog], bits);
-    if (bits & (SR_ST_DEADLOCK | SR_ST_STEP_LIMIT | SR_ST_INTERNAL)) atomicMin(&A.prog_abort[Ls->prog], Ls->launch);
+    if (bits & (SR_ST_DEADLOCK | SR_ST_STEP_LIMIT | SR_ST_INTERNAL)) atomicOr(&A.launch_dead[Ls->index], 1u);
   }
 }
 
-// One CTA per simulated block; one kernel launch per (program, launch).  MINB = 2 caps
-// registers so that two 1024-thread CTAs fit an SM.
+// A launch is skipped when the launch before it in its stream, or the one it waits for,
+// stopped or was skipped (Sec. 3, streams and events; Sec. 3.1, the interpreter halts).
+__device__ __forceinline__ bool deps_dead(const RunArgs& A, const LaunchDev& L) {
+  const volatile uint32_t* dead = A.launch_dead;
+  return (L.dep_prev != kNoDep && dead[L.dep_prev]) || (L.dep_wait != kNoDep && dead[L.dep_wait]);
+}
+
+// One CTA per simulated block; one kernel launch per (program, launch), in an order that
+// respects every stream and wait.  MINB = 2 caps registers so that two 1024-thread CTAs fit
+// an SM.
 template <int MINB, bool Fused>
 __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t li) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -788,8 +796,9 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
   __shared__ uint32_t s_skip;
   if (threadIdx.x == 0) {
     Ls = A.launches[li];
-    // launches after a deadlock / step limit of the same program are skipped
-    s_skip = *reinterpret_cast<volatile uint32_t*>(&A.prog_abort[Ls.prog]) < Ls.launch;
+    // (the launches before this one have completed: they ran earlier on this CUDA stream)
+    s_skip = deps_dead(A, Ls);
+    if (s_skip) atomicOr(&A.launch_dead[Ls.index], 1u);
     if (!s_skip) {
       mbar_init(&mbar);
       bulk_load(smem, A.code + Ls.code_off, Ls.ir_bytes, &mbar);
@@ -808,8 +817,9 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
 
 // Persistent: CTAs pop (launch, first block) items from a device queue; an item runs
 // `groups` simulated blocks side by side, each on its own warps and named barrier.
-// Items are ordered launch-wave by launch-wave, and an item of launch l waits (bounded)
-// until every block of launch l-1 of the same program has completed.
+// Items are ordered launch-wave by launch-wave, and an item waits (bounded) until every
+// block of the launches it follows (the previous launch of its stream, the one it waits
+// for) has completed; launches of other streams run meanwhile.
 template <bool Fused>
 __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -828,11 +838,15 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
     if (threadIdx.x == 0) {
       Ls = A.launches[it.x];
       uint32_t skip = 0;
-      if (Ls.launch > 0) {
-        const uint32_t need = A.launches[it.x - 1].grid;
+      // wait (bounded) until every block of the launches this one follows has completed;
+      // they are earlier in the queue, so CTAs that never wait on this item hold them
+      const uint32_t deps[2] = {Ls.dep_prev, Ls.dep_wait};
+      for (uint32_t j = 0; j < 2 && !skip; ++j) {
+        if (deps[j] == kNoDep) continue;
+        const uint32_t need = A.launches[deps[j]].grid;
         bool ok = false;
         for (uint32_t s = 0; s < A.spin_limit; ++s) {
-          if (ld_acquire_gpu(&A.launch_done[it.x - 1]) >= need) { ok = true; break; }
+          if (ld_acquire_gpu(&A.launch_done[deps[j]]) >= need) { ok = true; break; }
           __nanosleep(128);
         }
         if (!ok) {
@@ -840,7 +854,8 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
           atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
         }
       }
-      if (!skip && *reinterpret_cast<volatile uint32_t*>(&A.prog_abort[Ls.prog]) < Ls.launch) skip = 1;
+      if (!skip && deps_dead(A, Ls)) skip = 1;
+      if (skip) atomicOr(&A.launch_dead[Ls.index], 1u);
       if (!skip) bulk_load(smem, A.code + Ls.code_off, Ls.ir_bytes, &mbar);
       s_skip = skip;
     }

@@ -89,6 +89,14 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     sr::LaunchDev d{};
     d.prog = 0;
     d.launch = l;
+    d.index = l;
+    d.dep_prev = d.dep_wait = sr::kNoDep;
+    for (uint32_t m = l; m-- > 0;)
+      if (prog->launches[m].stream == pl.stream) {
+        d.dep_prev = m;
+        break;
+      }
+    if (pl.wait) d.dep_wait = pl.wait - 1;
     d.entry = prog->kernel_entry[pl.kernel];
     d.ncode = ncode;
     d.code_off = 0;
@@ -128,7 +136,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   const size_t o_code = take((size_t)npacked * 8);
   const size_t o_launch = take((size_t)std::max(1u, nl) * sizeof(sr::LaunchDev));
   const size_t o_blocks = take((size_t)nblocks * sizeof(sr::BlockRes));
-  const size_t o_status = take(8);                     // status, abort mark
+  const size_t o_status = take(4 + 4 * (size_t)std::max(1u, nl));   // status, per-launch stop marks
   const size_t o_counters = take(sizeof(sr::Counters));
   const size_t o_total = take(8);
   const size_t o_heads = take(kMaxWaves * 4 + 4);      // checker work heads + error flag
@@ -170,7 +178,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   if (nl) NA_TRY(cudaMemcpyAsync(base + o_launch, L, (size_t)nl * sizeof(sr::LaunchDev), cudaMemcpyHostToDevice, s));
   NA_TRY(cudaMemsetAsync(base + o_blocks, 0, (size_t)nblocks * sizeof(sr::BlockRes), s));
   NA_TRY(cudaMemsetAsync(base + o_status, 0, 4, s));
-  NA_TRY(cudaMemsetAsync(base + o_status + 4, 0xFF, 4, s));
+  NA_TRY(cudaMemsetAsync(base + o_status + 4, 0, 4 * (size_t)std::max(1u, nl), s));
   NA_TRY(cudaMemsetAsync(base + o_counters, 0, sizeof(sr::Counters), s));
   NA_TRY(cudaMemsetAsync(base + o_total, 0, 8, s));
   NA_TRY(cudaMemsetAsync(base + o_heads, 0, kMaxWaves * 4 + 4, s));
@@ -186,7 +194,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   ra.log = reinterpret_cast<unsigned long long*>(base + o_log);
   ra.blocks = reinterpret_cast<sr::BlockRes*>(base + o_blocks);
   ra.prog_status = reinterpret_cast<uint32_t*>(base + o_status);
-  ra.prog_abort = reinterpret_cast<uint32_t*>(base + o_status + 4);
+  ra.launch_dead = reinterpret_cast<uint32_t*>(base + o_status + 4);
   ra.counters = reinterpret_cast<sr::Counters*>(base + o_counters);
   uint32_t* heads = reinterpret_cast<uint32_t*>(base + o_heads);
   for (uint32_t wi = 0; wi < nwaves; ++wi) {

@@ -61,7 +61,7 @@ struct sr_batch {
   uint32_t max_key_bits = 1;
   uint32_t batched_smem = 0;
   uint64_t total_code = 0, total_arena = 0, log_records = 0;
-  DevBuf code, launches_d, arena_init, arena_work, log, blocks, prog_status, prog_abort, counters, items_d,
+  DevBuf code, launches_d, arena_init, arena_work, log, blocks, prog_status, launch_dead, counters, items_d,
       queue_head, launch_done, scratch, work_head, err_flag, offsets, partials, out, total, item_launch_d;
   uint64_t out_cap = 0;
   cudaStream_t stream = nullptr;
@@ -125,7 +125,7 @@ int alloc_buf(sr_ctx* c, DevBuf& b, size_t bytes, cudaStream_t s, const char* wh
 
 void free_batch_buffers(sr_ctx* c, sr_batch* b, cudaStream_t s) {
   DevBuf* all[] = {&b->code, &b->launches_d, &b->arena_init, &b->arena_work, &b->log, &b->blocks,
-                   &b->prog_status, &b->prog_abort, &b->counters, &b->items_d, &b->queue_head,
+                   &b->prog_status, &b->launch_dead, &b->counters, &b->items_d, &b->queue_head,
                    &b->launch_done, &b->scratch, &b->work_head, &b->err_flag, &b->offsets, &b->partials,
                    &b->out, &b->total, &b->item_launch_d};
   for (DevBuf* d : all) dev_free(c, *d, s);
@@ -171,7 +171,7 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
   CUDA_TRY(c, cudaMemcpyAsync(b->arena_work.p, b->arena_init.p, b->total_arena * 4, cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(c, cudaMemsetAsync(b->blocks.p, 0, (size_t)b->nblocks * sizeof(sr::BlockRes), s));
   CUDA_TRY(c, cudaMemsetAsync(b->prog_status.p, 0, (size_t)b->nprogs * 4, s));
-  CUDA_TRY(c, cudaMemsetAsync(b->prog_abort.p, 0xFF, (size_t)b->nprogs * 4, s));
+  CUDA_TRY(c, cudaMemsetAsync(b->launch_dead.p, 0, std::max<size_t>(1, b->launches.size()) * 4, s));
   CUDA_TRY(c, cudaMemsetAsync(b->counters.p, 0, sizeof(sr::Counters), s));
   CUDA_TRY(c, cudaMemsetAsync(b->launch_done.p, 0, b->launches.size() * 4, s));
   CUDA_TRY(c, cudaMemsetAsync(b->total.p, 0, 8, s));
@@ -189,7 +189,7 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
   ra.log = (unsigned long long*)b->log.p;
   ra.blocks = (sr::BlockRes*)b->blocks.p;
   ra.prog_status = (uint32_t*)b->prog_status.p;
-  ra.prog_abort = (uint32_t*)b->prog_abort.p;
+  ra.launch_dead = (uint32_t*)b->launch_dead.p;
   ra.counters = (sr::Counters*)b->counters.p;
   ra.items = (const uint2*)b->items_d.p;
   ra.launch_done = (uint32_t*)b->launch_done.p;
@@ -353,11 +353,20 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       const BoundScratch ws{colour.data(), acc.data(), bar.data(), spc.data(), snx.data()};
       for (uint32_t k = 0; k < P.nkernels; ++k) kb[k] = bound_kernel(P.code, P.ncode, P.kernel_entry[k], ws);
     }
+    const uint32_t first_launch = (uint32_t)b->launches.size();   // the program's launches are contiguous
     for (uint32_t l = 0; l < P.nlaunches; ++l) {
       const sr_launch& L = P.launches[l];
       LaunchDev d{};
       d.prog = i;
       d.launch = l;
+      d.index = first_launch + l;
+      d.dep_prev = d.dep_wait = sr::kNoDep;
+      for (uint32_t m = l; m-- > 0;)
+        if (P.launches[m].stream == L.stream) {
+          d.dep_prev = first_launch + m;
+          break;
+        }
+      if (L.wait) d.dep_wait = first_launch + L.wait - 1;
       d.entry = P.kernel_entry[L.kernel];
       d.ncode = P.ncode;
       d.code_off = code_off[i];
@@ -478,7 +487,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       {&b->log, b->log_records * 8, "access log"},
       {&b->blocks, (size_t)b->nblocks * sizeof(sr::BlockRes), "block results"},
       {&b->prog_status, (size_t)n * 4, "status"},
-      {&b->prog_abort, (size_t)n * 4, "abort marks"},
+      {&b->launch_dead, std::max<size_t>(1, b->launches.size()) * 4, "launch stop marks"},
       {&b->counters, sizeof(sr::Counters), "counters"},
       {&b->items_d, std::max<size_t>(1, b->items.size()) * 8, "work items"},
       {&b->queue_head, (size_t)nwaves * 4, "queue heads"},

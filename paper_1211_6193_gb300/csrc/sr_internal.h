@@ -48,7 +48,11 @@ struct LaunchDev {
   uint32_t check_group, check_item;      // race check: blocks per work item, index of the first item
   uint32_t uninit;                       // 1 = report shared loads of words no thread wrote
   uint32_t fused;                        // 1 = race summaries kept by the interpreter (no log)
+  // the launches (batch indices) this one follows: the previous launch of its stream and the
+  // one it waits for (kNoDep: none), and its own batch index
+  uint32_t dep_prev, dep_wait, index;
 };
+constexpr uint32_t kNoDep = 0xFFFFFFFFu;
 
 // Per simulated block, written by the interpreter (n_log, n_misc, flags) and the checker (n_race).
 struct BlockRes { uint32_t n_log, n_race, n_misc, flags; };
@@ -66,7 +70,7 @@ struct RunArgs {
   unsigned long long* log;      // access-log pool
   BlockRes* blocks;
   uint32_t* prog_status;        // SR_ST_* bits
-  uint32_t* prog_abort;         // lowest launch index that stopped the program (or ~0)
+  uint32_t* launch_dead;        // per launch: 1 = a block stopped it, or it was skipped
   Counters* counters;
   // batched mode
   const uint2* items;           // (launch index, first block)

@@ -2,6 +2,7 @@
 declared in include/*.h, and validates programs on the host."""
 import ctypes
 import os
+import subprocess
 import re
 
 import numpy as np
@@ -46,12 +47,23 @@ def test_binding_names_match_header():
     assert set(declared_functions()) <= set(binding.EXPORTS) | set()
 
 
-def test_struct_layouts_match_header():
-    # 8-byte instruction, 32-byte report, launch = 9 words
+def test_struct_layouts_match_header(tmp_path):
+    # 8-byte instruction, 32-byte report, launch = 11 words
     assert ctypes.sizeof(binding.sr_instr) == 8
-    assert ctypes.sizeof(binding.sr_launch) == 36
+    assert ctypes.sizeof(binding.sr_launch) == 44
     assert binding.REPORT_DTYPE.itemsize == 32
     assert ir.INSTR_DTYPE.itemsize == 8
+    # the C compiler's layout of the header's sr_launch equals the binding's
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "simtcheck.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(sr_launch), offsetof(sr_launch, params),'
+                   ' offsetof(sr_launch, stream), offsetof(sr_launch, wait)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(binding.sr_launch), binding.sr_launch.params.offset, binding.sr_launch.stream.offset,
+            binding.sr_launch.wait.offset]
+    assert got == want
 
 
 def test_opcode_numbers_match_header():

@@ -321,6 +321,25 @@ def test_fused_race_check_matches_the_log_path_on_a_larger_batch(B):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_streams_and_event_waits(B, mode):
+    """Sec. 3, streams and events: launches of several streams with event waits (batched
+    mode runs launches of different streams at the same time); a deadlock skips its own
+    stream and what waits on it, and nothing else."""
+    from stream_programs import all_programs, fork_join_expected
+    got, _ = assert_parity(B, all_programs(), mode)
+    assert np.array_equal(got.arenas[0], fork_join_expected(True))
+    assert np.array_equal(got.arenas[1], fork_join_expected(False))
+
+
+def test_stream_wait_on_a_later_launch_is_rejected(B):
+    import stream_programs as sp
+    p = sp.fork_join(True)
+    p.launches[2] = ir.Launch(0, 1, 4, 0, (4, 20), stream=0, wait=5)
+    with pytest.raises(B.SimtCheckError):
+        B.check([p])
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_reducing_barriers(B, mode):
     """__syncthreads_and/_or/_count: predicates over full and partial warps, reducing and
     plain barriers meeting, a deadlock at a reducing barrier, reducing barriers in a loop."""

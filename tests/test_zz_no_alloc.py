@@ -28,10 +28,11 @@ def env():
 
 
 def _programs():
+    from stream_programs import all_programs
     return [fig1.program(), fig1.program(race=True), fig1.program(deadlock=True),
             families.reduction_plain(n_blocks=64),
             stencil2d.program(log2w=7, steps=3, buggy_launch=1)] + \
-        families.batch(n_programs=6, seed=17, max_grid=8, bug_rate=0.7)
+        families.batch(n_programs=6, seed=17, max_grid=8, bug_rate=0.7) + all_programs()
 
 
 def _noalloc(env, prog, cap):
