@@ -82,3 +82,43 @@ def all_programs():
     wide.append(ir.Launch(COPY, 1, 4, 0, (8, 200), stream=9, wait=2))       # joins stream 0
     prog_wide = ir.Program(code, entries, wide, np.zeros(208, np.int32), name="wide_streams")
     return [fork_join(True), fork_join(False), prog_wide]
+
+
+def _ancestors(launches, l):
+    """Launches ordered before launch l: its stream predecessors and waits, transitively."""
+    seen, todo = set(), [l]
+    while todo:
+        m = todo.pop()
+        prev = next((k for k in range(m - 1, -1, -1) if launches[k].stream == launches[m].stream), None)
+        for d in (prev, launches[m].wait if launches[m].wait >= 0 else None):
+            if d is not None and d not in seen:
+                seen.add(d)
+                todo.append(d)
+    return seen
+
+
+def random_programs(seed, count):
+    """Seeded programs of 1-4 streams, 1-12 launches, random event waits and a few deadlocking
+    launches.  Launch l writes only words [4l, 4l + 4) and copies only from a launch ordered
+    before it, so no two unordered launches share a written word (well-formed by construction)."""
+    rng = np.random.default_rng(seed)
+    code, entries = _code()
+    out = []
+    for p in range(count):
+        nstreams, nl = int(rng.integers(1, 5)), int(rng.integers(1, 13))
+        launches = []
+        for l in range(nl):
+            stream = int(rng.integers(0, nstreams))
+            wait = int(rng.integers(0, l)) if l and rng.random() < 0.3 else -1
+            launches.append(ir.Launch(WRITE, 1, 4, 0, (4 * l, 0), stream=stream, wait=wait))
+            anc = sorted(_ancestors(launches, l))
+            r = rng.random()
+            if r < 0.1:
+                kind, params = STALL, ()
+            elif anc and r < 0.6:
+                kind, params = COPY, (4 * int(rng.choice(anc)), 4 * l)
+            else:
+                kind, params = WRITE, (4 * l, int(rng.integers(0, 1000)))
+            launches[l] = ir.Launch(kind, 1, 4, 0, params, stream=stream, wait=wait)
+        out.append(ir.Program(code, entries, launches, np.full(4 * nl, -1, np.int32), name=f"streams_{seed}_{p}"))
+    return out

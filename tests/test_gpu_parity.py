@@ -331,6 +331,13 @@ def test_streams_and_event_waits(B, mode):
     assert np.array_equal(got.arenas[1], fork_join_expected(False))
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_streams_on_random_dependency_graphs(B, mode):
+    """Seeded programs of 1-4 streams with random event waits and deadlocking launches."""
+    from stream_programs import random_programs
+    assert_parity(B, random_programs(11, 40), mode)
+
+
 def test_stream_wait_on_a_later_launch_is_rejected(B):
     import stream_programs as sp
     p = sp.fork_join(True)

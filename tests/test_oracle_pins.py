@@ -669,3 +669,36 @@ def test_stream_waits_must_name_an_earlier_launch():
     p.launches[2] = ir.Launch(0, 1, 4, 0, (4, 20), stream=0, wait=5)
     with pytest.raises(ValueError):
         oracle.run([p])
+
+
+def _stream_model(p):
+    """The three kernels of tests/stream_programs.py executed directly: launches in index
+    order; a launch whose stream predecessor or awaited launch stopped or was skipped is
+    skipped; STALL stops its launch (deadlock)."""
+    import stream_programs as sp
+    arena, dead, status = p.global_init.astype(np.int64).copy(), set(), 0
+    for l, L in enumerate(p.launches):
+        prev = next((k for k in range(l - 1, -1, -1) if p.launches[k].stream == L.stream), None)
+        if (prev is not None and prev in dead) or (L.wait >= 0 and L.wait in dead):
+            dead.add(l)
+            continue
+        if L.kernel == sp.STALL:
+            dead.add(l)
+            status = oracle.ST_DEADLOCK
+        elif L.kernel == sp.WRITE:
+            arena[L.params[0]:L.params[0] + 4] = L.params[1] + np.arange(4)
+        else:
+            arena[L.params[1]:L.params[1] + 4] = arena[L.params[0]:L.params[0] + 4] + 1
+    return arena.astype(np.int32), status
+
+
+def test_streams_on_random_dependency_graphs_match_a_direct_model():
+    import stream_programs as sp
+    progs = sp.random_programs(7, 60)
+    res = oracle.run(progs, check_streams=True, check_interblock=True)
+    assert res.stream_conflicts == 0 and res.interblock_conflicts == 0
+    for i, p in enumerate(progs):
+        want, st = _stream_model(p)
+        assert np.array_equal(res.arenas[i], want), p.name
+        assert int(res.status[i]) == st, p.name
+    assert 10 < sum(int(s) for s in res.status) < 50        # both outcomes well represented
