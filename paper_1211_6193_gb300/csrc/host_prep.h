@@ -189,6 +189,18 @@ inline uint32_t key_bits_for(uint32_t shw) {
 }
 
 
+// The launches (indices within the program, or `none`) that launch l follows: the previous
+// launch of its stream and the launch it waits for (Sec. 3, streams and events).
+inline void launch_deps(const sr_launch* launches, uint32_t l, uint32_t none, uint32_t& prev, uint32_t& wait) {
+  prev = none;
+  for (uint32_t m = l; m-- > 0;)
+    if (launches[m].stream == launches[l].stream) {
+      prev = m;
+      break;
+    }
+  wait = launches[l].wait ? launches[l].wait - 1 : none;
+}
+
 // Access-log region (records per block, even) of one launch: the static bound of its
 // kernel, or `loop_records` for kernels with loops, plus room for barrier/error records.
 inline uint64_t launch_log_cap(const KernelBound& k, uint32_t block_dim, uint32_t check_races, uint32_t loop_records) {

@@ -90,13 +90,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     d.prog = 0;
     d.launch = l;
     d.index = l;
-    d.dep_prev = d.dep_wait = sr::kNoDep;
-    for (uint32_t m = l; m-- > 0;)
-      if (prog->launches[m].stream == pl.stream) {
-        d.dep_prev = m;
-        break;
-      }
-    if (pl.wait) d.dep_wait = pl.wait - 1;
+    launch_deps(prog->launches, l, sr::kNoDep, d.dep_prev, d.dep_wait);
     d.entry = prog->kernel_entry[pl.kernel];
     d.ncode = ncode;
     d.code_off = 0;

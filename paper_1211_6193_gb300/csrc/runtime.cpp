@@ -360,13 +360,9 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       d.prog = i;
       d.launch = l;
       d.index = first_launch + l;
-      d.dep_prev = d.dep_wait = sr::kNoDep;
-      for (uint32_t m = l; m-- > 0;)
-        if (P.launches[m].stream == L.stream) {
-          d.dep_prev = first_launch + m;
-          break;
-        }
-      if (L.wait) d.dep_wait = first_launch + L.wait - 1;
+      launch_deps(P.launches, l, sr::kNoDep, d.dep_prev, d.dep_wait);
+      if (d.dep_prev != sr::kNoDep) d.dep_prev += first_launch;
+      if (d.dep_wait != sr::kNoDep) d.dep_wait += first_launch;
       d.entry = P.kernel_entry[L.kernel];
       d.ncode = P.ncode;
       d.code_off = code_off[i];
