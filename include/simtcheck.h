@@ -203,22 +203,44 @@ int sr_validate_program(const sr_program* prog, char* msg, size_t msg_len);
 
 /* Validate, pack and upload n programs (code, launch tables, initial arenas) into
  * device-resident arenas; returns a batch handle.  The initial arenas stay resident so
- * that run_and_check can be repeated.  Enqueued on `stream`. */
+ * that run_and_check can be repeated.  Enqueued on `stream`.
+ * Paper: Sec. 2 (the host allocates device memory, copies the inputs and configures each
+ * kernel call <<<grid, block, shared bytes, stream>>>) and Fig. 1 lines 22-34 (the sum
+ * program's host side); here the host program is replaced by the sr_program descriptor.
+ *   progs   host array of n descriptors, read during the call only (copied to the device);
+ *   stream  cudaStream_t for the uploads (the call waits for them before returning);
+ *   out     receives the batch handle (NULL on failure).
+ * Errors: SR_E_INVAL (a program fails validation; nothing is enqueued), SR_E_NOMEM,
+ * SR_E_CUDA. */
 int load_programs(sr_ctx* ctx, const sr_program* progs, uint32_t n, void* stream, sr_batch** out);
 
 /* Reset every program's global arena to its initial image, run all launches of all
  * programs, check the access logs and barriers, and order the reports.  Asynchronous
- * on `stream`. */
+ * on `stream`.
+ * Paper: Sec. 3 "Threads and memory" (every thread of the grid runs the kernel; per-block
+ * shared memory) and "Barrier synchronization" (__syncthreads); Sec. 3.1 (race detection:
+ * two threads, one shared location, no barrier between, at least one write; the history
+ * is cleared at each barrier; deadlock detection at a barrier some thread never reaches).
+ * Errors: SR_E_INVAL (null handle), SR_E_CUDA (a launch failed).  Races, deadlocks and
+ * the other findings about the simulated program are reports, not errors. */
 int run_and_check(sr_ctx* ctx, sr_batch* batch, void* stream);
 
 /* Copy the sorted reports to dst (capacity cap records) and the total into *n_total.
- * dst == NULL only queries the size.  SR_E_RANGE if cap < total (dst untouched). */
+ * dst == NULL only queries the size.  SR_E_RANGE if cap < total (dst untouched).
+ * Paper: Sec. 3.2 (cudak prints its diagnostics - a possible race on shared memory and
+ * the source line, or a deadlock caused by a misplaced __syncthreads - beside the
+ * program's output); here each diagnostic is one sr_report record.
+ *   dst  host memory (pageable or page-locked) for cap records, owned by the caller.
+ * Synchronises with the batch's stream.  SR_E_TIMEOUT if a device-side wait of the race
+ * check gave up (the reports are then incomplete). */
 int fetch_reports(sr_ctx* ctx, sr_batch* batch, sr_report* dst, uint64_t cap, uint64_t* n_total);
 
 /* prog value of fetch_memory / sr_batch_status that addresses every program at once. */
 #define SR_ALL_PROGRAMS 0xFFFFFFFFu
 
-/* Copy program `prog`'s final global arena (n_words = its size) to dst.  With
+/* Paper: Sec. 3.2 (the program's own output, e.g. Fig. 1's OUTPUT 767, read back from
+ * device memory by the host program).
+ * Copy program `prog`'s final global arena (n_words = its size) to dst.  With
  * prog == SR_ALL_PROGRAMS every arena is copied in one copy, in program order, program k's
  * at word offset sum over i < k of round_up(global_words_i, 4) (each arena starts on a
  * 16-byte boundary; padding words are zero); n_words = that sum over all programs.  dst == NULL only queries the size;
@@ -239,9 +261,12 @@ const char* sr_last_error(sr_ctx* ctx);
 
 /* ---------------------------------------------------------------- no-allocation entry point
  * The paper has no counterpart to this call: it serves callers that cannot allocate
- * device memory - code that runs while a CUDA graph is being captured, frameworks that
- * own every byte of the GPU through their own allocator, or processes that forbid
- * cudaMalloc after start-up.  It runs the whole check of one program (the same kernels
+ * device memory - frameworks that own every byte of the GPU through their own allocator
+ * (a second allocator would fight theirs for memory), or processes that forbid cudaMalloc
+ * after start-up (allocation can synchronise the device and stall other work).  It is
+ * not for use while a CUDA graph is being captured: it copies from host stack memory and
+ * synchronises the stream, so on a capturing stream it returns SR_E_INVAL at once and
+ * leaves the capture untouched.  It runs the whole check of one program (the same kernels
  * as load_programs + run_and_check + fetch_reports, plain mode, default options) and
  * allocates nothing: every intermediate buffer lives in one file-scope __device__ array
  * of SR_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process
@@ -251,15 +276,20 @@ const char* sr_last_error(sr_ctx* ctx);
  *              arena out (updated in place);
  *   d_reports  device memory for report_cap records: the sorted reports (at most report_cap);
  *   n_reports  host: total number of reports;  status: host, SR_ST_* bits of the program.
- * Synchronous on `stream`.  Returns SR_E_RANGE when the program needs more scratch than
+ * Synchronous on `stream`.  The host side keeps its staging arrays in thread-local storage
+ * (about 150 KB per calling thread, allocated once by the C++ runtime, not per call).
+ * Returns SR_E_RANGE when the program needs more scratch than
  * the array holds (more than 256 launches, or logs that do not fit even one launch at a
  * time) or when report_cap < *n_reports (extra reports dropped), SR_E_INVAL for an
- * invalid program, SR_E_CUDA for a failed CUDA call.
+ * invalid program or a stream that is being captured, SR_E_CUDA for a failed CUDA call.
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress and sets the kernels' shared-memory attributes; make that first
- * call before any stream capture.  All calls share the one array and it keeps the last
- * call's contents: calls that overlap on the GPU (other streams, other host threads) race
- * and corrupt each other's results. */
+ * cudaGetSymbolAddress and sets the kernels' shared-memory attributes (once per device,
+ * also when several host threads make their first call at the same time).  All calls
+ * share the one array and it keeps the last call's contents: calls that overlap on the GPU
+ * (other streams, other host threads) race and corrupt each other's results.  The race
+ * check runs on min(SMs, 8) CTAs here (each holds 256 KB of the array as staging), fewer
+ * than the allocating path uses on a large GPU: results are the same, large programs are
+ * checked more slowly. */
 #define SR_NOALLOC_SCRATCH_BYTES (32u << 20)
 int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena, sr_report* d_reports, uint64_t report_cap,
                              uint64_t* n_reports, uint32_t* status, void* stream);

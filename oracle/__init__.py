@@ -26,6 +26,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 
 # report kinds / status bits (same numbers as simt_oracle.h)
 RACE, DIVERGENCE, DEADLOCK, STEP_LIMIT, ERR_OOB_SHARED, ERR_OOB_GLOBAL, ERR_DIV0, ERR_UNINIT_SHARED = range(1, 9)
+GLOBAL_RACE, GLOBAL_BLOCKS, GLOBAL_LAUNCHES = 9, 10, 11      # with check_global
 CLS_WW, CLS_WR, CLS_WA, CLS_AR = 1, 2, 4, 8
 ST_DEADLOCK, ST_STEP_LIMIT = 1, 2
 
@@ -52,7 +53,7 @@ class _Program(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("round_budget", C.c_uint32), ("check_races", C.c_uint32), ("schedule", C.c_uint32),
                 ("nthreads", C.c_uint32), ("check_interblock", C.c_uint32), ("max_blocks", C.c_uint32),
-                ("check_uninit", C.c_uint32), ("check_streams", C.c_uint32)]
+                ("check_uninit", C.c_uint32), ("check_streams", C.c_uint32), ("check_global", C.c_uint32)]
 
 
 class _Result(C.Structure):
@@ -99,7 +100,7 @@ class OracleResult:
     thread_instrs: int
     shared_accesses: int
     rounds: int
-    interblock_conflicts: int
+    interblock_conflicts: int    # check_interblock: global words two blocks of a launch touch, one writing
     stream_conflicts: int = 0    # check_streams: global words two unordered launches share, one writing
 
     def report_tuples(self):
@@ -108,7 +109,7 @@ class OracleResult:
 
 def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, schedule: str = "lockstep",
         nthreads: int = 1, check_interblock: bool = False, max_blocks: int = 0,
-        check_uninit: bool = False, check_streams: bool = False) -> OracleResult:
+        check_uninit: bool = False, check_streams: bool = False, check_global: bool = False) -> OracleResult:
     """Run ``programs`` (``workloads.ir.Program``) through the oracle."""
     lib = _load()
     keep = []
@@ -132,7 +133,7 @@ def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, sch
         progs[i].launches, progs[i].nlaunches = C.addressof(ls), len(p.launches)
         progs[i].arena, progs[i].arena_words = (arena.ctypes.data if arena.size else None), arena.size
     opts = _Opts(round_budget, int(check_races), {"lockstep": 0, "sequential": 1}[schedule], nthreads,
-                 int(check_interblock), max_blocks, int(check_uninit), int(check_streams))
+                 int(check_interblock), max_blocks, int(check_uninit), int(check_streams), int(check_global))
     res = _Result()
     rc = lib.orc_run(C.addressof(progs), len(programs), C.byref(opts), C.byref(res))
     if rc != 0:

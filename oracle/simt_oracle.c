@@ -10,7 +10,13 @@
  *   run_block        - one thread block: rounds, barrier resolution, step budget
  *   exec_one         - one instruction of one thread
  *   finish_epoch     - race check of the accesses since the last barrier (Sec. 3.1:
- *                      pairwise definition; the history is cleared at the barrier)
+ *                      pairwise definition; the history is cleared at the barrier), of
+ *                      shared words and, with check_global, of global words
+ *   block_races      - with check_global: pairs of blocks of one launch that touch a
+ *                      global word, one writing (no barrier orders blocks, Sec. 2)
+ *   launch_races     - with check_global: pairs of launches that no stream order or event
+ *                      wait orders and that touch a global word, one writing (Sec. 3,
+ *                      streams and events)
  *   resolve          - barrier check at the point where no thread can run
  *                      (Sec. 3 "Barrier synchronization"; Sec. 3.1 deadlock paragraph),
  *                      and the results of __syncthreads_and/_or/_count at a release
@@ -37,6 +43,8 @@ const char* orc_last_error(void) { return g_err; }
 typedef struct { orc_report* v; uint64_t n, cap; } rep_vec;
 typedef struct { uint32_t addr, tid, kind, pc; } access_t;
 typedef struct { access_t* v; uint64_t n, cap; } acc_vec;
+typedef struct { uint32_t addr, block, kind, pc; } gaccess_t;   /* a global access of a launch */
+typedef struct { gaccess_t* v; uint64_t n, cap; } gacc_vec;
 typedef struct { int32_t addr, val; } store_t;
 typedef struct { store_t* v; uint64_t n, cap; } st_vec;
 
@@ -50,6 +58,10 @@ static void rep_push(rep_vec* r, orc_report x) {
   r->v[r->n++] = x;
 }
 static void acc_push(acc_vec* r, access_t x) {
+  if (r->n == r->cap) { r->cap = r->cap ? 2 * r->cap : 256; r->v = xrealloc(r->v, r->cap * sizeof(*r->v)); }
+  r->v[r->n++] = x;
+}
+static void gacc_push(gacc_vec* r, gaccess_t x) {
   if (r->n == r->cap) { r->cap = r->cap ? 2 * r->cap : 256; r->v = xrealloc(r->v, r->cap * sizeof(*r->v)); }
   r->v[r->n++] = x;
 }
@@ -75,10 +87,14 @@ typedef struct {
   rep_vec* reps;
   uint64_t thread_instrs, shared_accesses, rounds;
   uint32_t status;               /* ORC_ST_* seen in this launch */
-  /* inter-block conflict bookkeeping (serial mode only) */
-  int32_t* writer; int32_t* reader; uint64_t conflicts;
+  /* check_interblock: per global word of the launch, the block that wrote it and the block
+     that read it (-1 none, -2 two or more distinct blocks); shared by the host threads of a
+     launch and updated with atomic compare-and-swap, so the result is order-independent */
+  int32_t* writer; int32_t* reader;
   /* check_streams: per global word of this launch, 1 = read, 2 = written (serial mode only) */
   uint8_t* acc;
+  /* check_global: the global accesses of this host thread's blocks of the launch */
+  gacc_vec* lacc;
 } launch_ctx;
 
 typedef struct {
@@ -93,7 +109,8 @@ typedef struct {
   uint8_t err_any;
   uint8_t* written;              /* shared words some thread of the block stored or added to */
   uint32_t* un_cnt; uint32_t* un_min;     /* loads of unwritten words, per pc, current epoch */
-  acc_vec acc;                   /* accesses of the current epoch */
+  acc_vec acc;                   /* shared accesses of the current epoch */
+  acc_vec gacc;                  /* global accesses of the current epoch (check_global) */
   st_vec sst, gst, ats;          /* deferred shared stores, global stores, atomics (round) */
   uint32_t epoch;
   int deferred;                  /* 1 = lockstep rounds, 0 = immediate (sequential) */
@@ -115,19 +132,23 @@ static void note_uninit(block_t* B, uint32_t pc, uint32_t t) {
   if (t < B->un_min[pc]) B->un_min[pc] = t;
   B->err_any = 1;
 }
-static void note_global(block_t* B, int32_t addr, int is_write) {
+/* one block's mark on a word: -1 (nobody) becomes the block; a second, different block
+   makes it -2 (two or more); compare-and-swap so that host threads may share the array */
+static void mark_block(int32_t* slot, int32_t me) {
+  int32_t cur = __atomic_load_n(slot, __ATOMIC_RELAXED);
+  for (;;) {
+    if (cur == me || cur == -2) return;
+    int32_t want = cur == -1 ? me : -2;
+    if (__atomic_compare_exchange_n(slot, &cur, want, 0, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) return;
+  }
+}
+static void note_global(block_t* B, int32_t addr, uint32_t t, uint32_t pc, int is_write) {
   launch_ctx* C = B->C;
   if (C->acc) C->acc[addr] |= is_write ? 2u : 1u;
-  if (!C->writer) return;
-  int32_t me = (int32_t)B->block;
-  if (is_write) {
-    if (C->writer[addr] != -1 && C->writer[addr] != me) C->conflicts++;
-    if (C->reader[addr] != -1 && C->reader[addr] != me) C->conflicts++;
-    C->writer[addr] = me;
-  } else {
-    if (C->writer[addr] != -1 && C->writer[addr] != me) C->conflicts++;
-    if (C->reader[addr] == -1) C->reader[addr] = me;
-    else if (C->reader[addr] != me) C->reader[addr] = -2;
+  if (C->writer) mark_block(is_write ? &C->writer[addr] : &C->reader[addr], (int32_t)B->block);
+  if (C->lacc) {
+    acc_push(&B->gacc, (access_t){(uint32_t)addr, t, is_write ? K_W : K_R, pc});
+    gacc_push(C->lacc, (gaccess_t){(uint32_t)addr, B->block, is_write ? K_W : K_R, pc});
   }
 }
 
@@ -232,14 +253,14 @@ static void exec_one(block_t* B, uint32_t t, uint32_t pc) {
     case ORC_LDG: {
       int32_t addr = add32(va, imm), v = 0;
       if (addr < 0 || (uint64_t)addr >= P->arena_words) note_err(B, pc, t);
-      else { v = P->arena[addr]; note_global(B, addr, 0); }
+      else { v = P->arena[addr]; note_global(B, addr, t, pc, 0); }
       reg_write(B, t, d, v);
       break;
     }
     case ORC_STG: {
       int32_t addr = add32(va, imm);
       if (addr < 0 || (uint64_t)addr >= P->arena_words) { note_err(B, pc, t); break; }
-      note_global(B, addr, 1);
+      note_global(B, addr, t, pc, 1);
       if (B->deferred) st_push(&B->gst, addr, vb); else P->arena[addr] = vb;
       break;
     }
@@ -295,42 +316,54 @@ static void emit(block_t* B, uint32_t kind, uint32_t a, uint32_t b, uint32_t c) 
   rep_push(B->C->reps, r);
 }
 
-/* race check of one barrier interval: the pairwise definition of Sec. 3.1, then
- * error records of the interval; the access history is then cleared */
+/* the conflict class of two accesses by different threads (Sec. 3.1: at least one writes;
+   reading: atomic adds commute with each other but not with reads or writes); 0 = none */
+static uint32_t conflict_class(uint32_t k1, uint32_t k2) {
+  if (k1 == K_W && k2 == K_W) return ORC_CLS_WW;
+  if ((k1 == K_W && k2 == K_R) || (k1 == K_R && k2 == K_W)) return ORC_CLS_WR;
+  if ((k1 == K_W && k2 == K_A) || (k1 == K_A && k2 == K_W)) return ORC_CLS_WA;
+  if ((k1 == K_A && k2 == K_R) || (k1 == K_R && k2 == K_A)) return ORC_CLS_AR;
+  return 0;                                     /* read-read, atomic-atomic */
+}
+
+/* race check of one interval's accesses to one memory: every pair of accesses to a word
+   by distinct threads, one writing (Sec. 3.1); one record of kind `kind` per racy word */
+static void interval_races(block_t* B, acc_vec* acc, uint32_t kind) {
+  qsort(acc->v, acc->n, sizeof(access_t), cmp_access);
+  uint64_t i = 0;
+  while (i < acc->n) {
+    uint64_t j = i;
+    while (j < acc->n && acc->v[j].addr == acc->v[i].addr) ++j;
+    uint32_t cls = 0, t1 = UINT32_MAX, t2 = UINT32_MAX, pclo = UINT32_MAX, pchi = 0;
+    for (uint64_t x = i; x < j; ++x) {
+      const access_t* p = &acc->v[x];
+      if (p->pc < pclo) pclo = p->pc;
+      if (p->pc > pchi) pchi = p->pc;
+      for (uint64_t y = x + 1; y < j; ++y) {
+        const access_t* q = &acc->v[y];
+        if (p->tid == q->tid) continue;
+        uint32_t bit = conflict_class(p->kind, q->kind);
+        if (!bit) continue;
+        cls |= bit;
+        uint32_t lo = p->tid < q->tid ? p->tid : q->tid, hi = p->tid ^ q->tid ^ lo;
+        if (lo < t1 || (lo == t1 && hi < t2)) { t1 = lo; t2 = hi; }
+      }
+    }
+    if (cls) emit(B, kind, acc->v[i].addr, (t1 << 16) | t2, (cls << 24) | (pclo << 12) | pchi);
+    i = j;
+  }
+}
+
+/* race check of one barrier interval: the pairwise definition of Sec. 3.1 on shared words
+ * (and, with check_global, on global words), then error records of the interval; the
+ * access history is then cleared */
 static void finish_epoch(block_t* B) {
   const orc_program* P = B->C->P;
   B->C->shared_accesses += B->acc.n;
-  if (B->C->O->check_races && B->acc.n) {
-    qsort(B->acc.v, B->acc.n, sizeof(access_t), cmp_access);
-    uint64_t i = 0;
-    while (i < B->acc.n) {
-      uint64_t j = i;
-      while (j < B->acc.n && B->acc.v[j].addr == B->acc.v[i].addr) ++j;
-      uint32_t cls = 0, t1 = UINT32_MAX, t2 = UINT32_MAX, pclo = UINT32_MAX, pchi = 0;
-      for (uint64_t x = i; x < j; ++x) {
-        const access_t* p = &B->acc.v[x];
-        if (p->pc < pclo) pclo = p->pc;
-        if (p->pc > pchi) pchi = p->pc;
-        for (uint64_t y = x + 1; y < j; ++y) {
-          const access_t* q = &B->acc.v[y];
-          if (p->tid == q->tid) continue;
-          uint32_t k1 = p->kind, k2 = q->kind, bit = 0;
-          if (k1 == K_W && k2 == K_W) bit = ORC_CLS_WW;
-          else if ((k1 == K_W && k2 == K_R) || (k1 == K_R && k2 == K_W)) bit = ORC_CLS_WR;
-          else if ((k1 == K_W && k2 == K_A) || (k1 == K_A && k2 == K_W)) bit = ORC_CLS_WA;
-          else if ((k1 == K_A && k2 == K_R) || (k1 == K_R && k2 == K_A)) bit = ORC_CLS_AR;
-          if (!bit) continue;                     /* read-read, atomic-atomic */
-          cls |= bit;
-          uint32_t lo = p->tid < q->tid ? p->tid : q->tid, hi = p->tid ^ q->tid ^ lo;
-          if (lo < t1 || (lo == t1 && hi < t2)) { t1 = lo; t2 = hi; }
-        }
-      }
-      if (cls) emit(B, ORC_REP_RACE, B->acc.v[i].addr, (t1 << 16) | t2,
-                    (cls << 24) | (pclo << 12) | pchi);
-      i = j;
-    }
-  }
+  if (B->C->O->check_races && B->acc.n) interval_races(B, &B->acc, ORC_REP_RACE);
   B->acc.n = 0;
+  if (B->gacc.n) interval_races(B, &B->gacc, ORC_REP_GLOBAL_RACE);
+  B->gacc.n = 0;
   if (B->err_any) {
     for (uint32_t pc = 0; pc < P->ncode; ++pc) {
       if (!B->err_cnt[pc]) continue;
@@ -434,7 +467,8 @@ static void run_block(launch_ctx* C, uint32_t block) {
   }
   C->rounds += rounds;
   free(B.pc); free(B.st); free(B.wpc); free(B.bk); free(B.bp); free(B.bd); free(B.regs); free(B.sh);
-  free(B.err_cnt); free(B.err_min); free(B.un_cnt); free(B.un_min); free(B.written); free(B.acc.v); free(B.sst.v); free(B.gst.v); free(B.ats.v);
+  free(B.err_cnt); free(B.err_min); free(B.un_cnt); free(B.un_min); free(B.written); free(B.acc.v); free(B.gacc.v);
+  free(B.sst.v); free(B.gst.v); free(B.ats.v);
 }
 
 /* ------------------------------------------------------------ validation */
@@ -474,6 +508,118 @@ static int validate(const orc_program* P, uint32_t idx) {
   return 0;
 }
 
+/* ------------------------------------------------------------ global-memory races */
+static int cmp_gaccess(const void* x, const void* y) {
+  const gaccess_t* p = x; const gaccess_t* q = y;
+  if (p->addr != q->addr) return p->addr < q->addr ? -1 : 1;
+  if (p->block != q->block) return p->block < q->block ? -1 : 1;
+  if (p->kind != q->kind) return p->kind < q->kind ? -1 : 1;
+  if (p->pc != q->pc) return p->pc < q->pc ? -1 : 1;
+  return 0;
+}
+
+/* Races between the blocks of one launch on global words: blocks of a grid run with no
+ * synchronisation point between them (Sec. 2: only the end of the kernel call orders them),
+ * so two accesses to a word by different blocks, one writing, race whatever the barrier
+ * intervals.  Per word: the classes over all such pairs, the smallest pair of blocks, and
+ * the pc range of every access of the launch to the word.  The accesses are sorted by
+ * (word, block, kind, pc); repeated (block, kind) entries of a word add nothing to the pairs
+ * and are compared once. */
+static void block_races(gacc_vec* a, uint32_t prog, uint32_t launch, rep_vec* out) {
+  qsort(a->v, a->n, sizeof(gaccess_t), cmp_gaccess);
+  gacc_vec u = {0};                             /* the word's distinct (block, kind) entries */
+  uint64_t i = 0;
+  while (i < a->n) {
+    uint64_t j = i;
+    uint32_t pclo = UINT32_MAX, pchi = 0;
+    u.n = 0;
+    while (j < a->n && a->v[j].addr == a->v[i].addr) {
+      const gaccess_t* x = &a->v[j];
+      if (x->pc < pclo) pclo = x->pc;
+      if (x->pc > pchi) pchi = x->pc;
+      if (u.n == 0 || u.v[u.n - 1].block != x->block || u.v[u.n - 1].kind != x->kind) gacc_push(&u, *x);
+      ++j;
+    }
+    uint32_t cls = 0, b1 = UINT32_MAX, b2 = UINT32_MAX;
+    for (uint64_t x = 0; x < u.n; ++x)
+      for (uint64_t y = x + 1; y < u.n; ++y) {
+        const gaccess_t* p = &u.v[x]; const gaccess_t* q = &u.v[y];
+        if (p->block == q->block) continue;
+        uint32_t bit = conflict_class(p->kind, q->kind);
+        if (!bit) continue;
+        cls |= bit;
+        uint32_t lo = p->block < q->block ? p->block : q->block, hi = p->block ^ q->block ^ lo;
+        if (lo < b1 || (lo == b1 && hi < b2)) { b1 = lo; b2 = hi; }
+      }
+    if (cls) {
+      orc_report r = {ORC_REP_GLOBAL_BLOCKS, prog, launch, b1, 0, a->v[i].addr, b2, (cls << 24) | (pclo << 12) | pchi};
+      rep_push(out, r);
+    }
+    i = j;
+  }
+  free(u.v);
+}
+
+typedef struct { uint32_t addr, launch, kind; } laccess_t;   /* a launch touched a word */
+typedef struct { laccess_t* v; uint64_t n, cap; } lacc_vec;
+static void lacc_push(lacc_vec* r, laccess_t x) {
+  if (r->n == r->cap) { r->cap = r->cap ? 2 * r->cap : 256; r->v = xrealloc(r->v, r->cap * sizeof(*r->v)); }
+  r->v[r->n++] = x;
+}
+static int cmp_laccess(const void* x, const void* y) {
+  const laccess_t* p = x; const laccess_t* q = y;
+  if (p->addr != q->addr) return p->addr < q->addr ? -1 : 1;
+  if (p->launch != q->launch) return p->launch < q->launch ? -1 : 1;
+  if (p->kind != q->kind) return p->kind < q->kind ? -1 : 1;
+  return 0;
+}
+
+/* before[l * nl + m] = 1 when launch m precedes launch l through a chain of stream order
+ * (the previous launch of a stream) and event waits (Sec. 3, streams and events) */
+static uint8_t* order_matrix(const int32_t* dep_prev, const int32_t* dep_wait, uint32_t nl) {
+  uint8_t* before = calloc((size_t)(nl ? nl : 1) * (nl ? nl : 1), 1);
+  for (uint32_t l = 0; l < nl; ++l) {
+    int32_t d[2] = {dep_prev[l], dep_wait[l]};
+    for (int k = 0; k < 2; ++k) {
+      if (d[k] < 0) continue;
+      before[(size_t)l * nl + (uint32_t)d[k]] = 1;
+      for (uint32_t m = 0; m < nl; ++m)
+        if (before[(size_t)(uint32_t)d[k] * nl + m]) before[(size_t)l * nl + m] = 1;
+    }
+  }
+  return before;
+}
+
+/* Races between launches of one program on global words: two launches that nothing orders
+ * may run at the same time (Sec. 3, streams and events), so a word both touch, one writing,
+ * races.  Per word: the classes over all such pairs and the smallest pair (l1 < l2). */
+static void launch_races(lacc_vec* a, uint32_t prog, const uint8_t* before, uint32_t nl, rep_vec* out) {
+  qsort(a->v, a->n, sizeof(laccess_t), cmp_laccess);
+  uint64_t i = 0;
+  while (i < a->n) {
+    uint64_t j = i;
+    uint32_t writes = 0;
+    while (j < a->n && a->v[j].addr == a->v[i].addr) writes += a->v[j++].kind == K_W;
+    uint32_t cls = 0, l1 = UINT32_MAX, l2 = UINT32_MAX;
+    for (uint64_t x = i; x < j && writes; ++x)
+      for (uint64_t y = x + 1; y < j; ++y) {
+        const laccess_t* p = &a->v[x]; const laccess_t* q = &a->v[y];
+        if (p->launch == q->launch) continue;
+        uint32_t m = p->launch < q->launch ? p->launch : q->launch, l = p->launch ^ q->launch ^ m;
+        if (before[(size_t)l * nl + m]) continue;   /* ordered: m completes before l starts */
+        uint32_t bit = conflict_class(p->kind, q->kind);
+        if (!bit) continue;
+        cls |= bit;
+        if (m < l1 || (m == l1 && l < l2)) { l1 = m; l2 = l; }
+      }
+    if (cls) {
+      orc_report r = {ORC_REP_GLOBAL_LAUNCHES, prog, l1, 0, 0, a->v[i].addr, l2, cls << 24};
+      rep_push(out, r);
+    }
+    i = j;
+  }
+}
+
 /* ------------------------------------------------------------ launches / programs */
 typedef struct { launch_ctx* C; uint32_t b0, b1; } worker_arg;
 static void* worker(void* p) {
@@ -504,10 +650,11 @@ int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc
   for (uint32_t p = 0; p < nprogs; ++p) {
     const orc_program* P = &progs[p];
     int32_t *writer = NULL, *reader = NULL;
-    if (O.check_interblock && nth == 1 && P->arena_words) {
+    if (O.check_interblock && P->arena_words) {
       writer = malloc(P->arena_words * sizeof(int32_t));
       reader = malloc(P->arena_words * sizeof(int32_t));
     }
+    lacc_vec prog_acc = {0};                   /* check_global: (word, launch, kind) */
     const uint32_t nl = P->nlaunches;
     /* the launches each launch follows: the previous one of its stream, the one it waits for */
     int32_t* dep_prev = malloc((nl ? nl : 1) * sizeof(int32_t));
@@ -535,9 +682,11 @@ int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc
       uint32_t nw = nth < nblocks ? nth : nblocks;
       launch_ctx* ctx = calloc(nw, sizeof(launch_ctx));
       rep_vec* reps = calloc(nw, sizeof(rep_vec));
+      gacc_vec* lacc = O.check_global ? calloc(nw, sizeof(gacc_vec)) : NULL;
       for (uint32_t i = 0; i < nw; ++i) {
         ctx[i].P = P; ctx[i].prog_idx = p; ctx[i].launch_idx = l; ctx[i].L = L; ctx[i].O = &O;
         ctx[i].budget = budget; ctx[i].reps = &reps[i]; ctx[i].writer = writer; ctx[i].reader = reader;
+        ctx[i].lacc = lacc ? &lacc[i] : NULL;
       }
       if (acc) ctx[0].acc = acc[l] = calloc(P->arena_words, 1);
       if (nw == 1) {
@@ -560,27 +709,49 @@ int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc
         res->thread_instrs += ctx[i].thread_instrs;
         res->shared_accesses += ctx[i].shared_accesses;
         res->rounds += ctx[i].rounds;
-        res->interblock_conflicts += ctx[i].conflicts;
         for (uint64_t k = 0; k < reps[i].n; ++k) rep_push(&all, reps[i].v[k]);
         free(reps[i].v);
       }
       free(reps); free(ctx);
+      if (writer) {
+        /* words two blocks of the launch touched, one writing */
+        for (uint64_t w = 0; w < P->arena_words; ++w)
+          if (writer[w] == -2 || (writer[w] >= 0 && reader[w] != -1 && reader[w] != writer[w]))
+            res->interblock_conflicts++;
+      }
+      if (lacc) {
+        gacc_vec la = {0};
+        for (uint32_t i = 0; i < nw; ++i) {
+          for (uint64_t k = 0; k < lacc[i].n; ++k) gacc_push(&la, lacc[i].v[k]);
+          free(lacc[i].v);
+        }
+        free(lacc);
+        block_races(&la, p, l, &all);          /* sorts la by (word, block, kind, pc) */
+        for (uint64_t k = 0; k < la.n;) {      /* per word: did the launch read it, write it */
+          uint64_t e = k;
+          int rd = 0, wr = 0;
+          for (; e < la.n && la.v[e].addr == la.v[k].addr; ++e) {
+            if (la.v[e].kind == K_W) wr = 1; else rd = 1;
+          }
+          if (rd) lacc_push(&prog_acc, (laccess_t){la.v[k].addr, l, K_R});
+          if (wr) lacc_push(&prog_acc, (laccess_t){la.v[k].addr, l, K_W});
+          k = e;
+        }
+        free(la.v);
+      }
       res->status[p] |= st;
       if (st & (ORC_ST_DEADLOCK | ORC_ST_STEP_LIMIT)) dead[l] = 1;   /* launches after it are skipped */
     }
+    if (O.check_global) {
+      uint8_t* before = order_matrix(dep_prev, dep_wait, nl);
+      launch_races(&prog_acc, p, before, nl, &all);
+      free(before);
+    }
+    free(prog_acc.v);
     if (acc) {
       /* pairs of launches that no chain of stream order and event waits orders: any global
          word that both touch, one of them writing, makes the result depend on timing */
-      uint8_t* before = calloc((size_t)(nl ? nl : 1) * (nl ? nl : 1), 1);   /* before[l*nl+m]: m precedes l */
-      for (uint32_t l = 0; l < nl; ++l) {
-        int32_t d[2] = {dep_prev[l], dep_wait[l]};
-        for (int k = 0; k < 2; ++k) {
-          if (d[k] < 0) continue;
-          before[(size_t)l * nl + (uint32_t)d[k]] = 1;
-          for (uint32_t m = 0; m < nl; ++m)
-            if (before[(size_t)(uint32_t)d[k] * nl + m]) before[(size_t)l * nl + m] = 1;
-        }
-      }
+      uint8_t* before = order_matrix(dep_prev, dep_wait, nl);   /* before[l*nl+m]: m precedes l */
       for (uint32_t l = 0; l < nl; ++l)
         for (uint32_t m = 0; m < l; ++m) {
           if (before[(size_t)l * nl + m] || !acc[l] || !acc[m]) continue;

@@ -28,7 +28,11 @@
  *     x%0 give 0 plus an ERR_DIV0 record; INT_MIN/-1 = INT_MIN, INT_MIN%-1 = 0; shift
  *     counts masked with 31, SHR arithmetic;
  *   - out-of-range shared/global accesses are suppressed (loads give 0) and recorded;
- *   - atomic-atomic pairs are not races; global memory is not race-checked;
+ *   - atomic-atomic pairs are not races;
+ *   - global memory (optional, check_global): the same pair rule inside a block's barrier
+ *     interval; any two blocks of one launch touching a word, one writing (blocks of a launch
+ *     have no synchronisation point, Sec. 2); any two launches that no stream order or event
+ *     wait orders touching a word, one writing (Sec. 3, streams and events);
  *   - a barrier whose waiting threads sit at different barrier instructions is
  *     reported as DIVERGENCE and then released; waiting plus exited threads is a
  *     DEADLOCK: the block stops and the program's later launches are skipped;
@@ -56,7 +60,17 @@ enum {
 enum {
   ORC_REP_RACE = 1, ORC_REP_DIVERGENCE = 2, ORC_REP_DEADLOCK = 3, ORC_REP_STEP_LIMIT = 4,
   ORC_REP_ERR_OOB_SHARED = 5, ORC_REP_ERR_OOB_GLOBAL = 6, ORC_REP_ERR_DIV0 = 7,
-  ORC_REP_ERR_UNINIT_SHARED = 8
+  ORC_REP_ERR_UNINIT_SHARED = 8,
+  /* check_global: a = global word; b, c as for RACE (classes WW and WR only) */
+  ORC_REP_GLOBAL_RACE = 9,
+  /* check_global: block = b1, epoch = 0, a = word, b = b2 (b1 < b2, the smallest pair of
+     blocks of the launch that conflict on the word), c = classes << 24 | pc range over every
+     access of the launch to the word */
+  ORC_REP_GLOBAL_BLOCKS = 10,
+  /* check_global: launch = l1, block = 0, epoch = 0, a = word, b = l2 (l1 < l2, the smallest
+     unordered pair of launches that conflict on the word), c = classes << 24 over every such
+     pair */
+  ORC_REP_GLOBAL_LAUNCHES = 11
 };
 /* race class bits (field c bits 24..27) */
 enum { ORC_CLS_WW = 1, ORC_CLS_WR = 2, ORC_CLS_WA = 4, ORC_CLS_AR = 8 };
@@ -86,11 +100,13 @@ typedef struct {
   uint32_t check_races;      /* 0 = skip the race check (plain interpreter) */
   uint32_t schedule;         /* 0 = round-lockstep (canonical), 1 = thread-sequential */
   uint32_t nthreads;         /* host threads over blocks of one launch (0/1 = serial) */
-  uint32_t check_interblock; /* 1 = flag global words shared between blocks of a launch */
+  uint32_t check_interblock; /* 1 = count global words that two blocks of one launch touch, one
+                                writing (diagnostic; serial and threaded modes) */
   uint32_t max_blocks;       /* >0: run only blocks [0, max_blocks) of each launch (timing samples) */
   uint32_t check_uninit;     /* 1 = report shared loads of words no thread of the block wrote */
   uint32_t check_streams;    /* 1 = count global words that two launches no stream or event orders
                                 both touch, one writing (serial mode only) */
+  uint32_t check_global;     /* 1 = report global-memory races (kinds 9, 10, 11) */
 } orc_opts;
 
 typedef struct {
@@ -99,7 +115,8 @@ typedef struct {
   uint64_t thread_instrs;                    /* lane-instructions executed */
   uint64_t shared_accesses;                  /* shared accesses seen by the race check */
   uint64_t rounds;                           /* rounds executed, all blocks */
-  uint64_t interblock_conflicts;             /* diagnostic (check_interblock) */
+  uint64_t interblock_conflicts;             /* diagnostic (check_interblock): words, summed
+                                                over launches */
   uint64_t stream_conflicts;                 /* diagnostic (check_streams) */
 } orc_result;
 

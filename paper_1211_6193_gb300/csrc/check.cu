@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(NC + 32, MINB) k_check(CheckArgs A) {
         for (uint32_t b = 0; b < NBUF && b < k; ++b) {
           const uint32_t last = b + ((k - 1 - b) / NBUF) * NBUF;
           const uint32_t never = 0;
-          mbar_wait(&full[b], (last / NBUF) & 1u, A.spin_limit, &never);
+          mbar_wait(&full[b], (last / NBUF) & 1u, kCopyWaitLimit, &never);
         }
       }
       __syncwarp();

@@ -92,6 +92,17 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phas
   return false;
 }
 
+// Wait for the CTA's own code-staging copy.  Every thread polls; the CTA agrees on the
+// outcome (__syncthreads_or), so that no thread takes a named barrier the others skip.  If the
+// copy has not landed within kCopyWaitLimit polls it is waited for once more with the same
+// bound; `drained` then says whether it has landed (the shared buffer and the mbarrier phase
+// may be reused) or is still in flight (the CTA must leave both alone and exit).
+__device__ __forceinline__ bool stage_wait(unsigned long long* bar, uint32_t phase, bool& drained) {
+  const bool ok = !__syncthreads_or(!mbar_wait(bar, phase, kCopyWaitLimit));
+  drained = ok || !__syncthreads_or(!mbar_wait(bar, phase, kCopyWaitLimit));
+  return ok;
+}
+
 __device__ __forceinline__ void group_sync(uint32_t id, uint32_t nthr) {
   if (nthr == 32)
     __syncwarp();
@@ -807,7 +818,8 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
   __syncthreads();
   if (s_skip) return;
   // every thread must take the same branch before the block's named barriers
-  if (__syncthreads_or(!mbar_wait(&mbar, 0, A.spin_limit))) {
+  bool drained;
+  if (!stage_wait(&mbar, 0, drained)) {
     if (threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
     return;
   }
@@ -861,8 +873,9 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
     }
     __syncthreads();
     const uint32_t nblk = min(Ls.groups, Ls.grid - it.y);
+    bool drained = true;
     if (!s_skip) {
-      const bool ok = !__syncthreads_or(!mbar_wait(&mbar, phase, A.spin_limit));
+      const bool ok = stage_wait(&mbar, phase, drained);
       phase ^= 1u;
       const uint32_t nw = (Ls.bdim + 31) >> 5;
       const uint32_t wid = threadIdx.x >> 5, g = wid / nw;
@@ -876,6 +889,9 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
       __threadfence();
       atomicAdd(&A.launch_done[it.x], nblk);
     }
+    // a staging copy still in flight owns the code buffer and the mbarrier: this CTA takes no
+    // further item (the others drain the queue)
+    if (!drained) break;
   }
 }
 

@@ -1,15 +1,16 @@
 // noalloc.cu - sr_check_program_noalloc: the whole check of one program without any
 // device (or host heap) allocation.
 //
-// Some callers cannot allocate: code running inside a CUDA graph that is being
-// captured, inside a framework that owns every byte of device memory, or in a process
-// that forbids cudaMalloc after start-up.  This entry point runs the same kernels as
+// Some callers cannot allocate: code inside a framework that owns every byte of device
+// memory through its own allocator, or in a process that forbids cudaMalloc after
+// start-up.  This entry point runs the same kernels as
 // load_programs + run_and_check, but every intermediate buffer (packed code, launch
 // table, access logs, per-block results, scan and checker scratch) lives in one
 // file-scope __device__ array of SR_NOALLOC_SCRATCH_BYTES.  The caller passes the inputs
 // (program descriptors in host memory, the global arena on the device) and the outputs
 // (the arena, updated in place, and a device report buffer).
 #include <algorithm>
+#include <mutex>
 
 #include "host_prep.h"
 #include "sr_internal.h"
@@ -24,13 +25,29 @@ constexpr uint32_t kMaxLaunches = 256;
 constexpr uint32_t kMaxWaves = 256;
 constexpr uint32_t kCheckCtas = 8;          // checker CTAs (each owns 256 KB of race-entry staging)
 
-void* g_scratch_addr[kMaxDevices];           // device address of the array, per device
+// Device address of the array and the result of the one-time set-up, per device.  The
+// set-up runs once per device under std::call_once, also when several host threads make
+// their first call at the same time.
+void* g_scratch_addr[kMaxDevices];
+cudaError_t g_setup_err[kMaxDevices];
+std::once_flag g_setup_once[kMaxDevices];
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NoallocWave {
   uint32_t li0, li1, gb0, gb1;
 };
+
+// Host staging of one call (~150 KB): thread-local, so that a call needs neither heap
+// memory nor a large stack (callers on threads with small stacks).
+struct HostStaging {
+  uint2 code[SR_MAX_CODE + 2];
+  uint8_t colour[SR_MAX_CODE + 1];
+  uint32_t acc[SR_MAX_CODE + 1], bar[SR_MAX_CODE + 1], spc[SR_MAX_CODE + 1], snx[SR_MAX_CODE + 1];
+  sr::LaunchDev L[kMaxLaunches];
+  NoallocWave waves[kMaxWaves];
+};
+thread_local HostStaging t_staging;
 
 }  // namespace
 
@@ -49,6 +66,14 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   pv.global_init = &one_word;
   if (validate(&pv, msg, sizeof msg) != SR_OK) return SR_E_INVAL;
   if (prog->nlaunches > kMaxLaunches) return SR_E_RANGE;
+  // on a stream that is being captured the copies and the synchronisation below would fail
+  // and invalidate the caller's capture: refuse before touching the stream
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return SR_E_INVAL;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return SR_E_INVAL;
 
   // ---- once per device: the array's device address and the kernels' attributes
   int dev = 0, sms = 0, optin = 0;
@@ -56,21 +81,21 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return SR_E_CUDA;
-  if (!g_scratch_addr[dev]) {
+  std::call_once(g_setup_once[dev], [dev, optin]() {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e == cudaSuccess) e = sr::init_kernel_attributes((uint32_t)optin);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return SR_E_CUDA;
-    }
-    g_scratch_addr[dev] = ptr;
-  }
+    if (e != cudaSuccess) cudaGetLastError();
+    g_setup_err[dev] = e;
+    g_scratch_addr[dev] = e == cudaSuccess ? ptr : nullptr;
+  });
+  if (g_setup_err[dev] != cudaSuccess || !g_scratch_addr[dev]) return SR_E_CUDA;
   unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
 
-  // ---- pack code and launch table (host stack only)
+  // ---- pack code and launch table (thread-local host staging)
+  HostStaging& T = t_staging;
   const uint32_t ncode = prog->ncode;
-  uint2 code[SR_MAX_CODE + 2];
+  uint2* code = T.code;
   const RegMap rm = map_registers(*prog);
   for (uint32_t pc = 0; pc < ncode; ++pc) code[pc] = pack(prog->code[pc], rm);
   const uint32_t z = rm.nrows - 1;
@@ -78,10 +103,8 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   uint32_t npacked = ncode + 1;
   if (npacked & 1) code[npacked++] = make_uint2(SR_OP_EXIT, 0);
 
-  uint8_t colour[SR_MAX_CODE + 1];
-  uint32_t acc[SR_MAX_CODE + 1], bar[SR_MAX_CODE + 1], spc[SR_MAX_CODE + 1], snx[SR_MAX_CODE + 1];
-  const BoundScratch ws{colour, acc, bar, spc, snx};
-  sr::LaunchDev L[kMaxLaunches];
+  const BoundScratch ws{T.colour, T.acc, T.bar, T.spc, T.snx};
+  sr::LaunchDev* L = T.L;
   uint64_t nblocks = 0, check_items = 0;
   for (uint32_t l = 0; l < prog->nlaunches; ++l) {
     const sr_launch& pl = prog->launches[l];
@@ -143,7 +166,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   const uint64_t log_records = (SR_NOALLOC_SCRATCH_BYTES - off) / 8;
 
   // waves: consecutive launches whose logs fit the remaining scratch together
-  NoallocWave waves[kMaxWaves];
+  NoallocWave* waves = T.waves;
   uint32_t nwaves = 0;
   uint64_t used = 0;
   for (uint32_t l = 0; l < nl; ++l) {

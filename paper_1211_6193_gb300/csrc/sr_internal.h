@@ -14,6 +14,11 @@ namespace sr {
 constexpr uint32_t kNoDest = 31;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kMaxBudget = 1u << 26;  // epochs and rounds stay below 2^26
+// Polls of an mbarrier that only a CTA's own bulk copy (global -> its shared memory) completes.
+// No other agent is involved, so this bound does not follow the caller's spin_limit: a copy that
+// has not landed after this many polls is waited for once more, with the same bound, before the
+// CTA returns or reuses the buffer, so that no copy is left writing shared memory.
+constexpr uint32_t kCopyWaitLimit = 1u << 24;
 
 // thread status of a simulated thread
 enum : uint32_t { ST_RUN = 0, ST_WAIT = 1, ST_EXIT = 2, ST_NONE = 3 };

@@ -291,10 +291,11 @@ def draw_spec(seed: int, max_grid: int = 4096, bug_rate: float = 0.3,
 
 
 def batch(n_programs: int = 4096, seed: int = 3, max_grid: int = 4096, bug_rate: float = 0.3,
-          families: Tuple[str, ...] = FAMILIES) -> List[Program]:
-    """The batched workload: program i drawn from SplitMix64 sub-stream (seed, i)."""
+          families: Tuple[str, ...] = FAMILIES, indices=None) -> List[Program]:
+    """The batched workload: program i drawn from SplitMix64 sub-stream (seed, i).  With
+    ``indices``, only those programs of the n_programs (the same ones, in that order)."""
     out = []
-    for i in range(n_programs):
+    for i in (range(n_programs) if indices is None else indices):
         s = rng.derive(seed, i)
         out.append(build_family(draw_spec(s, max_grid, bug_rate, families), s))
     return out

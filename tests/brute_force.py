@@ -23,12 +23,15 @@ from paper_1211_6193_gb300.workloads import ir
 # ------------------------------------------------------------ per-thread event lists
 
 
-def thread_events(prog: ir.Program, tid: int):
+def thread_events(prog: ir.Program, tid: int, space: str = "shared"):
     """Run one thread alone, loads symbolic; return its events and global stores.
 
     events: ("R", addr, pc, load_id) | ("W", addr, pc, value) | ("A", addr, pc, value) | ("B",)
     gstores: (addr, value) with value an int or ("load", load_id)
+    With space == "global" the events are the global loads and stores of words
+    [0, meta["nwords"]) and every other global store is a gstore.
     """
+    gwords = prog.meta.get("nwords", 0) if space == "global" else 0
     launch = prog.launches[0]
     regs: Dict[int, object] = {i: 0 for i in range(16)}
     for i, v in enumerate(launch.params):
@@ -68,6 +71,12 @@ def thread_events(prog: ir.Program, tid: int):
             events.append(("W", concrete(rd(a)) + imm, pc, concrete(rd(b))))
         elif base == ir.ATOMS:
             events.append(("A", concrete(rd(a)) + imm, pc, concrete(rd(b))))
+        elif base == ir.LDG and space == "global" and concrete(rd(a)) + imm < gwords:
+            regs[d] = ("load", nload)
+            events.append(("R", concrete(rd(a)) + imm, pc, nload))
+            nload += 1
+        elif base == ir.STG and space == "global" and concrete(rd(a)) + imm < gwords:
+            events.append(("W", concrete(rd(a)) + imm, pc, concrete(rd(b))))
         elif base == ir.STG:
             gstores.append((concrete(rd(a)) + imm, rd(b)))
         elif base == ir.BAR:
@@ -86,17 +95,20 @@ def thread_events(prog: ir.Program, tid: int):
 # ------------------------------------------------------------ interleavings
 
 
-def enumerate_outcomes(prog: ir.Program):
-    """All final arenas over all barrier-respecting interleavings, plus reachable positions."""
+def enumerate_outcomes(prog: ir.Program, space: str = "shared"):
+    """All final arenas over all barrier-respecting interleavings, plus reachable positions.
+    With space == "global" the interleaved memory is the arena's words [0, meta["nwords"])."""
     launch = prog.launches[0]
-    n, nwords = launch.block_dim, launch.shmem_words
-    per = [thread_events(prog, t) for t in range(n)]
+    n = launch.block_dim
+    nwords = launch.shmem_words if space == "shared" else prog.meta["nwords"]
+    per = [thread_events(prog, t, space) for t in range(n)]
     evs = [p[0] for p in per]
     lens = [len(e) for e in evs]
     outcomes: Set[Tuple[int, ...]] = set()
     positions: Set[Tuple[int, ...]] = set()
     seen = set()
-    stack = [(tuple([0] * n), tuple([0] * nwords), tuple(() for _ in range(n)))]
+    mem0 = [0] * nwords if space == "shared" else [int(x) for x in prog.global_init[:nwords]]
+    stack = [(tuple([0] * n), tuple(mem0), tuple(() for _ in range(n)))]
     while stack:
         state = stack.pop()
         if state in seen:
@@ -106,6 +118,8 @@ def enumerate_outcomes(prog: ir.Program):
         positions.add(pos)
         if all(pos[i] == lens[i] for i in range(n)):
             arena = np.array(prog.global_init, dtype=np.int64)
+            if space == "global":
+                arena[:nwords] = mem
             for t in range(n):
                 for addr, v in per[t][1]:
                     arena[addr] = loads[t][v[1]] if isinstance(v, tuple) else v

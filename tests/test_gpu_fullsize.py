@@ -44,7 +44,10 @@ def test_full_size_batched(B):
         step = 256
         for i0 in range(0, len(progs), step):
             i1 = min(len(progs), i0 + step)
-            want = oracle.run(progs[i0:i1], nthreads=CORES)
+            # check_interblock certifies the reading that no two blocks of a launch share a
+            # written global word (blocks run concurrently here, in order in the oracle)
+            want = oracle.run(progs[i0:i1], nthreads=CORES, check_interblock=True)
+            assert want.interblock_conflicts == 0, i0
             _same_reports(reps[cut[i0]:cut[i1]], want.reports, prog_offset=i0)
             for k in range(i0, i1):
                 assert np.array_equal(b.fetch_memory(k), want.arenas[k - i0]), k
@@ -55,7 +58,8 @@ def test_full_size_batched(B):
 def test_full_size_stencil(B):
     p = stencil2d.program(log2w=13, steps=16, buggy_launch=8, seed=4)
     got = B.check([p], mode="plain")
-    want = oracle.run([p], nthreads=CORES)
+    want = oracle.run([p], nthreads=CORES, check_interblock=True)
+    assert want.interblock_conflicts == 0
     _same_reports(got.reports, want.reports)
     assert np.array_equal(got.arenas[0], want.arenas[0])
     assert int(got.status[0]) == int(want.status[0]) == 0

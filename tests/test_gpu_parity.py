@@ -437,3 +437,26 @@ def test_full_size_plain_reduction(B):
     want = oracle.run([p], max_blocks=8)
     assert got.report_tuples()[:8 * 32] == want.report_tuples()
     assert got.stats.shared_accesses == 16384 * 4094
+
+
+def tag_wrap_program(iters: int = 300000) -> ir.Program:
+    """One block of two threads runs `iters` barrier intervals: each thread stores its own
+    word every interval (no race), and every 1024th interval thread t also reads word t + 1
+    (thread 0's read races with thread 1's store of word 1).  More than 2^18 intervals on
+    one checker CTA make the checker's 18-bit interval tags wrap."""
+    from paper_1211_6193_gb300.workloads.ir import Asm, Launch, Program, TID, r0, r1, r2, r3, r4
+    a = Asm()
+    a.s2r(r0, TID).mov(r1, iters)
+    a.label("loop").sts(r0, r1, 0).and_(r2, r1, 1023).seq(r3, r2, 0).brz(r3, "skip")
+    a.lds(r4, r0, 1)
+    a.label("skip").bar().sub(r1, r1, 1).brnz(r1, "loop").exit()
+    return Program(a.assemble(), [0], [Launch(0, 1, 2, 3, ())], np.zeros(4, np.int32), name=f"tag_wrap_{iters}")
+
+
+@pytest.mark.parametrize("variant", [0, 1, 5])
+def test_checker_interval_tags_wrap(B, variant):
+    p = tag_wrap_program()
+    got, want = assert_parity(B, [p], "plain", check_variant=variant, loop_log_records=1 << 20)
+    # iterations 300000, 299999, ... 1: the racy ones are those whose counter is a multiple of 1024
+    assert len(got.reports) == 300000 // 1024
+    assert all(r[0] == B.RACE and r[5] == 1 and r[6] == 1 for r in got.report_tuples())

@@ -18,7 +18,8 @@ MUTANTS = {
     "atomic_atomic_is_race": (
         "if (!bit) continue;",
         "if (!bit && !(k1 == K_A && k2 == K_A)) continue; if (!bit) bit = ORC_CLS_WA;"),
-    "history_not_cleared_at_barrier": ("  B->acc.n = 0;\n  if (B->err_any)", "  if (B->err_any)"),
+    "history_not_cleared_at_barrier": ("  B->acc.n = 0;\n  if (B->gacc.n)", "  if (B->gacc.n)"),
+    "global_history_not_cleared_at_barrier": ("  B->gacc.n = 0;\n", ""),
     "same_thread_pairs_race": ("if (p->tid == q->tid) continue;", ""),
     "stores_visible_within_round": (
         "if (B->deferred) st_push(&B->sst, addr, vb); else B->sh[addr] = vb;", "B->sh[addr] = vb;"),
@@ -43,7 +44,7 @@ MUTANTS = {
     "skip_not_propagated": ("dead[l] = 1;                                            /* skipped */", ""),
     "divergence_unchecked": ("if (pmin != pmax)        /* all threads wait", "if (0)        /* all threads wait"),
     "logical_right_shift": ("return va < 0 ? ~((~va) >> s) : (va >> s);", "return as_i32((uint32_t)va >> s);"),
-    "pc_range_not_recorded": ("if (p->pc < pclo) pclo = p->pc;\n        if (p->pc > pchi) pchi = p->pc;", ""),
+    "pc_range_not_recorded": ("if (p->pc < pclo) pclo = p->pc;\n      if (p->pc > pchi) pchi = p->pc;", ""),
     "shared_bound_off_by_one": (
         "if (addr < 0 || (uint32_t)addr >= B->shw) { note_err(B, pc, t); break; }",
         "if (addr < 0 || (uint32_t)addr >= B->shw + 1) { note_err(B, pc, t); break; }"),
@@ -56,6 +57,20 @@ MUTANTS = {
                                      "B->bp[t] = base == ORC_BAR || va != 0;"),
     "written_marked_at_issue": ("if (!B->deferred) B->written[addr] = 1;", "B->written[addr] = 1;"),
     "atomics_do_not_initialise": ("  for (uint64_t i = 0; i < B->ats.n; ++i) B->written[B->ats.v[i].addr] = 1;\n", ""),
+    "interblock_counter_never_increments": ("res->interblock_conflicts++;", ";"),
+    "interblock_same_block_conflicts": ("if (cur == me || cur == -2) return;", "if (cur == -2) return;"),
+    "global_block_pairs_include_same_block": ("if (p->block == q->block) continue;", ""),
+    "global_block_pair_largest": (
+        "if (lo < b1 || (lo == b1 && hi < b2)) { b1 = lo; b2 = hi; }",
+        "if (b1 == UINT32_MAX || lo > b1 || (lo == b1 && hi > b2)) { b1 = lo; b2 = hi; }"),
+    "launch_order_ignored": (
+        "if (before[(size_t)l * nl + m]) continue;   /* ordered: m completes before l starts */", ""),
+    "launch_reads_dropped": ("if (rd) lacc_push(&prog_acc, (laccess_t){la.v[k].addr, l, K_R});", ""),
+    "global_loads_not_checked": (
+        "acc_push(&B->gacc, (access_t){(uint32_t)addr, t, is_write ? K_W : K_R, pc});",
+        "if (is_write) acc_push(&B->gacc, (access_t){(uint32_t)addr, t, K_W, pc});"),
+    "global_interval_check_skipped": (
+        "if (B->gacc.n) interval_races(B, &B->gacc, ORC_REP_GLOBAL_RACE);", ""),
     "warps_of_16": (
         "uint32_t lo = 32 * w, hi = lo + 32 < B->n ? lo + 32 : B->n;",
         "uint32_t lo = 16 * w, hi = lo + 16 < B->n ? lo + 16 : B->n; if (lo >= B->n) continue;"),
@@ -84,7 +99,8 @@ def test_pins_catch_planted_oracle_mistake(workspace, name):
     shutil.rmtree(os.path.join(workspace, "oracle", "_build"), ignore_errors=True)
     try:
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                            "tests/test_oracle_pins.py"], cwd=workspace, capture_output=True, text=True,
+                            "tests/test_oracle_pins.py", "tests/test_oracle_global.py"], cwd=workspace,
+                           capture_output=True, text=True,
                            timeout=120)
         caught = r.returncode != 0
     except subprocess.TimeoutExpired:

@@ -48,14 +48,47 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
     results, st = srv.serve(jobs)
     srv.close()
     assert st.jobs == len(jobs) and st.batches >= 3 and st.max_inflight_seen >= 2
+    import oracle
     alone = {}
     for j in jobs:
         key = id(j.program)
         if key not in alone:
             alone[key] = binding.check([j.program])
+            # and alone it is the oracle's result
+            want = oracle.run([j.program])
+            assert alone[key].report_tuples() == want.report_tuples(), j.program.name
+            assert np.array_equal(alone[key].arenas[0], want.arenas[0]), j.program.name
+            assert int(alone[key].status[0]) & 3 == int(want.status[0]), j.program.name
         a, r = alone[key], results[j.jid]
         # every field but `prog` (the job's slot in its micro-batch)
         assert [tuple(int(x) for x in t)[:1] + tuple(int(x) for x in t)[2:] for t in r.reports] == \
             [t[:1] + t[2:] for t in a.report_tuples()], j.jid
         assert np.array_equal(r.arena, a.arenas[0]), j.jid
         assert r.status == int(a.status[0]), j.jid
+
+
+@pytest.mark.gpu
+def test_serving_job_pool_matches_the_oracle():
+    """The 512-program pool the serving benchmark draws its jobs from (seed 5, full-size
+    grids), run as one batch, against the oracle on every program (a slice at a time)."""
+    import os
+
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1211_6193_gb300 import binding, build
+    build.build()
+    pool = serving.job_pool(512, seed=5)
+    got = binding.check(pool, mode="batched")
+    reps = got.reports
+    cut = np.searchsorted(reps["prog"], np.arange(0, len(pool) + 1, dtype=np.uint32))
+    for i0 in range(0, len(pool), 128):
+        i1 = min(len(pool), i0 + 128)
+        want = oracle.run(pool[i0:i1], nthreads=os.cpu_count() or 1)
+        w = want.reports.copy()
+        w["prog"] += np.uint32(i0)
+        assert [tuple(int(x) for x in r) for r in reps[cut[i0]:cut[i1]]] == [tuple(int(x) for x in r) for r in w]
+        for k in range(i0, i1):
+            assert np.array_equal(got.arenas[k], want.arenas[k - i0]), k
+        assert list(got.status[i0:i1] & 3) == list(want.status)
