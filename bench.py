@@ -1,23 +1,30 @@
-"""Benchmark: checked shared accesses per second (race-checked SIMT interpretation).
+"""Benchmark: checked accesses/s and simulated thread-instructions/s, batched vs plain, with
+the HBM roofline of the whole hot path.
 
-Default workload (the plain single program): a shared-memory tree reduction over 2^24
-int32 values uniform in [0, 100) (SplitMix64 seed 1), 16384 blocks x 1024 threads, the
-barrier after level 3 missing (every block reports 32 races).  One step = one pass of
-the whole hot path: arena reset, SIMT interpretation with access logging, race check of
+Default workload (batched): 4096 seed-generated programs (reduction / 1-D stencil radius 1-8
+/ 32x32 tiled transpose / 256-bin shared-atomic histogram), grids log-uniform in [1, 4096],
+blockDim 32-1024, shared arrays up to 48 KB, 20-400 instructions, 30% with one planted bug
+(SplitMix64 seed 3): 1.97M blocks, 1.0e9 simulated threads, 6.1e9 checked shared accesses.
+One step = one pass of the whole hot path over the resident batch: arena reset, SIMT
+interpretation of every launch with access logging (one persistent launch), race check of
 every barrier interval, barrier checks, canonical report ordering.
 
-  value  : checked shared accesses / s with the programs resident on the device
+  value  : checked shared accesses / s, batched path, programs resident on the device
+  plain_path : the same programs through one kernel launch per (program, launch)
   e2e    : the same metric through the C ABI from pinned host buffers, per step
            load_programs (H2D) + run_and_check + fetch_reports + fetch_memory of every
            program (D2H)
-  roofline     : the interpreter against the int32 lane rate (152 SMs x 128 lanes x clock)
-                 and the race check against the measured HBM bandwidth (8 B per logged
-                 access + 16 B per race entry), each from its own CUDA-event stage time
+  roofline : the algorithmic HBM bytes of a step (16 B per checked shared access, 4 B per
+             simulated global load or store, 32 B per report, the initial and final arenas)
+             over the dominant kernel's (the interpreter's) CUDA-event time, against the
+             measured copy bandwidth; beside it the interpreter's issue picture and the race
+             check's own HBM roofline
   cpu_baseline : the CPU oracle on the host cores, on a bounded block sample
   clocks       : nvidia-smi samples of the SM clock and throttle reasons while timing
 
-Other workloads (--workload): ``batched`` = 4096 seed-generated programs (batched and
-plain paths both timed), ``stencil2d`` = the 8192^2, 16-launch log-heavy stencil.
+Other workloads (--workload): ``reduction`` = the plain 2^24-element tree reduction (16384 x
+1024 threads, missing barrier at level 3), ``stencil2d`` = the 8192^2, 16-launch log-heavy
+stencil, ``serving`` = continuous batching at 2000 jobs/s.
 Kernel shapes (interpreter CTAs per SM or register budget, race-check variant) are picked
 by the autotuner before the timed region unless a shape flag or --no-tune fixes them.
 --impl reference times the CPU oracle on a bounded block sample of the same workload.
@@ -38,7 +45,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "checked shared accesses/s (race-checked SIMT interpretation)"
+METRIC = "checked accesses/sec + sim thread-instr/sec (batched vs plain), HBM % roofline"
 UNIT = "accesses/s"
 WORKLOADS = {
     "reduction": "plain single program: shared-memory tree reduction over 2^24 int32, 16384 blocks x 1024 threads, "
@@ -60,7 +67,7 @@ def parse():
                          "that the clock samples, taken every 200 ms, fall inside the timed region; else 10)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="reduction", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
     ap.add_argument("--interp-variant", type=int, default=0, choices=[0, 1, 2],
                     help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
@@ -169,7 +176,7 @@ def oracle_rate(progs, sample_blocks: int):
 
 
 def default_sample(name: str) -> int:
-    return {"reduction": 16384, "batched": 8, "stencil2d": 256, "serving": 8}[name]
+    return {"reduction": 16384, "batched": 4, "stencil2d": 256, "serving": 8}[name]
 
 
 def run_reference(args):
@@ -360,30 +367,44 @@ def run_native(args):
         plain = {"value": pst.shared_accesses / (pms / 1e3), "ms_per_step": pms, "stage_ms": pstage,
                  "batched_speedup": pms / (dev_ms / args.steps), "shapes": popts}
 
-    # ---- rooflines: the interpreter (dominant) is bound by integer issue, the checker by HBM
-    int_peak = 152 * 128 * sm_max * 1e6            # int32 lane-ops/s: 152 SMs x 128 lanes x max clock
-    interp_rate = st.thread_instrs / (stage["interp"] / 1e3)
-    check_bytes = 8 * st.shared_accesses + 16 * n_reports
-    check_gbs = check_bytes / (stage["check"] / 1e3) / 1e9 if stage["check"] > 0 else 0.0
+    # ---- roofline of the whole hot path (HBM): the algorithmic bytes of one step, over the
+    # dominant kernel's (the interpreter's) CUDA-event time, against the measured copy bandwidth
+    arena_words = sum((p.global_init.size + 3) & ~3 for p in progs)
+    alg = {"checked_shared_access": 16, "simulated_global_access": 4, "report": 32, "arena_word": 8}
+    step_bytes = (alg["checked_shared_access"] * st.shared_accesses + alg["simulated_global_access"] *
+                  st.global_accesses + alg["report"] * n_reports + alg["arena_word"] * arena_words)
+    interp_kernel = "k_interp_plain" if mode == "plain" else "k_interp_batched"
+    achieved = step_bytes / (stage["interp"] / 1e3) / 1e9
     isha, csha = src_sha("interp.cu", "sr_internal.h"), src_sha("check.cu", "sr_internal.h")
     fused = bool(opts.get("fused_check"))
     units = {"block": nblocks, "record": st.shared_accesses}
-    roofline = {"bound": "alu", "kernel": "k_interp_plain" if mode == "plain" else "k_interp_batched",
-                "achieved": interp_rate, "peak": int_peak, "unit": "int32 ops/s", "frac": interp_rate / int_peak,
-                "algorithmic_unit": "simulated thread-instruction",
-                "traffic": None if fused else traffic_per_launch(
-                    args.workload, "k_interp_plain" if mode == "plain" else "k_interp_batched", isha, units),
-                "peak_source": "derived: 152 SMs x 128 int32 lanes x sm_max_mhz (MEASURED_PEAKS.json)",
-                "stage_ms": stage,
-                "checker": {"bound": "hbm", "kernel": check_kernel(opts.get("check_variant", 0)),
-                            "achieved": check_gbs, "peak": hbm_peak,
-                            "unit": "GB/s", "frac": check_gbs / hbm_peak, "peak_source": peak_src,
-                            "algorithmic_bytes": "8 B read per logged access + 16 B per race entry",
-                            "traffic": traffic_per_launch(args.workload, check_kernel(opts.get("check_variant", 0)),
-                                                          csha, units)}}
+    int_peak = 152 * 128 * sm_max * 1e6            # int32 lane-ops/s: 152 SMs x 128 lanes x max clock
+    roofline = {
+        "bound": "hbm", "kernel": interp_kernel, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+        "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy)",
+        "traffic": None if fused else traffic_per_launch(args.workload, interp_kernel, isha, units),
+        "algorithmic_bytes_per_step": step_bytes,
+        "algorithmic_bytes": "16 B per checked shared access (8 B record written + read), 4 B per simulated "
+                             "global load/store, 32 B per report, 8 B per arena word (initial read + final write)",
+        "step_frac": step_bytes / (dev_ms / args.steps / 1e3) / 1e9 / hbm_peak,
+        "stage_ms": stage,
+        "interpreter_issue": {
+            "sim_thread_instrs_per_s": st.thread_instrs / (stage["interp"] / 1e3),
+            "int32_lane_peak": int_peak, "frac_of_lane_peak": st.thread_instrs / (stage["interp"] / 1e3) / int_peak,
+            "note": "issue-bound: real warp-instructions per simulated warp-instruction and issue-active % are "
+                    "in profiles/ (ncu, small case)"},
+    }
     if fused:      # races decided inside the interpreter: no log is written, the check stage only skips
         roofline["checker"] = {"bound": None, "kernel": None, "stage_ms": stage["check"],
                                "note": "fused race check: no access log written or read"}
+    else:
+        check_bytes = 8 * st.shared_accesses + 16 * n_reports
+        check_gbs = check_bytes / (stage["check"] / 1e3) / 1e9 if stage["check"] > 0 else 0.0
+        roofline["checker"] = {
+            "bound": "hbm", "kernel": check_kernel(opts.get("check_variant", 0)), "achieved": check_gbs,
+            "peak": hbm_peak, "unit": "GB/s", "frac": check_gbs / hbm_peak, "peak_source": peak_src,
+            "algorithmic_bytes": "8 B read per logged access + 16 B per race entry",
+            "traffic": traffic_per_launch(args.workload, check_kernel(opts.get("check_variant", 0)), csha, units)}
 
     # ---- end to end through the C ABI from pinned host buffers: per step load_programs (the
     # programs' code and initial arenas host -> device), run_and_check, fetch_reports and one
@@ -422,7 +443,6 @@ def run_native(args):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {sample} blocks of every launch ({n} accesses, {dt:.1f} s)",
                "thread_instrs_per_s": irate}
-    launches_per_step = sum(len(p.launches) for p in progs) if mode == "plain" else 1
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -433,7 +453,7 @@ def run_native(args):
             "sim_thread_instrs_per_s": thread_instr_rate, "shared_accesses_per_step": st.shared_accesses,
             "reports_per_step": n_reports, "wall_s": t_wall, "e2e": e2e, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk,
-            "gpu_launches": args.steps * (launches_per_step + 5)}
+            "gpu_launches": args.steps * st.kernels, "waves": st.waves}
     if plain is not None:
         line["plain_path"] = plain
     if rank == 0:

@@ -100,8 +100,19 @@ enum {
   SR_REP_ERR_OOB_SHARED = 5, /* a = pc, b = lowest tid, c = thread executions in the interval */
   SR_REP_ERR_OOB_GLOBAL = 6, /* same fields */
   SR_REP_ERR_DIV0 = 7,       /* same fields */
-  SR_REP_ERR_UNINIT_SHARED = 8 /* (with opts.check_uninit) a shared load of a word no thread of the
+  SR_REP_ERR_UNINIT_SHARED = 8, /* (with opts.check_uninit) a shared load of a word no thread of the
                                   block stored or added to in an earlier round; same fields */
+  /* with opts.check_global (Sec. 3.1's race definition on global words): */
+  SR_REP_GLOBAL_RACE = 9,    /* inside a barrier interval of a block: a = word of the program's
+                                arena, b and c as for SR_REP_RACE (classes WW and WR) */
+  SR_REP_GLOBAL_BLOCKS = 10, /* between blocks of one launch (nothing orders them before the kernel
+                                call ends, Sec. 2): block = b1, epoch = 0, a = word, b = b2 (b1 < b2,
+                                the smallest conflicting pair of blocks), c = class << 24 | pc_lo << 12
+                                | pc_hi over the launch's accesses to the word */
+  SR_REP_GLOBAL_LAUNCHES = 11 /* between launches that no stream order or event wait orders (Sec. 3,
+                                streams and events): launch = l1, block = 0, epoch = 0, a = word,
+                                b = l2 (l1 < l2, the smallest such conflicting pair), c = class << 24
+                                over every such pair */
 };
 enum { SR_CLS_WW = 1, SR_CLS_WR = 2, SR_CLS_WA = 4, SR_CLS_AR = 8 };
 
@@ -180,6 +191,12 @@ typedef struct {
                                 writes no access log, for every launch whose summaries fit in
                                 shared memory beside the block; same reports.  0 = access log +
                                 race-check kernel */
+  uint32_t check_global;     /* 1 = also check global memory for races (SR_REP_GLOBAL_*): every global
+                                load and store is logged (16 B) and the logs are grouped by word with a
+                                radix sort.  A program whose launches are not all ordered keeps its
+                                launches in one wave; fused_check is ignored (the log path runs).
+                                Programs racing on global memory have timing-dependent memory images:
+                                the reports are exact, the racing words are not.  0 = off */
 } sr_opts;
 
 #define SR_CHECK_VARIANTS 5
@@ -192,6 +209,10 @@ typedef struct {
   uint64_t log_bytes;        /* bytes of access-log capacity reserved on the device */
   uint64_t blocks;           /* simulated blocks in the batch */
   float ms_reset, ms_interp, ms_check, ms_compact;   /* last run, when opts.profile */
+  uint32_t waves;            /* launch groups whose logs were resident together in the last run */
+  uint32_t kernels;          /* kernel launches of the library enqueued by the last run */
+  float ms_global;           /* last run, when opts.profile: the global-memory race check */
+  uint64_t global_records;   /* global accesses logged for the global-memory race check (last run) */
 } sr_stats;
 
 /* Create a context on the current CUDA device.  opts may be NULL (defaults). */

@@ -25,6 +25,7 @@ SR_OK, SR_E_INVAL, SR_E_NOMEM, SR_E_CUDA, SR_E_TIMEOUT, SR_E_RANGE = 0, -1, -2, 
 SR_ALL_PROGRAMS = 0xFFFFFFFF
 MODE_PLAIN, MODE_BATCHED = 0, 1
 RACE, DIVERGENCE, DEADLOCK, STEP_LIMIT, ERR_OOB_SHARED, ERR_OOB_GLOBAL, ERR_DIV0, ERR_UNINIT_SHARED = range(1, 9)
+GLOBAL_RACE, GLOBAL_BLOCKS, GLOBAL_LAUNCHES = 9, 10, 11
 ST_DEADLOCK, ST_STEP_LIMIT, ST_LOG_OVERFLOW, ST_INTERNAL = 1, 2, 4, 8
 REPORT_DTYPE = np.dtype([(n, "<u4") for n in ("kind", "prog", "launch", "block", "epoch", "a", "b", "c")])
 
@@ -65,14 +66,15 @@ class sr_opts(C.Structure):
                 ("interp_variant", C.c_uint32), ("use_graph", C.c_uint32), ("profile", C.c_uint32),
                 ("spin_limit", C.c_uint32), ("log_budget_mb", C.c_uint32), ("report_cap", C.c_uint32),
                 ("allocator", C.POINTER(sr_allocator)), ("check_variant", C.c_uint32),
-                ("check_uninit", C.c_uint32), ("fused_check", C.c_uint32)]
+                ("check_uninit", C.c_uint32), ("fused_check", C.c_uint32), ("check_global", C.c_uint32)]
 
 
 class sr_stats(C.Structure):
     _fields_ = [("thread_instrs", C.c_uint64), ("shared_accesses", C.c_uint64), ("global_accesses", C.c_uint64),
                 ("reports", C.c_uint64), ("log_bytes", C.c_uint64), ("blocks", C.c_uint64),
                 ("ms_reset", C.c_float), ("ms_interp", C.c_float), ("ms_check", C.c_float),
-                ("ms_compact", C.c_float)]
+                ("ms_compact", C.c_float), ("waves", C.c_uint32), ("kernels", C.c_uint32),
+                ("ms_global", C.c_float), ("global_records", C.c_uint64)]
 
 
 EXPORTS = ["sr_create", "sr_destroy", "sr_validate_program", "load_programs", "run_and_check", "fetch_reports",
@@ -203,6 +205,10 @@ class Stats:
     ms_interp: float
     ms_check: float
     ms_compact: float
+    waves: int
+    kernels: int
+    ms_global: float
+    global_records: int
 
 
 class Context:
@@ -212,7 +218,7 @@ class Context:
                  loop_log_records: int = 0, interp_variant: int = 0, use_graph: bool = False,
                  profile: bool = False, spin_limit: int = 0, log_budget_mb: int = 0, report_cap: int = 0,
                  torch_allocator: bool = True, check_variant: int = 0, check_uninit: bool = False,
-                 fused_check: bool = False):
+                 fused_check: bool = False, check_global: bool = False):
         self.lib = load_library()
         self.allocator = TorchAllocator() if torch_allocator else None
         o = sr_opts()
@@ -224,6 +230,7 @@ class Context:
         o.check_variant = check_variant
         o.check_uninit = int(check_uninit)
         o.fused_check = int(fused_check)
+        o.check_global = int(check_global)
         if self.allocator is not None:
             o.allocator = C.pointer(self.allocator.struct)
         self.opts = o

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsimtcheck.so")
-SOURCES = ["interp.cu", "check.cu", "compact.cu", "runtime.cpp", "noalloc.cu"]
+SOURCES = ["interp.cu", "check.cu", "gcheck.cu", "compact.cu", "runtime.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -925,7 +925,8 @@ cudaError_t init_check_attributes(uint32_t smem_optin) {
 
 cudaError_t init_kernel_attributes(uint32_t smem_optin) {
   cudaError_t e = init_interp_attributes(smem_optin);
-  return e == cudaSuccess ? init_check_attributes(smem_optin) : e;
+  if (e == cudaSuccess) e = init_check_attributes(smem_optin);
+  return e == cudaSuccess ? init_gcheck_attributes(smem_optin) : e;
 }
 
 cudaError_t launch_check(const CheckArgs& a, uint32_t variant, uint32_t ctas, cudaStream_t s) {

@@ -3,6 +3,7 @@
 // of a kernel's per-block access log.  Internal; not part of the C ABI.
 #pragma once
 #include <cstdio>
+#include <vector>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,19 +43,21 @@ inline bool can_err(uint32_t b) {
 struct KernelBound {
   bool cyclic = false;
   uint32_t accesses = 0, barriers = 0, err_pcs = 0;
+  uint32_t gaccesses = 0;   // global loads and stores on the longest such path
 };
-// Workspace of bound_kernel: 4 arrays of ncode + 1 entries (callers own the memory).
+// Workspace of bound_kernel: 5 arrays of ncode + 1 entries (callers own the memory).
 struct BoundScratch {
   uint8_t* colour;
   uint32_t* acc;
   uint32_t* bar;
   uint32_t* stack_pc;
   uint32_t* stack_next;
+  uint32_t* gacc;
 };
 inline KernelBound bound_kernel(const sr_instr* code, uint32_t ncode, uint32_t entry, const BoundScratch& w) {
   KernelBound kb;
   // iterative DFS with colours; longest paths by memoised post-order
-  for (uint32_t i = 0; i <= ncode; ++i) { w.colour[i] = 0; w.acc[i] = 0; w.bar[i] = 0; }
+  for (uint32_t i = 0; i <= ncode; ++i) { w.colour[i] = 0; w.acc[i] = 0; w.bar[i] = 0; w.gacc[i] = 0; }
   uint32_t depth = 0;
   auto succ = [&](uint32_t pc, uint32_t i, uint32_t& out) -> bool {
     if (pc >= ncode) return false;
@@ -89,21 +92,28 @@ inline KernelBound bound_kernel(const sr_instr* code, uint32_t ncode, uint32_t e
       continue;
     }
     const uint32_t pc = w.stack_pc[top];
-    uint32_t a = 0, br = 0, s;
-    for (uint32_t i = 0; succ(pc, i, s); ++i) { a = a > w.acc[s] ? a : w.acc[s]; br = br > w.bar[s] ? br : w.bar[s]; }
+    uint32_t a = 0, br = 0, g = 0, s;
+    for (uint32_t i = 0; succ(pc, i, s); ++i) {
+      a = a > w.acc[s] ? a : w.acc[s];
+      br = br > w.bar[s] ? br : w.bar[s];
+      g = g > w.gacc[s] ? g : w.gacc[s];
+    }
     if (pc < ncode) {
       const uint32_t b = code[pc].op_d_a_b & 0x7Fu;
       a += is_shared_access(b);
       br += is_barrier(b);
+      g += (b == SR_OP_LDG || b == SR_OP_STG);
       kb.err_pcs += can_err(b);
     }
     w.acc[pc] = a;
     w.bar[pc] = br;
+    w.gacc[pc] = g;
     w.colour[pc] = 2;
     --depth;
   }
   kb.accesses = w.acc[entry];
   kb.barriers = w.bar[entry];
+  kb.gaccesses = w.gacc[entry];
   return kb;
 }
 
@@ -214,6 +224,40 @@ inline uint64_t launch_log_cap(const KernelBound& k, uint32_t block_dim, uint32_
   }
   if (!check_races) recs = 0;
   return (recs + 2 * misc + 1) & ~1ull;
+}
+
+// Global-log region (records per block, even) of one launch for the global-memory race
+// check: the kernel's static bound of global loads and stores per thread, or `loop_records`
+// for kernels with loops.
+inline uint64_t launch_glog_cap(const KernelBound& k, uint32_t block_dim, uint32_t loop_records) {
+  const uint64_t recs = k.cyclic ? (uint64_t)loop_records : (uint64_t)k.gaccesses * block_dim;
+  return (recs + 1) & ~1ull;
+}
+
+// Launch-order bit matrix of one program (Sec. 3, streams and events): bit l * nl + m is set
+// when launch m precedes launch l through stream order and event waits, transitively.
+// Returns false (nothing written) when every pair of launches is ordered.
+inline bool launch_order_bits(const sr_launch* launches, uint32_t nl, std::vector<uint32_t>& bits) {
+  std::vector<uint8_t> before((size_t)nl * nl, 0);
+  for (uint32_t l = 0; l < nl; ++l) {
+    uint32_t prev, wait;
+    launch_deps(launches, l, UINT32_MAX, prev, wait);
+    for (uint32_t d : {prev, wait}) {
+      if (d == UINT32_MAX) continue;
+      before[(size_t)l * nl + d] = 1;
+      for (uint32_t m = 0; m < nl; ++m)
+        if (before[(size_t)d * nl + m]) before[(size_t)l * nl + m] = 1;
+    }
+  }
+  bool all = true;
+  for (uint32_t l = 0; l < nl && all; ++l)
+    for (uint32_t m = 0; m < l; ++m)
+      if (!before[(size_t)l * nl + m]) { all = false; break; }
+  if (all) return false;
+  bits.assign(((size_t)nl * nl + 31) / 32, 0u);
+  for (size_t i = 0; i < (size_t)nl * nl; ++i)
+    if (before[i]) bits[i / 32] |= 1u << (i % 32);
+  return true;
 }
 
 }  // namespace host

@@ -40,7 +40,8 @@ struct BlockVars {
   uint32_t n_misc, epoch, k0, flags, decision, err_dirty, status;
   uint32_t bar_np, bar_nw;     // at a release: true predicates, released threads
   uint32_t race_out;           // fused race check: race entries written so far
-  uint32_t pad[5];
+  uint32_t gcursor;            // global-log records reserved by the block
+  uint32_t pad[4];
 };
 static_assert(sizeof(BlockVars) <= 64, "block vars");
 
@@ -196,6 +197,28 @@ __device__ __forceinline__ void log_access(BlockVars* bv, unsigned long long* re
   if (me) {
     const uint32_t pos = base + __popc(m & lanemask_lt());
     if (base < front_cap && pos < front_cap)
+      region[pos] = rec;
+    else
+      atomicOr(&bv->flags, BF_OVERFLOW);
+  }
+}
+
+// Append one 16-byte global-log record per lane with `me` to the block's global log (the
+// same warp-aggregated reservation as log_access).
+__device__ __forceinline__ void log_global(BlockVars* bv, uint4* region, uint32_t cap, bool me, uint4 rec,
+                                           uint32_t lane) {
+  const uint32_t m = __ballot_sync(FULL, me);
+  if (m == 0) return;
+  const uint32_t leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) {
+    base = *reinterpret_cast<volatile uint32_t*>(&bv->gcursor);
+    if (base < cap) base = atomicAdd(&bv->gcursor, (uint32_t)__popc(m));
+  }
+  base = __shfl_sync(FULL, base, leader);
+  if (me) {
+    const uint32_t pos = base + __popc(m & lanemask_lt());
+    if (base < cap && pos < cap)
       region[pos] = rec;
     else
       atomicOr(&bv->flags, BF_OVERFLOW);
@@ -384,9 +407,9 @@ __device__ void flush_errors(BlockVars* bv, uint32_t* err, uint32_t* un, const u
 }
 
 // Run one simulated block on warps [0, nw) of a group (bar_id = its named barrier).  The
-// fused race check is compiled in only where Fused is set, so that the kernels without it
-// keep their register budget.
-template <bool Fused>
+// fused race check is compiled in only where Fused is set, and the logging of global
+// accesses only where Global is set, so that the default kernels keep their register budget.
+template <bool Fused, bool Global>
 __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block, const uint2* __restrict__ ir,
                           unsigned char* gsm, uint32_t w, uint32_t nw, uint32_t bar_id) {
   const uint32_t lane = threadIdx.x & 31;
@@ -414,6 +437,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   const uint32_t arena_words = (uint32_t)Ls->arena_words;
   unsigned long long* region = A.log + Ls->log_base + (unsigned long long)block * log_cap;
   const bool logging = A.check_races != 0;
+  // global log of this block (with Global, for launches whose glog_cap is set)
+  const uint32_t gcap = Global ? Ls->glog_cap : 0u;
+  const uint32_t gb = Ls->block_base + block;
+  uint4* gregion = Global ? A.glog + Ls->glog_base + (unsigned long long)block * gcap : nullptr;
   const uint32_t budget = A.budget, spin = A.spin_limit;
   uint32_t* myregs = regs + tid;                 // row r of this thread: myregs[r * nthr]
 
@@ -440,6 +467,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     bv->n_misc = 0; bv->epoch = 0; bv->k0 = 0; bv->flags = 0;
     bv->decision = 0; bv->err_dirty = 0; bv->status = 0;
     bv->race_out = 0;
+    bv->gcursor = 0;
   }
   if (lane == 0) clk[w] = 0;
   group_sync(bar_id, nthr);
@@ -528,6 +556,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
               }
             } else {
               n_gacc += act;
+              if (Global && gcap)
+                log_global(bv, gregion, gcap, inb, make_uint4((uint32_t)addr, epoch, tid << 16 | p, gb), lane);
             }
             break;
           }
@@ -583,6 +613,9 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
               }
             } else {
               n_gacc += act;
+              if (Global && gcap)
+                log_global(bv, gregion, gcap, inb, make_uint4((uint32_t)addr, epoch, tid << 16 | 1u << 12 | p, gb),
+                           lane);
             }
             break;
           }
@@ -781,6 +814,11 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
     r.n_misc = bv->n_misc;
     r.flags = bv->flags;
     A.blocks[Ls->block_base + block] = r;
+    if (Global && gcap) {
+      const uint32_t ng = bv->gcursor < gcap ? bv->gcursor : gcap;
+      A.glog_n[gb] = ng;
+      if (ng) atomicAdd(&A.counters->global_records, (unsigned long long)ng);
+    }
     if (r.n_log) atomicAdd(&A.counters->shared_accesses, (unsigned long long)r.n_log);
     const uint32_t bits = bv->status | ((bv->flags & BF_OVERFLOW) ? (uint32_t)SR_ST_LOG_OVERFLOW : 0u) |
                           ((bv->flags & BF_INTERNAL) ? (uint32_t)SR_ST_INTERNAL : 0u);
@@ -799,7 +837,7 @@ __device__ __forceinline__ bool deps_dead(const RunArgs& A, const LaunchDev& L) 
 // One CTA per simulated block; one kernel launch per (program, launch), in an order that
 // respects every stream and wait.  MINB = 2 caps registers so that two 1024-thread CTAs fit
 // an SM.
-template <int MINB, bool Fused>
+template <int MINB, bool Fused, bool Global>
 __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t li) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LaunchDev Ls;
@@ -823,8 +861,8 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
     if (threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
     return;
   }
-  run_block<Fused>(A, &Ls, blockIdx.x, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes, threadIdx.x >> 5,
-            blockDim.x >> 5, 1);
+  run_block<Fused, Global>(A, &Ls, blockIdx.x, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes,
+                           threadIdx.x >> 5, blockDim.x >> 5, 1);
 }
 
 // Persistent: CTAs pop (launch, first block) items from a device queue; an item runs
@@ -832,7 +870,7 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
 // Items are ordered launch-wave by launch-wave, and an item waits (bounded) until every
 // block of the launches it follows (the previous launch of its stream, the one it waits
 // for) has completed; launches of other streams run meanwhile.
-template <bool Fused>
+template <bool Fused, bool Global>
 __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LaunchDev Ls;
@@ -880,8 +918,8 @@ __global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
       const uint32_t nw = (Ls.bdim + 31) >> 5;
       const uint32_t wid = threadIdx.x >> 5, g = wid / nw;
       if (ok && g < nblk)
-        run_block<Fused>(A, &Ls, it.y + g, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes + g * Ls.group_bytes,
-                  wid - g * nw, nw, 1 + g);
+        run_block<Fused, Global>(A, &Ls, it.y + g, reinterpret_cast<const uint2*>(smem),
+                                 smem + Ls.ir_bytes + g * Ls.group_bytes, wid - g * nw, nw, 1 + g);
       if (!ok && threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
     }
     __syncthreads();
@@ -913,12 +951,22 @@ static cudaError_t allow_dynamic_smem(K kernel, uint32_t smem_optin) {
 }
 
 cudaError_t init_interp_attributes(uint32_t smem_optin) {
-  cudaError_t e = allow_dynamic_smem(k_interp_plain<1, false>, smem_optin);
-  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, false>, smem_optin);
-  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<1, true>, smem_optin);
-  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, true>, smem_optin);
-  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<false>, smem_optin);
-  return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched<true>, smem_optin) : e;
+  cudaError_t e = allow_dynamic_smem(k_interp_plain<1, false, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, false, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<1, true, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, true, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<1, false, true>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, false, true>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<false, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<true, false>, smem_optin);
+  return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched<false, true>, smem_optin) : e;
+}
+
+// The plain-mode kernel for one launch: MINB (register budget) x fused race check x global log.
+template <int MINB>
+static void (*plain_kernel(bool fused, bool global))(RunArgs, uint32_t) {
+  if (global) return k_interp_plain<MINB, false, true>;
+  return fused ? k_interp_plain<MINB, true, false> : k_interp_plain<MINB, false, false>;
 }
 
 // variant: 1 = one CTA per SM budget (no register cap), 2 = two CTAs per SM, 0 = the one
@@ -926,24 +974,25 @@ cudaError_t init_interp_attributes(uint32_t smem_optin) {
 cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, uint32_t variant, cudaStream_t s) {
   const uint32_t threads = ((L.bdim + 31) / 32) * 32;
   const uint32_t smem = interp_plain_smem(L);
-  const bool fused = L.fused != 0;
+  const bool global = L.glog_cap != 0;
+  const bool fused = L.fused != 0 && !global;
   if (variant == 0) {
     int b1 = 0, b2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fused ? k_interp_plain<1, true> : k_interp_plain<1, false>,
-                                                  (int)threads, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fused ? k_interp_plain<2, true> : k_interp_plain<2, false>,
-                                                  (int)threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, plain_kernel<1>(fused, global), (int)threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, plain_kernel<2>(fused, global), (int)threads, smem);
     variant = b2 > b1 ? 2 : 1;
   }
   if (variant == 2)
-    (fused ? k_interp_plain<2, true> : k_interp_plain<2, false>)<<<L.grid, threads, smem, s>>>(a, li);
+    plain_kernel<2>(fused, global)<<<L.grid, threads, smem, s>>>(a, li);
   else
-    (fused ? k_interp_plain<1, true> : k_interp_plain<1, false>)<<<L.grid, threads, smem, s>>>(a, li);
+    plain_kernel<1>(fused, global)<<<L.grid, threads, smem, s>>>(a, li);
   return cudaGetLastError();
 }
 
-cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, cudaStream_t s) {
-  (fused ? k_interp_batched<true> : k_interp_batched<false>)<<<ctas, 1024, smem, s>>>(a);
+cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, bool global,
+                                  cudaStream_t s) {
+  auto k = global ? k_interp_batched<false, true> : fused ? k_interp_batched<true, false> : k_interp_batched<false, false>;
+  k<<<ctas, 1024, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ struct HostStaging {
   uint2 code[SR_MAX_CODE + 2];
   uint8_t colour[SR_MAX_CODE + 1];
   uint32_t acc[SR_MAX_CODE + 1], bar[SR_MAX_CODE + 1], spc[SR_MAX_CODE + 1], snx[SR_MAX_CODE + 1];
+  uint32_t gacc[SR_MAX_CODE + 1];
   sr::LaunchDev L[kMaxLaunches];
   NoallocWave waves[kMaxWaves];
 };
@@ -103,7 +104,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   uint32_t npacked = ncode + 1;
   if (npacked & 1) code[npacked++] = make_uint2(SR_OP_EXIT, 0);
 
-  const BoundScratch ws{T.colour, T.acc, T.bar, T.spc, T.snx};
+  const BoundScratch ws{T.colour, T.acc, T.bar, T.spc, T.snx, T.gacc};
   sr::LaunchDev* L = T.L;
   uint64_t nblocks = 0, check_items = 0;
   for (uint32_t l = 0; l < prog->nlaunches; ++l) {

@@ -34,6 +34,8 @@ struct Wave {
   uint32_t gb0, gb1;      // global block range
   uint32_t item0, item1;  // batched work items
   uint64_t log_records;
+  uint64_t glog_records;  // global-memory race check: records of the wave's global logs
+  uint32_t addr_bits;     // and the bits of its largest global word address
 };
 
 }  // namespace
@@ -64,6 +66,12 @@ struct sr_batch {
   DevBuf code, launches_d, arena_init, arena_work, log, blocks, prog_status, launch_dead, counters, items_d,
       queue_head, launch_done, scratch, work_head, err_flag, offsets, partials, out, total, item_launch_d;
   uint64_t out_cap = 0;
+  // global-memory race check (opts.check_global)
+  DevBuf glog, glog_n, goff, gpartials, gtotal, sort_a, sort_b, hist, status, tile_ctr, ord_bits, entries_a, entries_b,
+      gn, gcount, gstart, gn_sorted;
+  std::vector<uint32_t> ord_bits_h;
+  uint64_t glog_records = 0;               // largest wave's global-log records
+  uint64_t entry_cap = 0;                  // report entries of one wave that fit
   cudaStream_t stream = nullptr;
   bool ran = false;
   uint32_t check_ctas = 0;
@@ -73,6 +81,7 @@ struct sr_batch {
   // profiling
   std::vector<cudaEvent_t> events;
   uint32_t nevents_used = 0;
+  uint32_t kernels = 0;                    // kernel launches enqueued by the last run
 };
 
 namespace {
@@ -127,7 +136,9 @@ void free_batch_buffers(sr_ctx* c, sr_batch* b, cudaStream_t s) {
   DevBuf* all[] = {&b->code, &b->launches_d, &b->arena_init, &b->arena_work, &b->log, &b->blocks,
                    &b->prog_status, &b->launch_dead, &b->counters, &b->items_d, &b->queue_head,
                    &b->launch_done, &b->scratch, &b->work_head, &b->err_flag, &b->offsets, &b->partials,
-                   &b->out, &b->total, &b->item_launch_d};
+                   &b->out, &b->total, &b->item_launch_d, &b->glog, &b->glog_n, &b->goff, &b->gpartials,
+                   &b->gtotal, &b->sort_a, &b->sort_b, &b->hist, &b->status, &b->tile_ctr, &b->ord_bits,
+                   &b->entries_a, &b->entries_b, &b->gn, &b->gcount, &b->gstart, &b->gn_sorted};
   for (DevBuf* d : all) dev_free(c, *d, s);
 }
 
@@ -155,12 +166,54 @@ sr::CompactArgs compact_args(sr_batch* b, const Wave& w) {
   ka.out = (sr_report*)b->out.p;
   ka.out_cap = b->out_cap;
   ka.counters = (sr::Counters*)b->counters.p;
+  if (w.glog_records) {
+    ka.gcount = (const uint32_t*)b->gcount.p;
+    ka.gstart = (const unsigned long long*)b->gstart.p;
+    ka.gentries = (const uint4*)b->entries_a.p;
+    ka.gcap = b->entry_cap;
+  }
   return ka;
+}
+
+// The global-memory race check of wave wi (enqueued on s).
+sr::GcheckArgs gcheck_args(sr_ctx* c, sr_batch* b, uint32_t wi) {
+  const Wave& w = b->waves[wi];
+  sr::GcheckArgs g{};
+  g.launches = (const LaunchDev*)b->launches_d.p;
+  g.li0 = w.li0;
+  g.li1 = w.li1;
+  g.gb0 = w.gb0;
+  g.gb1 = w.gb1;
+  g.glog = (const uint4*)b->glog.p;
+  g.glog_n = (const uint32_t*)b->glog_n.p;
+  g.goff = (unsigned long long*)b->goff.p;
+  g.gtotal = (unsigned long long*)b->gtotal.p;
+  g.partials = (unsigned long long*)b->gpartials.p;
+  g.sort_a = (uint4*)b->sort_a.p;
+  g.sort_b = (uint4*)b->sort_b.p;
+  g.rec_cap = w.glog_records;
+  g.addr_passes = std::max(1u, (w.addr_bits + 7) / 8);
+  g.hist = (unsigned long long*)b->hist.p;
+  g.status = (unsigned long long*)b->status.p;
+  g.tile_ctr = (uint32_t*)b->tile_ctr.p;
+  g.err = (uint32_t*)b->err_flag.p;
+  g.spin_limit = c->opts.spin_limit;
+  g.sms = (uint32_t)c->sms;
+  g.ord_bits = (const uint32_t*)b->ord_bits.p;
+  g.entries_a = (uint4*)b->entries_a.p;
+  g.entries_b = (uint4*)b->entries_b.p;
+  g.entry_cap = b->entry_cap;
+  g.gn = (unsigned long long*)b->gn.p + wi;
+  g.gcount = (uint32_t*)b->gcount.p;
+  g.gstart = (unsigned long long*)b->gstart.p;
+  g.gn_sorted = (unsigned long long*)b->gn_sorted.p;
+  return g;
 }
 
 int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
   const sr_opts& o = c->opts;
   b->nevents_used = 0;
+  b->kernels = 0;
   auto mark = [&]() -> cudaEvent_t {
     if (!profile) return nullptr;
     cudaEvent_t e = next_event(b);
@@ -176,6 +229,7 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
   CUDA_TRY(c, cudaMemsetAsync(b->launch_done.p, 0, b->launches.size() * 4, s));
   CUDA_TRY(c, cudaMemsetAsync(b->total.p, 0, 8, s));
   CUDA_TRY(c, cudaMemsetAsync(b->err_flag.p, 0, 4, s));
+  if (o.check_global) CUDA_TRY(c, cudaMemsetAsync(b->glog_n.p, 0, (size_t)b->nblocks * 4, s));
   mark();
 
   sr::RunArgs ra{};
@@ -193,6 +247,8 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
   ra.counters = (sr::Counters*)b->counters.p;
   ra.items = (const uint2*)b->items_d.p;
   ra.launch_done = (uint32_t*)b->launch_done.p;
+  ra.glog = (uint4*)b->glog.p;
+  ra.glog_n = (uint32_t*)b->glog_n.p;
 
   for (size_t wi = 0; wi < b->waves.size(); ++wi) {
     const Wave& w = b->waves[wi];
@@ -202,10 +258,14 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       ra.queue_head = (uint32_t*)b->queue_head.p + wi;
       CUDA_TRY(c, cudaMemsetAsync(ra.queue_head, 0, 4, s));
       const uint32_t ctas = std::min<uint32_t>(ra.nitems, (uint32_t)c->sms * std::max(1u, o.ctas_per_sm));
-      if (ctas) CUDA_TRY(c, sr::launch_interp_batched(ra, ctas, b->batched_smem, o.fused_check && o.check_races, s));
+      if (ctas)
+        CUDA_TRY(c, sr::launch_interp_batched(ra, ctas, b->batched_smem,
+                                              o.fused_check && o.check_races && !o.check_global, o.check_global != 0, s));
+      b->kernels += ctas ? 1 : 0;
     } else {
       for (uint32_t li = w.li0; li < w.li1; ++li)
         CUDA_TRY(c, sr::launch_interp_plain(ra, li, b->launches[li], o.interp_variant, s));
+      b->kernels += w.li1 - w.li0;
     }
     mark();
     if (o.check_races) {
@@ -226,11 +286,15 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       CUDA_TRY(c, cudaMemsetAsync(ca.work_head, 0, 4, s));
       const uint32_t ctas = std::min<uint32_t>(b->check_ctas, ca.item1 - ca.item0);
       if (ctas) CUDA_TRY(c, sr::launch_check(ca, o.check_variant, ctas, s));
+      b->kernels += ctas ? 1 : 0;
     }
+    mark();
+    if (w.glog_records) CUDA_TRY(c, sr::launch_gcheck(gcheck_args(c, b, (uint32_t)wi), b->kernels, s));
     mark();
     const sr::CompactArgs ka = compact_args(b, w);
     CUDA_TRY(c, sr::launch_compact_scan(ka, s));
     CUDA_TRY(c, sr::launch_compact_emit(ka, s));
+    b->kernels += sr::compact_kernels(ka);
     mark();
   }
   return SR_OK;
@@ -349,11 +413,21 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
     std::vector<KernelBound> kb(P.nkernels);
     {
       std::vector<uint8_t> colour(P.ncode + 1);
-      std::vector<uint32_t> acc(P.ncode + 1), bar(P.ncode + 1), spc(P.ncode + 1), snx(P.ncode + 1);
-      const BoundScratch ws{colour.data(), acc.data(), bar.data(), spc.data(), snx.data()};
+      std::vector<uint32_t> acc(P.ncode + 1), bar(P.ncode + 1), spc(P.ncode + 1), snx(P.ncode + 1), gacc(P.ncode + 1);
+      const BoundScratch ws{colour.data(), acc.data(), bar.data(), spc.data(), snx.data(), gacc.data()};
       for (uint32_t k = 0; k < P.nkernels; ++k) kb[k] = bound_kernel(P.code, P.ncode, P.kernel_entry[k], ws);
     }
     const uint32_t first_launch = (uint32_t)b->launches.size();   // the program's launches are contiguous
+    // the global-memory race check of a program whose launches are not all ordered needs its
+    // launch-order matrix (and all its launches in one wave)
+    uint32_t ord_off = sr::kNoDep;
+    if (o.check_global && P.nlaunches > 1) {
+      std::vector<uint32_t> bits;
+      if (launch_order_bits(P.launches, P.nlaunches, bits)) {
+        ord_off = (uint32_t)b->ord_bits_h.size();
+        b->ord_bits_h.insert(b->ord_bits_h.end(), bits.begin(), bits.end());
+      }
+    }
     for (uint32_t l = 0; l < P.nlaunches; ++l) {
       const sr_launch& L = P.launches[l];
       LaunchDev d{};
@@ -380,6 +454,17 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
         return fail(c, SR_E_INVAL, "program %u launch %u: access log bound too large", i, l);
       }
       d.log_cap = (uint32_t)cap;
+      if (o.check_global) {
+        const uint64_t gcap = launch_glog_cap(k, L.block_dim, o.loop_log_records);
+        if (gcap >= (1ull << 31)) {
+          delete b;
+          return fail(c, SR_E_INVAL, "program %u launch %u: global log bound too large", i, l);
+        }
+        d.glog_cap = (uint32_t)gcap;
+      }
+      d.first_launch = first_launch;
+      d.nl_prog = P.nlaunches;
+      d.ord_off = ord_off;
       d.arena_off = b->arena_off[i];
       d.arena_words = P.global_words;
       d.ir_bytes = sr::ir_smem_bytes(P.ncode);
@@ -387,7 +472,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       const uint32_t nw = (L.block_dim + 31) / 32;
       d.uninit = o.check_uninit ? 1u : 0u;
       // the fused race check where its summaries fit beside the block, else the access log
-      d.fused = (o.fused_check && o.check_races && L.shmem_words) ? 1u : 0u;
+      d.fused = (o.fused_check && o.check_races && !o.check_global && L.shmem_words) ? 1u : 0u;
       d.group_bytes = sr::group_layout(nw * 32, L.shmem_words, P.ncode, rm.nrows, d.uninit, d.fused).total;
       if (d.fused && d.ir_bytes + d.group_bytes > smem_budget) {
         d.fused = 0;
@@ -430,28 +515,48 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   const uint64_t budget_records =
       std::max<uint64_t>(1, (o.log_budget_mb ? (uint64_t)o.log_budget_mb << 20
                                              : std::min<uint64_t>(96ull << 30, (uint64_t)free_b / 2)) / 8);
-  uint64_t wave_max = 0;
+  // (8-byte units per launch: its access logs, and with the global check its global logs,
+  // 16 B per record, held three times: the per-block regions and the two sort buffers)
+  uint64_t wave_max = 0, gwave_max = 0;
   {
-    Wave cur{0, 0, 0, 0, 0, 0, 0};
+    auto need_of = [&](const LaunchDev& d) {
+      return (uint64_t)d.grid * d.log_cap + 6ull * d.grid * d.glog_cap;
+    };
+    Wave cur{0, 0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t used = 0;
     for (uint32_t li = 0; li < b->launches.size(); ++li) {
       LaunchDev& d = b->launches[li];
-      const uint64_t need = (uint64_t)d.grid * d.log_cap;
-      if (cur.li1 > cur.li0 && cur.log_records + need > budget_records) {
+      uint64_t need = need_of(d);
+      // a program with unordered launches (global check) starts a wave only as a whole
+      if (d.ord_off != sr::kNoDep && d.launch == 0)
+        for (uint32_t m = li + 1; m < li + d.nl_prog; ++m) need += need_of(b->launches[m]);
+      const bool split_ok = d.ord_off == sr::kNoDep || d.launch == 0;
+      if (cur.li1 > cur.li0 && split_ok && used + need > budget_records) {
         b->waves.push_back(cur);
         wave_max = std::max(wave_max, cur.log_records);
-        cur = Wave{li, li, d.block_base, d.block_base, 0, 0, 0};
+        gwave_max = std::max(gwave_max, cur.glog_records);
+        cur = Wave{li, li, d.block_base, d.block_base, 0, 0, 0, 0, 0};
+        used = 0;
       }
       d.log_base = cur.log_records;
-      cur.log_records += need;
+      d.glog_base = cur.glog_records;
+      cur.log_records += (uint64_t)d.grid * d.log_cap;
+      cur.glog_records += (uint64_t)d.grid * d.glog_cap;
+      used += need_of(d);
+      if (d.glog_cap) cur.addr_bits = std::max(cur.addr_bits, key_bits_for((uint32_t)std::min<uint64_t>(
+                                                                 std::max<uint64_t>(1, d.arena_words), 1u << 31)));
       cur.li1 = li + 1;
       cur.gb1 = d.block_base + d.grid;
     }
     if (cur.li1 > cur.li0) {
       b->waves.push_back(cur);
       wave_max = std::max(wave_max, cur.log_records);
+      gwave_max = std::max(gwave_max, cur.glog_records);
     }
   }
   b->log_records = wave_max;
+  b->glog_records = gwave_max;
+  b->entry_cap = std::max<uint64_t>(1024, std::min<uint64_t>(gwave_max, o.report_cap ? o.report_cap : 1u << 20));
 
   // ---- batched work items: per wave, launch-index order, blocks in chunks of `groups`
   b->batched_smem = 0;
@@ -496,6 +601,25 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       {&b->out, b->out_cap * sizeof(sr_report), "reports"},
       {&b->total, 8, "report total"},
       {&b->item_launch_d, std::max<size_t>(1, b->item_launch.size()) * 4, "check item table"},
+      // global-memory race check (16-byte stand-ins when off)
+      {&b->glog, (size_t)b->glog_records * 16, "global logs"},
+      {&b->glog_n, o.check_global ? (size_t)b->nblocks * 4 : 0, "global log counts"},
+      {&b->goff, o.check_global ? ((size_t)b->nblocks + 1) * 8 : 0, "global log offsets"},
+      {&b->gpartials, o.check_global ? sr::gcheck_partials(b->nblocks) * 8 : 0, "global scan partials"},
+      {&b->gtotal, 8, "global record total"},
+      {&b->sort_a, (size_t)b->glog_records * 16, "global sort buffer"},
+      {&b->sort_b, (size_t)b->glog_records * 16, "global sort buffer"},
+      {&b->hist, o.check_global ? (size_t)12 * 256 * 8 : 0, "digit histograms"},
+      {&b->status, o.check_global ? sr::gcheck_tiles(std::max(b->glog_records, b->entry_cap)) * 256 * 8 : 0,
+       "sort tile states"},
+      {&b->tile_ctr, 12 * 4, "sort tile counters"},
+      {&b->ord_bits, std::max<size_t>(1, b->ord_bits_h.size()) * 4, "launch-order matrices"},
+      {&b->entries_a, o.check_global ? (size_t)b->entry_cap * 32 : 0, "global race entries"},
+      {&b->entries_b, o.check_global ? (size_t)b->entry_cap * 32 : 0, "global race entries"},
+      {&b->gn, (size_t)nwaves * 8, "global entry counts"},
+      {&b->gcount, o.check_global ? (size_t)b->nblocks * 4 : 0, "global entries per block"},
+      {&b->gstart, o.check_global ? ((size_t)b->nblocks + 1) * 8 : 0, "global entry offsets"},
+      {&b->gn_sorted, 8, "global entry total"},
   };
   for (auto& a : allocs) {
     rc = alloc_buf(c, *a.buf, a.bytes, s, a.what);
@@ -512,6 +636,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   if (e == cudaSuccess) e = up(b->launches_d, b->launches.data(), nl * sizeof(LaunchDev));
   if (e == cudaSuccess) e = up(b->items_d, b->items.data(), b->items.size() * 8);
   if (e == cudaSuccess) e = up(b->item_launch_d, b->item_launch.data(), b->item_launch.size() * 4);
+  if (e == cudaSuccess) e = up(b->ord_bits, b->ord_bits_h.data(), b->ord_bits_h.size() * 4);
   // every arena starts on a 16-byte boundary; the up to three padding words after it are
   // zeroed by copies too, not by a memset: a memset is a kernel, which would wait for SMs that
   // other batches' kernels hold, and the synchronisation below would wait with it
@@ -569,6 +694,32 @@ int fetch_reports(sr_ctx* c, sr_batch* b, sr_report* dst, uint64_t cap, uint64_t
   if (!c || !b) return fail(c, SR_E_INVAL, "null argument");
   if (!b->ran) return fail(c, SR_E_INVAL, "run_and_check has not been called");
   cudaStream_t s = b->stream;
+  if (c->opts.check_global) {
+    // a wave's global race entries outgrew their buffer: grow it and run again (runs are
+    // deterministic; the entries of every wave then fit)
+    std::vector<unsigned long long> gn(b->waves.size());
+    CUDA_TRY(c, cudaMemcpyAsync(gn.data(), b->gn.p, gn.size() * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    const unsigned long long need = gn.empty() ? 0 : *std::max_element(gn.begin(), gn.end());
+    if (need > b->entry_cap) {
+      dev_free(c, b->entries_a, s);
+      dev_free(c, b->entries_b, s);
+      dev_free(c, b->status, s);
+      b->entry_cap = need + need / 8 + 1024;
+      int rc = alloc_buf(c, b->entries_a, b->entry_cap * 32, s, "global race entries");
+      if (!rc) rc = alloc_buf(c, b->entries_b, b->entry_cap * 32, s, "global race entries");
+      if (!rc)
+        rc = alloc_buf(c, b->status, sr::gcheck_tiles(std::max(b->glog_records, b->entry_cap)) * 256 * 8, s,
+                       "sort tile states");
+      if (rc) return rc;
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+      rc = run_and_check(c, b, s);
+      if (rc) return rc;
+    }
+  }
   unsigned long long total = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&total, b->total.p, 8, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -644,18 +795,22 @@ int sr_batch_stats(sr_ctx* c, sr_batch* b, sr_stats* out) {
   out->reports = k.total_reports;
   out->log_bytes = b->log_records * 8;
   out->blocks = b->nblocks;
+  out->waves = (uint32_t)b->waves.size();
+  out->kernels = b->kernels;
+  out->global_records = k.global_records;
   if (c->opts.profile && b->nevents_used >= 2) {
     float ms = 0;
     cudaEventElapsedTime(&ms, b->events[0], b->events[1]);
     out->ms_reset = ms;
-    // per wave: interp, check, compact marks follow
-    for (uint32_t i = 1; i + 3 < b->nevents_used; i += 3) {   // per wave: interp, check, compact
+    for (uint32_t i = 1; i + 4 < b->nevents_used; i += 4) {   // per wave: interp, check, global, compact
       float t;
       cudaEventElapsedTime(&t, b->events[i], b->events[i + 1]);
       out->ms_interp += t;
       cudaEventElapsedTime(&t, b->events[i + 1], b->events[i + 2]);
       out->ms_check += t;
       cudaEventElapsedTime(&t, b->events[i + 2], b->events[i + 3]);
+      out->ms_global += t;
+      cudaEventElapsedTime(&t, b->events[i + 3], b->events[i + 4]);
       out->ms_compact += t;
     }
   }

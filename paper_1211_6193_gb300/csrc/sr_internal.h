@@ -56,6 +56,11 @@ struct LaunchDev {
   // the launches (batch indices) this one follows: the previous launch of its stream and the
   // one it waits for (kNoDep: none), and its own batch index
   uint32_t dep_prev, dep_wait, index;
+  // global-memory race check: global-log records per block (0 = off), the record offset of
+  // block 0's region; the program's first launch (batch index) and launch count, and the word
+  // offset of its launch-order bit matrix (kNoDep: every pair of its launches is ordered)
+  uint32_t glog_cap, first_launch, nl_prog, ord_off;
+  uint64_t glog_base;
 };
 constexpr uint32_t kNoDep = 0xFFFFFFFFu;
 
@@ -64,6 +69,7 @@ struct BlockRes { uint32_t n_log, n_race, n_misc, flags; };
 
 struct Counters {
   unsigned long long thread_instrs, global_accesses, total_reports, shared_accesses;
+  unsigned long long global_records;   // global-log records (global-memory race check)
 };
 
 struct RunArgs {
@@ -82,6 +88,9 @@ struct RunArgs {
   uint32_t nitems;
   uint32_t* queue_head;
   uint32_t* launch_done;        // completed blocks per launch
+  // global-memory race check: per-block global-log regions and per-block record counts
+  uint4* glog;
+  uint32_t* glog_n;
 };
 
 // Shared-memory footprint of one simulated block in the interpreter.
@@ -136,8 +145,17 @@ cudaError_t init_interp_attributes(uint32_t smem_optin);
 cudaError_t init_check_attributes(uint32_t smem_optin);
 cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& L, uint32_t variant, cudaStream_t s);
 // fused: run the instantiation with the fused race check (launches whose `fused` is 0 still
-// log their accesses in it)
-cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, cudaStream_t s);
+// log their accesses in it); global: the instantiation that logs global accesses (launches
+// whose glog_cap is 0 log none in it; it has no fused race check)
+cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, bool global,
+                                  cudaStream_t s);
+
+// Global-log record (16 bytes): x = word address in the program's arena, y = epoch (barrier
+// interval of the block), z = tid << 16 | kind << 12 | pc (kind 1 = store, 0 = load),
+// w = global block index in the batch.  A block's records are in epoch order.
+__host__ __device__ inline uint32_t grec_tid(const uint4& r) { return r.z >> 16; }
+__host__ __device__ inline uint32_t grec_write(const uint4& r) { return (r.z >> 12) & 1u; }
+__host__ __device__ inline uint32_t grec_pc(const uint4& r) { return r.z & 0xFFFu; }
 uint32_t interp_plain_smem(const LaunchDev& L);
 
 struct CheckArgs {
@@ -185,6 +203,39 @@ __host__ __device__ inline uint32_t check_group_for(uint32_t log_cap) {
   return g < 1 ? 1 : (g > kCheckMaxGroup ? kCheckMaxGroup : g);
 }
 
+// Global-memory race check of one wave (gcheck.cu).  Device buffers, all owned by the batch.
+struct GcheckArgs {
+  const LaunchDev* launches;
+  uint32_t li0, li1, gb0, gb1;      // the wave's launches and global blocks
+  const uint4* glog;                // per-block regions (LaunchDev::glog_base, glog_cap)
+  const uint32_t* glog_n;           // records per global block
+  unsigned long long* goff;         // per block of the wave: first record in sort_a
+  unsigned long long* gtotal;       // records of the wave
+  unsigned long long* partials;     // scan scratch (gcheck_partials)
+  uint4* sort_a;                    // rec_cap records each
+  uint4* sort_b;
+  unsigned long long rec_cap;       // >= the wave's records
+  uint32_t addr_passes;             // 8-bit digits of the largest word address of the wave
+  unsigned long long* hist;         // 12 x 256 digit counts
+  unsigned long long* status;       // gcheck_tiles(max(rec_cap, entry_cap)) x 256 tile states
+  uint32_t* tile_ctr;               // 12 tile counters
+  uint32_t* err;                    // set when a bounded wait gave up
+  uint32_t spin_limit;
+  uint32_t sms;
+  const uint32_t* ord_bits;         // launch-order matrices of programs with unordered launches
+  uint4* entries_a;                 // report entries, 32 bytes each (entry_cap)
+  uint4* entries_b;
+  unsigned long long entry_cap;
+  unsigned long long* gn;           // entries produced in this wave (may exceed entry_cap)
+  uint32_t* gcount;                 // per global block: its entries
+  unsigned long long* gstart;       // per block of the wave: its first entry in entries_a
+  unsigned long long* gn_sorted;    // scratch total
+};
+cudaError_t init_gcheck_attributes(uint32_t smem_optin);
+cudaError_t launch_gcheck(const GcheckArgs& g, uint32_t& kernels, cudaStream_t s);
+uint64_t gcheck_tiles(uint64_t records);
+uint64_t gcheck_partials(uint32_t nblocks);
+
 struct CompactArgs {
   const LaunchDev* launches;
   uint32_t nlaunches;
@@ -197,9 +248,16 @@ struct CompactArgs {
   sr_report* out;
   unsigned long long out_cap;
   Counters* counters;
+  // global-memory race check (NULL when off): per global block its entries, per block of
+  // the wave its first entry, and the entries in (block, epoch, kind, word) order
+  const uint32_t* gcount;
+  const unsigned long long* gstart;
+  const uint4* gentries;
+  unsigned long long gcap;      // entries the buffer holds (a wave that produced more is run again)
 };
 cudaError_t launch_compact_scan(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_compact_emit(const CompactArgs& a, cudaStream_t s);
 uint64_t compact_partials_count(uint32_t nblocks);
+uint32_t compact_kernels(const CompactArgs& a);   // kernel launches of launch_compact_scan + _emit
 
 }  // namespace sr

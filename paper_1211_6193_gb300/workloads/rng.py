@@ -44,19 +44,52 @@ class SplitMix64:
         return seq[self.randint(0, len(seq) - 1)]
 
 
+_CHUNK = 1 << 16
+
+
+def _outputs(seed: int, n: int, offset: int, finish, dtype) -> np.ndarray:
+    """Outputs offset..offset+n-1, chunk by chunk (in place, cache-sized), each chunk passed
+    through ``finish(z_uint64, out_chunk)``."""
+    out = np.empty(n, dtype=dtype)
+    z = np.empty(min(max(n, 1), _CHUNK), dtype=np.uint64)
+    t = np.empty_like(z)
+    g, m1, m2 = np.uint64(GAMMA), np.uint64(M1), np.uint64(M2)
+    base = np.uint64(seed & MASK64)
+    with np.errstate(over="ignore"):
+        for c0 in range(0, n, _CHUNK):
+            c1 = min(n, c0 + _CHUNK)
+            zc, tc = z[: c1 - c0], t[: c1 - c0]
+            zc[:] = np.arange(offset + c0 + 1, offset + c1 + 1, dtype=np.uint64)
+            np.multiply(zc, g, out=zc)
+            np.add(zc, base, out=zc)                           # seed + (i + 1) * GAMMA
+            np.right_shift(zc, np.uint64(30), out=tc)
+            np.bitwise_xor(zc, tc, out=zc)
+            np.multiply(zc, m1, out=zc)
+            np.right_shift(zc, np.uint64(27), out=tc)
+            np.bitwise_xor(zc, tc, out=zc)
+            np.multiply(zc, m2, out=zc)
+            np.right_shift(zc, np.uint64(31), out=tc)
+            np.bitwise_xor(zc, tc, out=zc)
+            finish(zc, out[c0:c1])
+    return out
+
+
 def stream(seed: int, n: int, offset: int = 0) -> np.ndarray:
     """Outputs offset..offset+n-1 of the stream seeded with ``seed`` (uint64 array)."""
-    with np.errstate(over="ignore"):
-        idx = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
-        z = np.uint64(seed & MASK64) + idx * np.uint64(GAMMA)
-        z = (z ^ (z >> np.uint64(30))) * np.uint64(M1)
-        z = (z ^ (z >> np.uint64(27))) * np.uint64(M2)
-        return z ^ (z >> np.uint64(31))
+    def keep(z, o):
+        o[:] = z
+    return _outputs(seed, n, offset, keep, np.uint64)
 
 
 def uniform_mod(seed: int, n: int, modulus: int, offset: int = 0) -> np.ndarray:
     """int32 values ``(x >> 32) % modulus`` for the first n outputs."""
-    return ((stream(seed, n, offset) >> np.uint64(32)) % np.uint64(modulus)).astype(np.int32)
+    m = np.uint64(modulus)
+
+    def finish(z, o):
+        np.right_shift(z, np.uint64(32), out=z)
+        np.remainder(z, m, out=z)
+        o[:] = z
+    return _outputs(seed, n, offset, finish, np.int32)
 
 
 def uniform_range(seed: int, n: int, lo: int, hi: int, offset: int = 0) -> np.ndarray:
@@ -66,7 +99,10 @@ def uniform_range(seed: int, n: int, lo: int, hi: int, offset: int = 0) -> np.nd
 
 def uniform_i32(seed: int, n: int, offset: int = 0) -> np.ndarray:
     """Full-range int32 values (high 32 bits reinterpreted)."""
-    return (stream(seed, n, offset) >> np.uint64(32)).astype(np.uint32).view(np.int32)
+    def finish(z, o):
+        np.right_shift(z, np.uint64(32), out=z)
+        o.view(np.uint32)[:] = z
+    return _outputs(seed, n, offset, finish, np.int32)
 
 
 def derive(seed: int, index: int) -> int:

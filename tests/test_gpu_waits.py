@@ -55,11 +55,15 @@ def slow_then_dependent(iters: int = 100000) -> Program:
                    np.zeros(4, np.int32), name="slow_then_dependent")
 
 
+# warp 1 of the lopsided block logs 2 x 32 shared accesses per iteration: 128,000 records
+LOG = 1 << 18
+
+
 def test_programs_are_valid_and_race_free_without_a_limit(B):
     for p in (lopsided_block(), slow_then_dependent()):
         want = oracle.run([p])
         for mode in ("plain", "batched"):
-            got = B.check([p], mode=mode)
+            got = B.check([p], mode=mode, loop_log_records=LOG)
             assert got.report_tuples() == want.report_tuples() == [], (p.name, mode)
             assert np.array_equal(got.arenas[0], want.arenas[0]), (p.name, mode)
             assert int(got.status[0]) == 0, (p.name, mode)
@@ -69,11 +73,11 @@ def test_programs_are_valid_and_race_free_without_a_limit(B):
 def test_clock_wait_runs_out(B, mode):
     p = lopsided_block()
     for _ in range(2):                    # the context stays usable: run twice
-        got = B.check([p], mode=mode, spin_limit=1)
+        got = B.check([p], mode=mode, spin_limit=1, loop_log_records=LOG)
         assert int(got.status[0]) & B.ST_INTERNAL, got.status
     # and an ordinary run afterwards is exact
     want = oracle.run([p])
-    got = B.check([p], mode=mode)
+    got = B.check([p], mode=mode, loop_log_records=LOG)
     assert np.array_equal(got.arenas[0], want.arenas[0]) and int(got.status[0]) == 0
 
 
