@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving arrival rate (jobs/s)")
     ap.add_argument("--blocks", type=int, default=16384,
                     help="blocks of the reduction (default: the full workload; smaller only for profiling)")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: split the one batch across the ranks (strong scaling; programs "
+                         "assigned by reserved log bytes) instead of one copy per rank (weak scaling)")
     ap.add_argument("--programs", type=int, default=4096,
                     help="programs of the batched workload, the first N of the same seeded batch "
                          "(default: the full workload; smaller only for profiling)")
@@ -314,7 +317,13 @@ def run_native(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    progs = workload(args.workload, rank, args.blocks, args.programs)
+    shard = args.shard and world > 1 and args.workload == "batched"
+    if shard:
+        from paper_1211_6193_gb300 import dist as sdist
+        progs = workload(args.workload, 0, args.blocks, args.programs)
+        progs = [progs[i] for i in sdist.shard(progs, world)[rank]]
+    else:
+        progs = workload(args.workload, rank, args.blocks, args.programs)
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(pk)) if os.path.exists(pk) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -352,12 +361,16 @@ def run_native(args):
         t_wall = time.perf_counter() - t_wall
     clk = clocks.summary()
     dev_ms = sum(per_step)
+    all_acc, all_instr = st.shared_accesses, st.thread_instrs
     if world > 1:
         t = torch.tensor([dev_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         dev_ms = float(t.item())
-    value = world * st.shared_accesses * args.steps / (dev_ms / 1e3)
-    thread_instr_rate = world * st.thread_instrs * args.steps / (dev_ms / 1e3)
+        n = torch.tensor([float(all_acc), float(all_instr)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
+        all_acc, all_instr = int(n[0].item()), int(n[1].item())
+    value = all_acc * args.steps / (dev_ms / 1e3)              # whole job: every rank's accesses
+    thread_instr_rate = all_instr * args.steps / (dev_ms / 1e3)
 
     plain = None
     if args.workload == "batched":     # the same programs through one kernel launch per (program, launch)
@@ -433,7 +446,12 @@ def run_native(args):
             times.append(time.perf_counter() - t0)
     ctx_e2e.close()
     del pin, progs_pinned
-    e2e = {"value": world * st.shared_accesses / statistics.mean(times), "unit": UNIT,
+    t_e2e = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": all_acc / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
@@ -445,11 +463,13 @@ def run_native(args):
                "thread_instrs_per_s": irate}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": workload_label(args), "mode": mode, "shapes": opts, "tuning": tuning,
                        "blocks": nblocks,
-                       "programs": len(progs), "parallelism": f"{world} independent replicas" if world > 1
-                       else "single GPU", "l2": "flushed between timed steps (256 MB write); logs exceed L2"},
+                       "programs": len(progs),
+                       "parallelism": (f"{world} ranks, one batch sharded by reserved log bytes" if shard else
+                                       f"{world} independent replicas") if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MB write); logs exceed L2"},
             "sim_thread_instrs_per_s": thread_instr_rate, "shared_accesses_per_step": st.shared_accesses,
             "reports_per_step": n_reports, "wall_s": t_wall, "e2e": e2e, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk,

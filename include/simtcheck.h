@@ -142,6 +142,12 @@ typedef struct {
    * global word that one of them writes (the result would depend on timing; not checked). */
   uint32_t stream;
   uint32_t wait;             /* 0..index of this launch; SR_E_INVAL otherwise */
+  /* Run only blocks [block_begin, block_begin + block_count) of the grid (a process's share
+   * of a launch whose blocks are split across processes, Sec. 2: the blocks of a grid are
+   * independent until the kernel call ends).  Block indices (S2R BID, reports) and GDIM keep
+   * the whole grid's numbering.  block_count 0 = every block (block_begin must be 0). */
+  uint32_t block_begin;
+  uint32_t block_count;
 } sr_launch;
 
 typedef struct {

@@ -40,7 +40,8 @@ class _Instr(C.Structure):
 class _Launch(C.Structure):
     _fields_ = [("kernel", C.c_uint32), ("grid", C.c_uint32), ("block_dim", C.c_uint32),
                 ("shmem_words", C.c_uint32), ("nparams", C.c_uint32), ("params", C.c_int32 * 4),
-                ("stream", C.c_uint32), ("wait", C.c_uint32)]
+                ("stream", C.c_uint32), ("wait", C.c_uint32), ("block_begin", C.c_uint32),
+                ("block_count", C.c_uint32)]
 
 
 class _Program(C.Structure):
@@ -125,6 +126,7 @@ def run(programs: Sequence, round_budget: int = 0, check_races: bool = True, sch
             for k, v in enumerate(l.params):
                 ls[j].params[k] = int(v)
             ls[j].stream, ls[j].wait = getattr(l, "stream", 0), getattr(l, "wait", -1) + 1
+            ls[j].block_begin, ls[j].block_count = getattr(l, "block_begin", 0), getattr(l, "block_count", 0)
         arena = np.array(p.global_init, dtype=np.int32, copy=True)
         arenas.append(arena)
         keep += [code, entries, ls]

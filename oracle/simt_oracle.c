@@ -502,6 +502,8 @@ static int validate(const orc_program* P, uint32_t idx) {
     if (L->wait > l) {
       snprintf(g_err, sizeof g_err, "program %u launch %u: waits for a launch that is not earlier", idx, l);
       return -1; }
+    if ((L->block_count == 0 && L->block_begin != 0) || (uint64_t)L->block_begin + L->block_count > L->grid) {
+      snprintf(g_err, sizeof g_err, "program %u launch %u: block range outside the grid", idx, l); return -1; }
   }
   if (P->arena_words > 0x7FFFFFFFull || (P->arena_words && !P->arena)) {
     snprintf(g_err, sizeof g_err, "program %u: bad arena", idx); return -1; }
@@ -673,7 +675,9 @@ int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc
         dead[l] = 1;                                            /* skipped */
         continue;
       }
-      uint32_t nblocks = L->grid;
+      /* the blocks run: [b_first, b_first + nblocks) of the grid */
+      uint32_t b_first = L->block_count ? L->block_begin : 0;
+      uint32_t nblocks = L->block_count ? L->block_count : L->grid;
       if (O.max_blocks && O.max_blocks < nblocks) nblocks = O.max_blocks;
       if (writer) {
         memset(writer, 0xFF, P->arena_words * sizeof(int32_t));
@@ -690,14 +694,14 @@ int orc_run(const orc_program* progs, uint32_t nprogs, const orc_opts* opts, orc
       }
       if (acc) ctx[0].acc = acc[l] = calloc(P->arena_words, 1);
       if (nw == 1) {
-        for (uint32_t b = 0; b < nblocks; ++b) run_block(&ctx[0], b);
+        for (uint32_t b = 0; b < nblocks; ++b) run_block(&ctx[0], b_first + b);
       } else {
         pthread_t* th = malloc(nw * sizeof(pthread_t));
         worker_arg* wa = malloc(nw * sizeof(worker_arg));
         for (uint32_t i = 0; i < nw; ++i) {
           wa[i].C = &ctx[i];
-          wa[i].b0 = (uint32_t)((uint64_t)nblocks * i / nw);
-          wa[i].b1 = (uint32_t)((uint64_t)nblocks * (i + 1) / nw);
+          wa[i].b0 = b_first + (uint32_t)((uint64_t)nblocks * i / nw);
+          wa[i].b1 = b_first + (uint32_t)((uint64_t)nblocks * (i + 1) / nw);
           pthread_create(&th[i], NULL, worker, &wa[i]);
         }
         for (uint32_t i = 0; i < nw; ++i) pthread_join(th[i], NULL);

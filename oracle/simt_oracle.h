@@ -86,6 +86,9 @@ typedef struct {
   uint32_t kernel, grid, block_dim, shmem_words, nparams;
   int32_t params[4];
   uint32_t stream, wait;
+  /* run only blocks [block_begin, block_begin + block_count) of the grid, numbered as in the
+     whole grid (count 0 = every block); Sec. 2: blocks of a grid are independent */
+  uint32_t block_begin, block_count;
 } orc_launch;
 typedef struct {
   const orc_instr* code; uint32_t ncode;

@@ -43,7 +43,8 @@ class sr_instr(C.Structure):
 class sr_launch(C.Structure):
     _fields_ = [("kernel", C.c_uint32), ("grid", C.c_uint32), ("block_dim", C.c_uint32),
                 ("shmem_words", C.c_uint32), ("nparams", C.c_uint32), ("params", C.c_int32 * 4),
-                ("stream", C.c_uint32), ("wait", C.c_uint32)]
+                ("stream", C.c_uint32), ("wait", C.c_uint32), ("block_begin", C.c_uint32),
+                ("block_count", C.c_uint32)]
 
 
 class sr_program(C.Structure):
@@ -136,6 +137,7 @@ class _Marshalled:
                 for k, v in enumerate(l.params):
                     ls[j].params[k] = int(v)
                 ls[j].stream, ls[j].wait = l.stream, l.wait + 1
+                ls[j].block_begin, ls[j].block_count = l.block_begin, l.block_count
             arena = np.ascontiguousarray(p.global_init, dtype=np.int32)
             self.keep += [code, entries, ls, arena]
             a = self.array[i]

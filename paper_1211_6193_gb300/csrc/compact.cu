@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(256) k_emit(CompactArgs A) {
       if (A.launches[mid].block_base <= gb) lo = mid; else hi = mid - 1;
     }
     const LaunchDev* L = A.launches + lo;
-    const uint32_t block = gb - L->block_base;
-    const uint4* reg4 = reinterpret_cast<const uint4*>(A.log + L->log_base + (unsigned long long)block * L->log_cap);
+    const uint32_t lb = gb - L->block_base;            // the block's place in this batch's share
+    const uint32_t block = lb + L->block_off;          // its index in the grid (reports)
+    const uint4* reg4 = reinterpret_cast<const uint4*>(A.log + L->log_base + (unsigned long long)lb * L->log_cap);
     const uint32_t top = L->log_cap / 2 - 1;        // misc entry j lives at reg4[top - j]
     const uint4* ge = ng ? A.gentries + 2 * A.gstart[gb - A.gb0] : nullptr;   // the block's global list
     const unsigned long long base = A.offsets[gb];

@@ -512,7 +512,9 @@ __global__ void __launch_bounds__(256) k_grun(GrunArgs A) {
         const LaunchDev& L = A.launches[lcur];
         uint32_t p1, p2;
         const uint32_t cls = pair_classes(lW, lR, kInf, p1, p2);
-        if (cls) emit_entry(A, L.block_base + p1, 1u, word, p2, cls << 24 | (lpl & 0xFFFu) << 12 | (lph & 0xFFFu));
+        if (cls)
+          emit_entry(A, L.block_base + p1, 1u, word, p2 + L.block_off,
+                     cls << 24 | (lpl & 0xFFFu) << 12 | (lph & 0xFFFu));
         if (pairs) {
           // this launch against every earlier launch of the run that nothing orders before it
           const uint32_t l = L.launch;

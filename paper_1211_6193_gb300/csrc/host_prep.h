@@ -149,6 +149,8 @@ inline int validate(const sr_program* p, char* msg, size_t len) {
     if (L.shmem_words > SR_MAX_SHMEM_WORDS) return bad("launch %u: shmem_words %u", l, L.shmem_words);
     if (L.nparams > 4) return bad("launch %u: nparams %u", l, L.nparams);
     if (L.wait > l) return bad("launch %u: waits for launch %u, which is not an earlier one", l, L.wait - 1);
+    if ((L.block_count == 0 && L.block_begin != 0) || (uint64_t)L.block_begin + L.block_count > L.grid)
+      return bad("launch %u: block range starting at %u outside the grid", l, L.block_begin);
   }
   if (p->global_words >= (1ull << 31)) return bad("global arena too large (%u)", (uint32_t)(p->global_words >> 20), 0);
   if (p->global_words && !p->global_init) return bad("global_init missing (%u words)", (uint32_t)p->global_words, 0);

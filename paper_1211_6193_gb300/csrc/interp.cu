@@ -517,9 +517,9 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
         switch (op) {
           case SR_OP_S2R: {
             const uint32_t v = imm == SR_SREG_TID    ? tid
-                               : imm == SR_SREG_BID  ? block
+                               : imm == SR_SREG_BID  ? block + Ls->block_off
                                : imm == SR_SREG_BDIM ? bdim
-                               : imm == SR_SREG_GDIM ? Ls->grid
+                               : imm == SR_SREG_GDIM ? Ls->gdim
                                                      : 32u;
             if (wr) myregs[d * nthr] = v;
             break;

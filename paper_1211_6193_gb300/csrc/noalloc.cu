@@ -118,7 +118,9 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     d.entry = prog->kernel_entry[pl.kernel];
     d.ncode = ncode;
     d.code_off = 0;
-    d.grid = pl.grid;
+    d.grid = pl.block_count ? pl.block_count : pl.grid;
+    d.gdim = pl.grid;
+    d.block_off = pl.block_begin;
     d.bdim = pl.block_dim;
     d.shw = pl.shmem_words;
     d.nparams = pl.nparams;
@@ -137,9 +139,9 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     d.groups = 1;
     d.check_group = sr::check_group_for(d.log_cap);
     d.check_item = (uint32_t)check_items;
-    check_items += (pl.grid + d.check_group - 1) / d.check_group;
+    check_items += (d.grid + d.check_group - 1) / d.check_group;
     if (d.ir_bytes + d.group_bytes + 1024 > (uint32_t)optin) return SR_E_RANGE;
-    nblocks += pl.grid;
+    nblocks += d.grid;
     L[l] = d;
   }
   const uint32_t nl = prog->nlaunches;

@@ -440,7 +440,9 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       d.entry = P.kernel_entry[L.kernel];
       d.ncode = P.ncode;
       d.code_off = code_off[i];
-      d.grid = L.grid;
+      d.grid = L.block_count ? L.block_count : L.grid;     // the blocks this batch runs
+      d.gdim = L.grid;
+      d.block_off = L.block_begin;
       d.bdim = L.block_dim;
       d.shw = L.shmem_words;
       d.nparams = L.nparams;
@@ -485,12 +487,12 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       }
       uint32_t g = std::min<uint32_t>(32 / nw, (smem_budget - d.ir_bytes) / d.group_bytes);
       if (nw >= 2) g = std::min<uint32_t>(g, 15);
-      d.groups = std::max<uint32_t>(1, std::min<uint32_t>(g, L.grid));
+      d.groups = std::max<uint32_t>(1, std::min<uint32_t>(g, d.grid));
       d.check_group = sr::check_group_for(d.log_cap);
       d.check_item = (uint32_t)check_items;
-      check_items += (L.grid + d.check_group - 1) / d.check_group;
+      check_items += (d.grid + d.check_group - 1) / d.check_group;
       b->max_key_bits = std::max(b->max_key_bits, d.key_bits);
-      nblocks += L.grid;
+      nblocks += d.grid;
       if (nblocks >= (1ull << 31) || check_items >= (1ull << 31)) {
         delete b;
         return fail(c, SR_E_INVAL, "too many simulated blocks in one batch");

@@ -61,6 +61,9 @@ struct LaunchDev {
   // offset of its launch-order bit matrix (kNoDep: every pair of its launches is ordered)
   uint32_t glog_cap, first_launch, nl_prog, ord_off;
   uint64_t glog_base;
+  // the blocks run are [block_off, block_off + grid) of a grid of gdim blocks (S2R BID and
+  // reports add block_off; S2R GDIM reads gdim)
+  uint32_t block_off, gdim;
 };
 constexpr uint32_t kNoDep = 0xFFFFFFFFu;
 

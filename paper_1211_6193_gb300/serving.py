@@ -86,7 +86,7 @@ def predicted_log_bytes(p: Program, loop_records: int = 65536) -> int:
         else:
             recs, misc = acc * l.block_dim, (bars + 1) * (1 + errs) + 1
         cap = (recs + 2 * misc + 1) & ~1
-        total += l.grid * cap * 8
+        total += (l.block_count or l.grid) * cap * 8
     return total
 
 

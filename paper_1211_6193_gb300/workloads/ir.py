@@ -252,6 +252,11 @@ class Launch:
     params: Tuple[int, ...] = ()
     stream: int = 0
     wait: int = -1
+    # run only blocks [block_begin, block_begin + block_count) of the grid (a process's share
+    # of a launch split across processes); 0 = every block.  Block indices keep the grid's
+    # numbering.
+    block_begin: int = 0
+    block_count: int = 0
 
 
 @dataclass

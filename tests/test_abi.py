@@ -48,21 +48,26 @@ def test_binding_names_match_header():
 
 
 def test_struct_layouts_match_header(tmp_path):
-    # 8-byte instruction, 32-byte report, launch = 11 words
+    # 8-byte instruction, 32-byte report, launch = 13 words
     assert ctypes.sizeof(binding.sr_instr) == 8
-    assert ctypes.sizeof(binding.sr_launch) == 44
+    assert ctypes.sizeof(binding.sr_launch) == 52
     assert binding.REPORT_DTYPE.itemsize == 32
     assert ir.INSTR_DTYPE.itemsize == 8
     # the C compiler's layout of the header's sr_launch equals the binding's
     src = tmp_path / "layout.c"
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "simtcheck.h"\n'
-                   'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(sr_launch), offsetof(sr_launch, params),'
-                   ' offsetof(sr_launch, stream), offsetof(sr_launch, wait)); return 0; }\n')
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sr_launch),'
+                   ' offsetof(sr_launch, params), offsetof(sr_launch, stream), offsetof(sr_launch, wait),'
+                   ' offsetof(sr_launch, block_count), sizeof(sr_opts), offsetof(sr_opts, check_global),'
+                   ' sizeof(sr_stats), offsetof(sr_stats, ms_global), offsetof(sr_stats, global_records));'
+                   ' return 0; }\n')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(binding.sr_launch), binding.sr_launch.params.offset, binding.sr_launch.stream.offset,
-            binding.sr_launch.wait.offset]
+            binding.sr_launch.wait.offset, binding.sr_launch.block_count.offset, ctypes.sizeof(binding.sr_opts),
+            binding.sr_opts.check_global.offset, ctypes.sizeof(binding.sr_stats), binding.sr_stats.ms_global.offset,
+            binding.sr_stats.global_records.offset]
     assert got == want
 
 

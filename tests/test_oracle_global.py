@@ -252,3 +252,25 @@ def test_global_check_adds_nothing_to_the_paper_and_generated_workloads():
     b = oracle.run(progs)
     assert a.report_tuples() == b.report_tuples()
     assert all(np.array_equal(x, y) for x, y in zip(a.arenas, b.arenas))
+
+
+# ------------------------------------------------------------------ block ranges
+def test_a_block_range_runs_those_blocks_of_the_grid():
+    """A launch restricted to blocks [b0, b1) of its grid (a process's share) runs exactly those
+    blocks with their grid numbering: their reports and the words they write equal the whole
+    grid's, restricted to them."""
+    from dataclasses import replace
+    p = families.reduction_plain(n_blocks=9, bdim=128, seed=1, omit_level=2)
+    full = oracle.run([p])
+    for b0, b1 in ((0, 3), (3, 9), (4, 5)):
+        q = Program(p.code, p.kernel_entry, [replace(p.launches[0], block_begin=b0, block_count=b1 - b0)],
+                    p.global_init)
+        part = oracle.run([q])
+        assert part.report_tuples() == [t for t in full.report_tuples() if b0 <= t[3] < b1]
+        out = p.meta["n"]                    # block b writes its sum to word n + b
+        got = part.arenas[0]
+        assert np.array_equal(got[out + b0:out + b1], full.arenas[0][out + b0:out + b1])
+        assert not np.any(got[out:out + b0]) and not np.any(got[out + b1:out + 9])
+    with pytest.raises(ValueError):          # a range past the grid is rejected
+        oracle.run([Program(p.code, p.kernel_entry, [replace(p.launches[0], block_begin=8, block_count=2)],
+                            p.global_init)])
