@@ -870,8 +870,8 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
 // Items are ordered launch-wave by launch-wave, and an item waits (bounded) until every
 // block of the launches it follows (the previous launch of its stream, the one it waits
 // for) has completed; launches of other streams run meanwhile.
-template <bool Fused, bool Global>
-__global__ void __launch_bounds__(1024, 1) k_interp_batched(RunArgs A) {
+template <int MINB, bool Fused, bool Global>
+__global__ void __launch_bounds__(1024, MINB) k_interp_batched(RunArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LaunchDev Ls;
   __shared__ __align__(8) unsigned long long mbar;
@@ -957,9 +957,10 @@ cudaError_t init_interp_attributes(uint32_t smem_optin) {
   if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, true, false>, smem_optin);
   if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<1, false, true>, smem_optin);
   if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, false, true>, smem_optin);
-  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<false, false>, smem_optin);
-  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<true, false>, smem_optin);
-  return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched<false, true>, smem_optin) : e;
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<1, false, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<2, false, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<1, true, false>, smem_optin);
+  return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched<1, false, true>, smem_optin) : e;
 }
 
 // The plain-mode kernel for one launch: MINB (register budget) x fused race check x global log.
@@ -989,9 +990,13 @@ cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& 
   return cudaGetLastError();
 }
 
+// two_per_sm: registers capped so that two 1024-thread CTAs share an SM (the default kernel
+// without the fused check or the global log only)
 cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, bool global,
-                                  cudaStream_t s) {
-  auto k = global ? k_interp_batched<false, true> : fused ? k_interp_batched<true, false> : k_interp_batched<false, false>;
+                                  bool two_per_sm, cudaStream_t s) {
+  auto k = global ? k_interp_batched<1, false, true>
+           : fused ? k_interp_batched<1, true, false>
+           : two_per_sm ? k_interp_batched<2, false, false> : k_interp_batched<1, false, false>;
   k<<<ctas, 1024, smem, s>>>(a);
   return cudaGetLastError();
 }

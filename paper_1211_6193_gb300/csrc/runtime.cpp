@@ -260,7 +260,8 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
       const uint32_t ctas = std::min<uint32_t>(ra.nitems, (uint32_t)c->sms * std::max(1u, o.ctas_per_sm));
       if (ctas)
         CUDA_TRY(c, sr::launch_interp_batched(ra, ctas, b->batched_smem,
-                                              o.fused_check && o.check_races && !o.check_global, o.check_global != 0, s));
+                                              o.fused_check && o.check_races && !o.check_global, o.check_global != 0,
+                                              o.ctas_per_sm >= 2, s));
       b->kernels += ctas ? 1 : 0;
     } else {
       for (uint32_t li = w.li0; li < w.li1; ++li)

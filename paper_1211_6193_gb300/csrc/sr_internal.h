@@ -151,7 +151,7 @@ cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& 
 // log their accesses in it); global: the instantiation that logs global accesses (launches
 // whose glog_cap is 0 log none in it; it has no fused race check)
 cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, bool global,
-                                  cudaStream_t s);
+                                  bool two_per_sm, cudaStream_t s);
 
 // Global-log record (16 bytes): x = word address in the program's arena, y = epoch (barrier
 // interval of the block), z = tid << 16 | kind << 12 | pc (kind 1 = store, 0 = load),

@@ -460,3 +460,12 @@ def test_checker_interval_tags_wrap(B, variant):
     # iterations 300000, 299999, ... 1: the racy ones are those whose counter is a multiple of 1024
     assert len(got.reports) == 300000 // 1024
     assert all(r[0] == B.RACE and r[5] == 1 and r[6] == 1 for r in got.report_tuples())
+
+
+def test_batched_two_ctas_per_sm(B):
+    """The batched interpreter capped for two 1024-thread CTAs per SM (ctas_per_sm 2) gives the
+    same results."""
+    progs = families.batch(n_programs=48, seed=3, max_grid=6, bug_rate=0.5)
+    progs += [stencil2d.program(log2w=7, steps=4, buggy_launch=2, seed=4)]
+    assert_parity(B, progs, "batched", ctas_per_sm=2)
+    assert_parity(B, progs, "batched", ctas_per_sm=2, use_graph=True)
