@@ -104,6 +104,22 @@ __device__ __forceinline__ bool stage_wait(unsigned long long* bar, uint32_t pha
   return ok;
 }
 
+// Shared-memory accesses by 32-bit shared-window address (cheaper address arithmetic than
+// generic pointers in the interpreter's tight loops).
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint2 lds_u64(uint32_t a) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ void group_sync(uint32_t id, uint32_t nthr) {
   if (nthr == 32)
     __syncwarp();
@@ -496,6 +512,43 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const bool act = (st == ST_RUN) && (pc == p);
       const uint2 ins = ir[p];
       const uint32_t op = ins.x & 0x3Fu;
+      if (conv && op <= SR_OP_SNE && op != SR_OP_DIV && op != SR_OP_REM) {
+        // Converged warp on a run of plain ALU instructions (the bulk of straight-line code;
+        // DIV and REM can fail and take the general path): every runnable lane is at the
+        // run's pc, nothing else can happen, so the run executes in this tight loop, one
+        // instruction per round, publishing the clock every round as the general path does.
+        const bool runl = st == ST_RUN;
+        uint32_t q = p, kk = k;
+        uint2 in = ins;
+        uint32_t o = op;
+        const uint32_t rs = smem_u32(myregs), rstride = nthr * 4u, irs = smem_u32(ir);   // shared addresses
+        for (;;) {
+          const uint32_t dd = (in.x >> 8) & 0xFFu, xa = (in.x >> 16) & 0xFFu, xb = in.x >> 24;
+          const int32_t a = (int32_t)lds_u32(rs + xa * rstride);
+          const int32_t b = (in.x & SR_BIMM) ? (int32_t)in.y : (int32_t)lds_u32(rs + xb * rstride);
+          int32_t r;
+          // ADD and MUL (the common filler) by selection, the others through the ALU
+          const uint32_t s_add = (uint32_t)a + (uint32_t)b, s_mul = (uint32_t)a * (uint32_t)b;
+          r = (int32_t)(o == SR_OP_ADD ? s_add : s_mul);
+          if (o != SR_OP_ADD && o != SR_OP_MUL) {
+            bool dz = false;
+            r = alu(o, a, b, dz);
+          }
+          if (runl && dd != kNoDest) sts_u32(rs + dd * rstride, (uint32_t)r);
+          ++q;
+          ++kk;
+          if (lane == 0) st_release_cta(&clk[w], 4u * kk);
+          if (kk >= budget) break;
+          in = lds_u64(irs + q * 8u);                // (the EXIT sentinel ends every run)
+          o = in.x & 0x3Fu;
+          if (o > SR_OP_SNE || o == SR_OP_DIV || o == SR_OP_REM) break;
+        }
+        n_instr += runl ? kk - k : 0u;
+        if (runl) pc = q;
+        pn = q;
+        k = kk;
+        continue;
+      }
       const uint32_t d = (ins.x >> 8) & 0xFFu, ra = (ins.x >> 16) & 0xFFu, rb = ins.x >> 24;
       const int32_t imm = (int32_t)ins.y;
       const int32_t va = (int32_t)myregs[ra * nthr];
