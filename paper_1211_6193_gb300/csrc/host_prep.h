@@ -2,6 +2,7 @@
 // libsimtcheck: validation, register renaming, instruction packing and the static bound
 // of a kernel's per-block access log.  Internal; not part of the C ABI.
 #pragma once
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 #include <cuda_runtime.h>
@@ -191,7 +192,23 @@ inline uint2 pack(const sr_instr& in, const RegMap& m) {
   d = (op_writes_d(b) && d != SR_RZ) ? m.row[d] : sr::kNoDest;
   ra = (op_reads_a(b) && ra != SR_RZ) ? m.row[ra] : zrow;
   rb = (op_reads_b(op) && rb != SR_RZ) ? m.row[rb] : zrow;
-  return make_uint2(op | d << 8 | ra << 16 | rb << 24, (uint32_t)in.imm);
+  return make_uint2(sr::pk_make(b, (op & SR_BIMM) ? 1u : 0u, d, ra, rb, 0), (uint32_t)in.imm);
+}
+
+// The EXIT sentinel after a program's last instruction (running past the end exits).
+inline uint2 exit_sentinel(const RegMap& m) {
+  return make_uint2(sr::pk_make(SR_OP_EXIT, 0, sr::kNoDest, m.nrows - 1, m.nrows - 1, 0), 0);
+}
+
+// Fill in the run lengths of n packed instructions (straight-line successors only: a run
+// never contains a branch, so it is valid from any entry pc).
+inline void set_run_lengths(uint2* code, uint32_t n) {
+  uint32_t next = 0;
+  for (uint32_t pc = n; pc-- > 0;) {
+    const uint32_t run = sr::pk_plain_alu(sr::pk_op(code[pc].x)) ? std::min(sr::kRunMax, 1 + next) : 0u;
+    code[pc].x = (code[pc].x & ((1u << 22) - 1)) | run << 22;
+    next = run;
+  }
 }
 
 inline uint32_t key_bits_for(uint32_t shw) {

@@ -459,6 +459,8 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
   uint4* gregion = Global ? A.glog + Ls->glog_base + (unsigned long long)block * gcap : nullptr;
   const uint32_t budget = A.budget, spin = A.spin_limit;
   uint32_t* myregs = regs + tid;                 // row r of this thread: myregs[r * nthr]
+  // the same as 32-bit shared-window addresses, for the fast paths
+  const uint32_t rs = smem_u32(myregs), rstride = nthr * 4u, shs = smem_u32(sh), irs = smem_u32(ir);
 
   // ---- block start: registers = params then zeros (the last row stays zero), shared zeroed
   for (uint32_t r = 0; r < nrows; ++r) myregs[r * nthr] = (r < Ls->nparams) ? (uint32_t)Ls->params[r] : 0u;
@@ -512,47 +514,94 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const bool act = (st == ST_RUN) && (pc == p);
       const uint2 ins = ir[p];
       const uint32_t op = ins.x & 0x3Fu;
-      if (conv && op <= SR_OP_SNE && op != SR_OP_DIV && op != SR_OP_REM) {
-        // Converged warp on a run of plain ALU instructions (the bulk of straight-line code;
-        // DIV and REM can fail and take the general path): every runnable lane is at the
-        // run's pc, nothing else can happen, so the run executes in this tight loop, one
-        // instruction per round, publishing the clock every round as the general path does.
+      if (conv && pk_run(ins.x)) {
+        // Converged warp at a run of plain ALU instructions (the bulk of straight-line code):
+        // every runnable lane is at p and the run touches no memory, so its last round can be
+        // published at once (other warps wait on a clock only for memory effects), and the
+        // run executes in this tight loop, one instruction per round.
         const bool runl = st == ST_RUN;
-        uint32_t q = p, kk = k;
+        const uint32_t len = min(pk_run(ins.x), budget - k);      // (k < budget here)
+        if (lane == 0) st_release_cta(&clk[w], 4u * (k + len));
+        uint32_t q = p;
         uint2 in = ins;
-        uint32_t o = op;
-        const uint32_t rs = smem_u32(myregs), rstride = nthr * 4u, irs = smem_u32(ir);   // shared addresses
-        for (;;) {
-          const uint32_t dd = (in.x >> 8) & 0xFFu, xa = (in.x >> 16) & 0xFFu, xb = in.x >> 24;
-          const int32_t a = (int32_t)lds_u32(rs + xa * rstride);
-          const int32_t b = (in.x & SR_BIMM) ? (int32_t)in.y : (int32_t)lds_u32(rs + xb * rstride);
-          int32_t r;
+        for (uint32_t i = 0;;) {
+          const uint32_t o = pk_op(in.x), dd = pk_d(in.x);
+          const uint32_t a = lds_u32(rs + pk_a(in.x) * rstride);
+          const uint32_t b = pk_imm(in.x) ? in.y : lds_u32(rs + pk_b(in.x) * rstride);
           // ADD and MUL (the common filler) by selection, the others through the ALU
-          const uint32_t s_add = (uint32_t)a + (uint32_t)b, s_mul = (uint32_t)a * (uint32_t)b;
-          r = (int32_t)(o == SR_OP_ADD ? s_add : s_mul);
+          uint32_t r = o == SR_OP_ADD ? a + b : a * b;
           if (o != SR_OP_ADD && o != SR_OP_MUL) {
             bool dz = false;
-            r = alu(o, a, b, dz);
+            r = (uint32_t)alu(o, (int32_t)a, (int32_t)b, dz);
           }
-          if (runl && dd != kNoDest) sts_u32(rs + dd * rstride, (uint32_t)r);
+          if (runl && dd != kNoDest) sts_u32(rs + dd * rstride, r);
           ++q;
-          ++kk;
-          if (lane == 0) st_release_cta(&clk[w], 4u * kk);
-          if (kk >= budget) break;
-          in = lds_u64(irs + q * 8u);                // (the EXIT sentinel ends every run)
-          o = in.x & 0x3Fu;
-          if (o > SR_OP_SNE || o == SR_OP_DIV || o == SR_OP_REM) break;
+          if (++i == len) break;
+          in = lds_u64(irs + q * 8u);
         }
-        n_instr += runl ? kk - k : 0u;
+        n_instr += runl ? len : 0u;
         if (runl) pc = q;
         pn = q;
-        k = kk;
+        k += len;
         continue;
       }
-      const uint32_t d = (ins.x >> 8) & 0xFFu, ra = (ins.x >> 16) & 0xFFu, rb = ins.x >> 24;
+      const uint32_t d = pk_d(ins.x), ra = pk_a(ins.x), rb = pk_b(ins.x);
       const int32_t imm = (int32_t)ins.y;
+      if (conv && (op == SR_OP_LDS || op == SR_OP_STS) && !uninit && !fused) {
+        // Converged warp, shared load or store without the optional checks: the general
+        // path's steps for this one case (every runnable lane is at p, the next pc is p + 1).
+        const bool runl = st == ST_RUN;
+        const int32_t addr = (int32_t)(lds_u32(rs + ra * rstride) + (uint32_t)imm);
+        const bool inb = runl && (uint32_t)addr < shw;
+        uint32_t kind;
+        if (op == SR_OP_LDS) {
+          kind = K_R;
+          if (nw > 1 && !wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k, false, 0, 0, 0, spin, omin)) {
+            timeout = true;
+            break;
+          }
+          const uint32_t v = inb ? lds_u32(shs + (uint32_t)addr * 4u) : 0u;
+          if (runl && d != kNoDest) sts_u32(rs + d * rstride, v);
+        } else {
+          kind = K_W;
+          const uint32_t vb = lds_u32(rs + rb * rstride);
+          if (nw > 1) {
+            const int32_t lo = __reduce_min_sync(FULL, inb ? addr : INT_MAX);
+            const int32_t hi = __reduce_max_sync(FULL, inb ? addr : INT_MIN);
+            if (lane == 0) {
+              rlo[w] = lo;
+              rhi[w] = hi;
+              rsp[w] = 1u;
+              st_release_cta(&clk[w], 4u * k + 1u);
+            }
+            if (!wait_clocks(clk, rlo, rhi, rsp, nw, w, lane, 4u * k + 1u, true, lo, hi, 1u, spin, omin)) {
+              timeout = true;
+              break;
+            }
+          }
+          // several lanes on one word: the highest tid's store is kept (see the general path)
+          const uint32_t sm = __ballot_sync(FULL, inb);
+          const int32_t off = __shfl_sync(FULL, addr - (int32_t)lane, sm ? __ffs(sm) - 1 : 0);
+          bool last = inb;
+          if (!__all_sync(FULL, !inb || addr - (int32_t)lane == off)) {
+            const uint32_t grp = __match_any_sync(FULL, inb ? (uint32_t)addr : (0x80000000u | lane));
+            last = inb && lane == 31u - __clz(grp);
+          }
+          if (last) sts_u32(shs + (uint32_t)addr * 4u, vb);
+        }
+        const uint32_t em = __ballot_sync(FULL, runl && !inb);
+        if (em) note_err(err, bv, p, w, em, lane);
+        if (logging) log_access(bv, region, front_cap, inb, rec_of(epoch_hi, lane_rec | kind << 12 | p, (uint32_t)addr), lane);
+        n_instr += runl;
+        if (runl) pc = p + 1;
+        pn = p + 1;
+        ++k;
+        __syncwarp();
+        if (lane == 0) st_release_cta(&clk[w], 4u * k);
+        continue;
+      }
       const int32_t va = (int32_t)myregs[ra * nthr];
-      const int32_t vb = (ins.x & SR_BIMM) ? imm : (int32_t)myregs[rb * nthr];
+      const int32_t vb = pk_imm(ins.x) ? imm : (int32_t)myregs[rb * nthr];
       const bool wr = act && d != kNoDest;
       uint32_t npc = p + 1, cn = p + 1;         // cn: the warp's next pc while converged
       bool memop = false;

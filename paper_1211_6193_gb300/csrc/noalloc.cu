@@ -99,10 +99,10 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
   uint2* code = T.code;
   const RegMap rm = map_registers(*prog);
   for (uint32_t pc = 0; pc < ncode; ++pc) code[pc] = pack(prog->code[pc], rm);
-  const uint32_t z = rm.nrows - 1;
-  code[ncode] = make_uint2(SR_OP_EXIT | sr::kNoDest << 8 | z << 16 | z << 24, 0);
+  code[ncode] = exit_sentinel(rm);
+  set_run_lengths(code, ncode + 1);
   uint32_t npacked = ncode + 1;
-  if (npacked & 1) code[npacked++] = make_uint2(SR_OP_EXIT, 0);
+  if (npacked & 1) code[npacked++] = exit_sentinel(rm);
 
   const BoundScratch ws{T.colour, T.acc, T.bar, T.spc, T.snx, T.gacc};
   sr::LaunchDev* L = T.L;

@@ -405,9 +405,9 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
     code_off[i] = (uint32_t)code.size();
     const RegMap rm = map_registers(P);
     for (uint32_t pc = 0; pc < P.ncode; ++pc) code.push_back(pack(P.code[pc], rm));
-    const uint32_t z = rm.nrows - 1;
-    code.push_back(make_uint2(SR_OP_EXIT | sr::kNoDest << 8 | z << 16 | z << 24, 0));
-    if (code.size() & 1) code.push_back(make_uint2(SR_OP_EXIT, 0));
+    code.push_back(exit_sentinel(rm));
+    set_run_lengths(code.data() + code_off[i], P.ncode + 1);
+    if (code.size() & 1) code.push_back(exit_sentinel(rm));
     b->arena_off[i] = arena_total;
     b->arena_words[i] = P.global_words;
     arena_total += (P.global_words + 3) & ~3ull;

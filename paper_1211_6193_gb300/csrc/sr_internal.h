@@ -8,10 +8,27 @@
 
 namespace sr {
 
-// Packed instructions (device copy): register fields are rows of the program's compacted
-// register file (only the registers the program uses, plus one zero row last); a
-// destination field of kNoDest drops the write (RZ or an opcode without a result).
+// Packed instructions (device copy), x word: op:6 | immediate operand:1 | d:5 | a:5 | b:5 |
+// run:10, y word: the immediate.  Register fields are rows of the program's compacted
+// register file (only the registers the program uses, plus one zero row last); a destination
+// of kNoDest drops the write (RZ or an opcode without a result).  `run` is the number of
+// consecutive plain ALU instructions (MOV..SNE except DIV and REM, which can fail) starting
+// at this one, at most kRunMax, 0 for any other instruction: such a run touches no memory.
 constexpr uint32_t kNoDest = 31;
+constexpr uint32_t kRunMax = 1023;
+__host__ __device__ constexpr uint32_t pk_op(uint32_t x) { return x & 0x3Fu; }
+__host__ __device__ constexpr uint32_t pk_imm(uint32_t x) { return (x >> 6) & 1u; }
+__host__ __device__ constexpr uint32_t pk_d(uint32_t x) { return (x >> 7) & 31u; }
+__host__ __device__ constexpr uint32_t pk_a(uint32_t x) { return (x >> 12) & 31u; }
+__host__ __device__ constexpr uint32_t pk_b(uint32_t x) { return (x >> 17) & 31u; }
+__host__ __device__ constexpr uint32_t pk_run(uint32_t x) { return x >> 22; }
+__host__ __device__ constexpr uint32_t pk_make(uint32_t op, uint32_t imm, uint32_t d, uint32_t a, uint32_t b,
+                                               uint32_t run) {
+  return op | imm << 6 | d << 7 | a << 12 | b << 17 | run << 22;
+}
+__host__ __device__ constexpr bool pk_plain_alu(uint32_t op) {
+  return op >= SR_OP_MOV && op <= SR_OP_SNE && op != SR_OP_DIV && op != SR_OP_REM;
+}
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kMaxBudget = 1u << 26;  // epochs and rounds stay below 2^26
 // Polls of an mbarrier that only a CTA's own bulk copy (global -> its shared memory) completes.
