@@ -154,6 +154,12 @@ __device__ __forceinline__ int32_t alu(uint32_t op, int32_t x, int32_t y, bool& 
   }
 }
 
+// The ALU out of line, for the tight loop's rare operations (its body stays small).
+__device__ __noinline__ uint32_t alu_slow(uint32_t o, uint32_t a, uint32_t b) {
+  bool dz = false;
+  return (uint32_t)alu(o, (int32_t)a, (int32_t)b, dz);
+}
+
 // Wait until every other warp of the block has published a clock >= need.  With
 // `order` (store stage), also wait for lower warps whose store of this same round
 // (clock == need) touches an overlapping range of the same memory space.
@@ -530,10 +536,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
           const uint32_t b = pk_imm(in.x) ? in.y : lds_u32(rs + pk_b(in.x) * rstride);
           // ADD and MUL (the common filler) by selection, the others through the ALU
           uint32_t r = o == SR_OP_ADD ? a + b : a * b;
-          if (o != SR_OP_ADD && o != SR_OP_MUL) {
-            bool dz = false;
-            r = (uint32_t)alu(o, (int32_t)a, (int32_t)b, dz);
-          }
+          if (o != SR_OP_ADD && o != SR_OP_MUL) r = alu_slow(o, a, b);
           if (runl && dd != kNoDest) sts_u32(rs + dd * rstride, r);
           ++q;
           if (++i == len) break;
