@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="library default shapes instead of the autotuner")
     ap.add_argument("--tune-cache", default=None, help="JSON file caching tuned shapes per workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-global-leg", action="store_true",
+                    help="skip the global-memory race check leg (measured on the plain reduction)")
     ap.add_argument("--cpu-sample-blocks", type=int, default=0, help="oracle sample (blocks per launch; 0 = auto)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving trace length (s)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving arrival rate (jobs/s)")
@@ -242,7 +244,7 @@ def measure(binding, torch, progs, opts, steps, warmup, flush, stream):
         batch.run_and_check()
     n_reports = len(batch.fetch_reports())
     stats = batch.stats()
-    stage = {"reset": [], "interp": [], "check": [], "compact": []}
+    stage = {"reset": [], "interp": [], "check": [], "global": [], "compact": []}
     per_step = []
     for _ in range(steps):
         flush.zero_()
@@ -419,6 +421,24 @@ def run_native(args):
             "algorithmic_bytes": "8 B read per logged access + 16 B per race entry",
             "traffic": traffic_per_launch(args.workload, check_kernel(opts.get("check_variant", 0)), csha, units)}
 
+    # ---- the global-memory race check (sr_opts.check_global) as a leg of its own, on the plain
+    # reduction (2^24 global loads + 16384 stores per step): its stage time and HBM roofline,
+    # 32 algorithmic bytes per logged global access (16 B record written once and read once)
+    global_leg = None
+    if args.workload == "batched" and not args.no_global_leg:
+        gprogs = workload("reduction", rank)
+        gopts = {"mode": "plain", "interp_variant": 2, "check_variant": 5, "check_global": 1}
+        gst, gn, gper, gstage = measure(binding, torch, gprogs, gopts, 3, 1, flush, stream)
+        ms_g = gstage["global"]
+        gbs = 32 * gst.global_records / (ms_g / 1e3) / 1e9 if ms_g > 0 else 0.0
+        global_leg = {"workload": WORKLOADS["reduction"], "records_per_step": gst.global_records,
+                      "stage_ms": gstage, "ms_per_step": statistics.mean(gper), "reports_per_step": gn,
+                      "roofline": {"bound": "hbm", "kernels": "k_ggather, k_rs_upsweep, k_rs_pass, k_grun",
+                                   "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                                   "algorithmic_bytes": "32 B per logged global access (16 B record written, "
+                                                        "read once); radix passes beyond that are "
+                                                        "implementation cost"}}
+
     # ---- end to end through the C ABI from pinned host buffers: per step load_programs (the
     # programs' code and initial arenas host -> device), run_and_check, fetch_reports and one
     # fetch of every final arena (device -> host)
@@ -476,6 +496,8 @@ def run_native(args):
             "gpu_launches": args.steps * st.kernels, "waves": st.waves}
     if plain is not None:
         line["plain_path"] = plain
+    if global_leg is not None:
+        line["global_check"] = global_leg
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
