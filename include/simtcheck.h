@@ -73,6 +73,8 @@ typedef struct sr_batch sr_batch;
 #define SR_E_CUDA (-3)     /* a CUDA call failed; see sr_last_error */
 #define SR_E_TIMEOUT (-4)  /* a device-side wait gave up (bounded spin) */
 #define SR_E_RANGE (-5)    /* destination buffer too small (size returned) */
+#define SR_E_BOUNDS (-6)   /* library built with SR_DEBUG_BOUNDS: an internal index check failed in a
+                              kernel (the access was skipped); the results are invalid */
 
 /* ---------------------------------------------------------------- IR opcodes */
 enum {
@@ -121,7 +123,9 @@ enum {
   SR_ST_DEADLOCK = 1,        /* a block deadlocked; later launches were skipped */
   SR_ST_STEP_LIMIT = 2,      /* a block ran out of rounds; later launches were skipped */
   SR_ST_LOG_OVERFLOW = 4,    /* a block's access log exceeded its region: race check incomplete */
-  SR_ST_INTERNAL = 8         /* a device-side wait timed out: results of the program are invalid */
+  SR_ST_INTERNAL = 8,        /* a device-side wait timed out: results of the program are invalid */
+  SR_ST_BOUNDS = 16          /* library built with SR_DEBUG_BOUNDS: an index check of the interpreter
+                                failed for this program (the access was skipped); results invalid */
 };
 
 typedef struct { uint32_t op_d_a_b; int32_t imm; } sr_instr;

@@ -21,12 +21,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libsimtcheck.so")
 
 # return codes / constants (include/simtcheck.h)
-SR_OK, SR_E_INVAL, SR_E_NOMEM, SR_E_CUDA, SR_E_TIMEOUT, SR_E_RANGE = 0, -1, -2, -3, -4, -5
+SR_OK, SR_E_INVAL, SR_E_NOMEM, SR_E_CUDA, SR_E_TIMEOUT, SR_E_RANGE, SR_E_BOUNDS = 0, -1, -2, -3, -4, -5, -6
 SR_ALL_PROGRAMS = 0xFFFFFFFF
 MODE_PLAIN, MODE_BATCHED = 0, 1
 RACE, DIVERGENCE, DEADLOCK, STEP_LIMIT, ERR_OOB_SHARED, ERR_OOB_GLOBAL, ERR_DIV0, ERR_UNINIT_SHARED = range(1, 9)
 GLOBAL_RACE, GLOBAL_BLOCKS, GLOBAL_LAUNCHES = 9, 10, 11
-ST_DEADLOCK, ST_STEP_LIMIT, ST_LOG_OVERFLOW, ST_INTERNAL = 1, 2, 4, 8
+ST_DEADLOCK, ST_STEP_LIMIT, ST_LOG_OVERFLOW, ST_INTERNAL, ST_BOUNDS = 1, 2, 4, 8, 16
 REPORT_DTYPE = np.dtype([(n, "<u4") for n in ("kind", "prog", "launch", "block", "epoch", "a", "b", "c")])
 
 

@@ -790,6 +790,8 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
       const uint32_t gb = first + b;
       const uint32_t n = sh[2 + b];
       if (!n) continue;
+      // (debug build: the block's records lie inside its region)
+      if (!dbg_ok(n <= cap && gb - base < L->grid, A.error_flag, kErrBounds)) continue;
       unsigned long long* const region = log0 + (unsigned long long)(gb - base) * cap;
       uint32_t race_out = 0, ep = 0, ivs = 0;
       // a stage: this thread's records plus three epochs (the stage's first and last
@@ -847,7 +849,7 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
     __syncthreads();
     ipar ^= 1u;
   }
-  if (bad || stop) atomicOr(A.error_flag, 2u);
+  if (bad || stop) atomicOr(A.error_flag, kErrCorrupt);
 }
 
 template <uint32_t NC, uint32_t PER, uint32_t MINB>

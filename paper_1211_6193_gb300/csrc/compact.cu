@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(256) k_emit(CompactArgs A) {
     const uint4* reg4 = reinterpret_cast<const uint4*>(A.log + L->log_base + (unsigned long long)lb * L->log_cap);
     const uint32_t top = L->log_cap / 2 - 1;        // misc entry j lives at reg4[top - j]
     const uint4* ge = ng ? A.gentries + 2 * A.gstart[gb - A.gb0] : nullptr;   // the block's global list
+    // (debug build: both lists lie inside the block's region)
+    if (!dbg_ok(2ull * (nr + nm) <= L->log_cap, A.error_flag, kErrBounds)) continue;
     const unsigned long long base = A.offsets[gb];
     // misc entries (epoch order) with epoch below / at most `ep`
     auto misc_below = [&](uint32_t ep, bool at_most) {

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(SC_T) k_count_offsets(const uint32_t* c, uint3
 __global__ void __launch_bounds__(256) k_ggather(const LaunchDev* launches, uint32_t li0, uint32_t li1,
                                                  uint32_t gb0, uint32_t gb1, const uint4* glog,
                                                  const uint32_t* glog_n, const unsigned long long* off,
-                                                 uint4* out) {
+                                                 uint4* out, unsigned long long cap, uint32_t* err) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
   for (uint32_t gb = gb0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gb < gb1; gb += nwarps) {
@@ -197,6 +197,8 @@ __global__ void __launch_bounds__(256) k_ggather(const LaunchDev* launches, uint
       if (launches[mid].block_base <= gb) lo = mid; else hi = mid - 1;
     }
     const LaunchDev& L = launches[lo];
+    // (debug build: the block's records fit its region and the gathered array)
+    if (!dbg_ok(n <= L.glog_cap && off[gb - gb0] + n <= cap, err, kErrBounds)) continue;
     const uint4* src = glog + L.glog_base + (unsigned long long)(gb - L.block_base) * L.glog_cap;
     uint4* dst = out + off[gb - gb0];
     for (uint32_t i = lane; i < n; i += 32) dst[i] = src[i];
@@ -653,7 +655,8 @@ cudaError_t launch_gcheck(const GcheckArgs& G, uint32_t& kernels, cudaStream_t s
   {
     const uint32_t want = (G.gb1 - G.gb0 + 7) / 8;
     const uint32_t ctas = std::max(1u, std::min(want, 8u * G.sms));
-    k_ggather<<<ctas, 256, 0, s>>>(G.launches, G.li0, G.li1, G.gb0, G.gb1, G.glog, G.glog_n, G.goff, G.sort_a);
+    k_ggather<<<ctas, 256, 0, s>>>(G.launches, G.li0, G.li1, G.gb0, G.gb1, G.glog, G.glog_n, G.goff, G.sort_a,
+                                   G.rec_cap, G.err);
     ++kernels;
   }
   // 2. sort by word address

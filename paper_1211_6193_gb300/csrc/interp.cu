@@ -530,8 +530,14 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
         if (lane == 0) st_release_cta(&clk[w], 4u * (k + len));
         uint32_t q = p;
         uint2 in = ins;
+        bool bad = false;                        // (debug build: an index check failed)
         for (uint32_t i = 0;;) {
           const uint32_t o = pk_op(in.x), dd = pk_d(in.x);
+          if (!dbg_ok(q <= ncode && pk_a(in.x) < nrows && pk_b(in.x) < nrows && (dd < nrows || dd == kNoDest),
+                      &A.prog_status[Ls->prog], SR_ST_BOUNDS)) {
+            bad = true;
+            break;
+          }
           const uint32_t a = lds_u32(rs + pk_a(in.x) * rstride);
           const uint32_t b = pk_imm(in.x) ? in.y : lds_u32(rs + pk_b(in.x) * rstride);
           // ADD and MUL (the common filler) by selection, the others through the ALU
@@ -542,6 +548,10 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
           if (++i == len) break;
           in = lds_u64(irs + q * 8u);
         }
+        if (bad) {                               // stop the block the way a wait that gave up does
+          timeout = true;
+          break;
+        }
         n_instr += runl ? len : 0u;
         if (runl) pc = q;
         pn = q;
@@ -550,6 +560,11 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       }
       const uint32_t d = pk_d(ins.x), ra = pk_a(ins.x), rb = pk_b(ins.x);
       const int32_t imm = (int32_t)ins.y;
+      if (!dbg_ok(p <= ncode && ra < nrows && rb < nrows && (d < nrows || d == kNoDest), &A.prog_status[Ls->prog],
+                  SR_ST_BOUNDS)) {
+        timeout = true;                          // (debug build) stop the block like a failed wait
+        break;
+      }
       if (conv && (op == SR_OP_LDS || op == SR_OP_STS) && !uninit && !fused) {
         // Converged warp, shared load or store without the optional checks: the general
         // path's steps for this one case (every runnable lane is at p, the next pc is p + 1).

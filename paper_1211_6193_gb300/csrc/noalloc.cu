@@ -248,6 +248,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     ka.out = d_reports;
     ka.out_cap = report_cap;
     ka.counters = ra.counters;
+    ka.error_flag = heads + kMaxWaves;
     NA_TRY(sr::launch_compact_scan(ka, s));
     NA_TRY(sr::launch_compact_emit(ka, s));
   }
@@ -260,6 +261,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
 #undef NA_TRY
   *n_reports = total;
   *status = st;
+  if (err & sr::kErrBounds) return SR_E_BOUNDS;
   if (err) return SR_E_TIMEOUT;
   return total > report_cap ? SR_E_RANGE : SR_OK;
 }

@@ -166,6 +166,7 @@ sr::CompactArgs compact_args(sr_batch* b, const Wave& w) {
   ka.out = (sr_report*)b->out.p;
   ka.out_cap = b->out_cap;
   ka.counters = (sr::Counters*)b->counters.p;
+  ka.error_flag = (uint32_t*)b->err_flag.p;
   if (w.glog_records) {
     ka.gcount = (const uint32_t*)b->gcount.p;
     ka.gstart = (const unsigned long long*)b->gstart.p;
@@ -752,7 +753,9 @@ int fetch_reports(sr_ctx* c, sr_batch* b, sr_report* dst, uint64_t cap, uint64_t
   CUDA_TRY(c, cudaMemcpyAsync(&err, b->err_flag.p, 4, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(c, cudaStreamSynchronize(s));
   if (n_total) *n_total = total;
-  if (err) return fail(c, SR_E_TIMEOUT, "the race checker's staging wait gave up");
+  if (err & sr::kErrBounds) return fail(c, SR_E_BOUNDS, "an internal index check failed (debug build)");
+  if (err & sr::kErrCorrupt) return fail(c, SR_E_TIMEOUT, "the race checker found an access log out of order");
+  if (err) return fail(c, SR_E_TIMEOUT, "a device-side wait of the checks gave up");
   if (!dst) return SR_OK;
   if (cap < total) return fail(c, SR_E_RANGE, "report buffer holds %llu, %llu needed", (unsigned long long)cap, total);
   if (total) CUDA_TRY(c, cudaMemcpyAsync(dst, b->out.p, total * sizeof(sr_report), cudaMemcpyDeviceToHost, s));

@@ -37,6 +37,19 @@ constexpr uint32_t kMaxBudget = 1u << 26;  // epochs and rounds stay below 2^26
 // CTA returns or reuses the buffer, so that no copy is left writing shared memory.
 constexpr uint32_t kCopyWaitLimit = 1u << 24;
 
+// Debug build (-DSR_DEBUG_BOUNDS): internal indices are checked before each access; a failed
+// check sets `flag_bits` in *flag and the access is skipped (no trap, no fault: the kernel
+// goes on and the host reports the failure).  In the default build the check is compiled away.
+#if defined(SR_DEBUG_BOUNDS) && defined(__CUDACC__)
+__device__ __forceinline__ bool dbg_ok(bool ok, uint32_t* flag, uint32_t flag_bits) {
+  if (!ok) atomicOr(flag, flag_bits);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool dbg_ok(bool, uint32_t*, uint32_t) { return true; }
+#endif
+constexpr uint32_t kErrTimeout = 1, kErrCorrupt = 2, kErrBounds = 4;   // batch error word bits
+
 // thread status of a simulated thread
 enum : uint32_t { ST_RUN = 0, ST_WAIT = 1, ST_EXIT = 2, ST_NONE = 3 };
 // access kinds inside a log record
@@ -274,6 +287,7 @@ struct CompactArgs {
   const unsigned long long* gstart;
   const uint4* gentries;
   unsigned long long gcap;      // entries the buffer holds (a wave that produced more is run again)
+  uint32_t* error_flag;         // debug build: kErrBounds
 };
 cudaError_t launch_compact_scan(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_compact_emit(const CompactArgs& a, cudaStream_t s);
