@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
     ap.add_argument("--interp-variant", type=int, default=0, choices=[0, 1, 2],
                     help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
-    ap.add_argument("--check-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
+    ap.add_argument("--check-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7],
                     help="race-check kernel shape (0 = default); setting a shape flag skips the autotuner")
     ap.add_argument("--fused-check", action="store_true",
                     help="race check inside the interpreter on per-word summaries (no access log)")
@@ -232,8 +232,9 @@ def traffic_per_launch(workload: str, kernel: str, src: str, units: dict):
 
 
 def check_kernel(variant: int) -> str:
-    """Kernel name of a race-check shape (variants 1-2: TMA ring, 3-5: register-staged)."""
-    return "k_check" if variant in (1, 2) else "k_check_reg"
+    """Kernel name of a race-check shape (variants 1-2: TMA ring, 3-5: register-staged, 6-7: lean
+    one-warp)."""
+    return "k_check" if variant in (1, 2) else "k_check_lean" if variant in (6, 7) else "k_check_reg"
 
 
 def measure(binding, torch, progs, opts, steps, warmup, flush, stream):

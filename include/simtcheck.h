@@ -209,7 +209,7 @@ typedef struct {
                                 the reports are exact, the racing words are not.  0 = off */
 } sr_opts;
 
-#define SR_CHECK_VARIANTS 5
+#define SR_CHECK_VARIANTS 7
 
 typedef struct {
   uint64_t thread_instrs;    /* simulated thread-instructions executed */

@@ -34,7 +34,7 @@ import numpy as np
 
 from .workloads.ir import Program
 
-CHECK_VARIANTS = (1, 2, 3, 4, 5)
+CHECK_VARIANTS = (1, 2, 3, 4, 5, 6, 7)
 INTERP_CANDIDATES = {
     "plain": ({"interp_variant": 1}, {"interp_variant": 2}),
     "batched": ({"ctas_per_sm": 1}, {"ctas_per_sm": 2}),

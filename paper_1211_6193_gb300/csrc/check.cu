@@ -852,6 +852,173 @@ __global__ void __launch_bounds__(NC, MINB) k_check_reg(CheckArgs A) {
   if (bad || stop) atomicOr(A.error_flag, kErrCorrupt);
 }
 
+// ---------------------------------------------------------------- lean one-warp form
+// One warp per CTA and one simulated block at a time, as in the one-warp register-staged form,
+// with a leaner main loop: a chunk is 32 x R records, lane l holding records base + 32 j + l
+// (one coalesced 8-byte load per j), the next chunk's loads in flight while this one is
+// applied.  A chunk whose first and last records belong to the open interval - most of them -
+// goes to the table with no per-record interval work; only a chunk in which intervals end is
+// taken apart interval by interval.  Intervals are closed, spilled and checked exactly by the
+// same code as in the other forms.
+template <uint32_t R>
+__device__ __forceinline__ void lean_load(const unsigned long long* region, uint32_t base, uint32_t n, uint32_t lane,
+                                          uint32_t (&lo)[R], uint32_t (&hi)[R]) {
+#pragma unroll
+  for (uint32_t j = 0; j < R; ++j) {
+    const uint32_t i = base + 32u * j + lane;
+    unsigned long long v = 0;
+    if (i < n) v = __ldcs(region + i);           // streamed once (the exact pass re-reads from L2 or HBM)
+    lo[j] = (uint32_t)v;
+    hi[j] = (uint32_t)(v >> 32);
+  }
+}
+
+template <uint32_t R>
+__global__ void __launch_bounds__(32, 20) k_check_lean(CheckArgs A) {
+  using C = RegCfg<32>;
+  constexpr uint32_t T = 32u * R;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t* tab = reinterpret_cast<uint32_t*>(smem + C::O_TABLE);
+  const uint32_t ntab = A.table_words;
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem + C::O_BM);
+  uint32_t* pre = reinterpret_cast<uint32_t*>(smem + C::O_PRE);
+  volatile uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + C::O_ITEM);
+  uint32_t* misc = reinterpret_cast<uint32_t*>(smem + C::O_MISC);
+  volatile uint32_t* s_racy = misc;              // [2] tag of the racy interval, by interval parity
+  uint32_t* wtot = misc + 8;
+  const uint32_t lane = threadIdx.x;
+  uint4* const stage_out = A.scratch + (size_t)blockIdx.x * kScratchWords;
+  uint32_t* const gtab = reinterpret_cast<uint32_t*>(stage_out + kCheckBins);
+  bool g_ready = false, bad = false;
+
+  for (uint32_t i = lane; i < ntab; i += 32) tab[i] = 0;
+  if (lane < 8) misc[lane] = 0;
+  {
+    uint32_t item = 0;
+    if (lane == 0) item = A.item0 + atomicAdd(A.work_head, 1u);
+    item_setup(A, __shfl_sync(FULL, item, 0), s_items, kAheadStages * T);
+  }
+  __syncwarp();
+  uint32_t ipar = 0;
+  uint32_t iv = 1, par = 0, tag = 1, tagw = 1u << 14;
+  for (;;) {
+    volatile uint32_t* sh = s_items + ipar * C::ITEM_WORDS;
+    const uint32_t item = sh[0];
+    if (item >= A.item1) break;
+    const LaunchDev* L = A.launches + sh[1];
+    const uint32_t first = L->block_base + (item - L->check_item) * L->check_group;
+    const uint32_t nb = min(L->check_group, L->block_base + L->grid - first);
+    unsigned long long* const log0 = A.log + L->log_base;
+    const uint32_t cap = L->log_cap, base0 = L->block_base, shw = L->shw;
+    for (uint32_t b = 0; b < nb && !bad; ++b) {
+      const uint32_t gb = first + b;
+      const uint32_t n = sh[2 + b];
+      if (!n) continue;
+      if (!dbg_ok(n <= cap && gb - base0 < L->grid, A.error_flag, kErrBounds)) continue;
+      unsigned long long* const region = log0 + (unsigned long long)(gb - base0) * cap;
+      const uint32_t* const hw = reinterpret_cast<const uint32_t*>(region) + 1;   // high word of record i: hw[2i]
+      uint32_t race_out = 0, ivs = 0;            // race entries written, start of the open interval
+      uint32_t cur = hw[0] >> 6;                 // its epoch
+      bool ovf = false;                          // some record of the open interval is past the table
+      // close the open interval at record `end`
+      auto close = [&](uint32_t end) {
+        const bool spill = __any_sync(FULL, ovf);
+        ovf = false;
+        if (spill) spill_interval<32>(gtab, shw, region, ivs, end, tagw, tag, s_racy + par, bad, g_ready);
+        close_interval<32>(tab, ntab, gtab, spill, g_ready, bm, pre, wtot, stage_out, s_racy, region, race_out, shw,
+                           iv, par, tag, tagw, cur, ivs, end);
+      };
+      uint32_t clo[R], chi[R];
+      lean_load<R>(region, 0, n, lane, clo, chi);
+      for (uint32_t base = 0; base < n; base += T) {
+        const uint32_t e = min(n, base + T);
+        uint32_t nlo[R], nhi[R];
+        const bool more = e < n;
+        if (more) {                              // the next chunk's loads go out first
+          lean_load<R>(region, e, n, lane, nlo, nhi);
+          const uint32_t far = base + kAheadStages * T;
+          if (lane == 0 && far < n) prefetch_l2(region + far, ((min(T, n - far) + 1u) & ~1u) * 8u);
+        }
+        // the epoch of the chunk's last record, from the register that holds it
+        uint32_t last_ep;
+        {
+          const uint32_t t = e - 1u - base, jl = t >> 5;
+          uint32_t h = chi[0];
+#pragma unroll
+          for (uint32_t j = 1; j < R; ++j) h = jl == j ? chi[j] : h;
+          last_ep = __shfl_sync(FULL, h, t & 31u) >> 6;
+        }
+        uint32_t valid = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < R; ++j) valid |= (base + 32u * j + lane < e ? 1u : 0u) << j;
+        if (last_ep == cur) {
+          // the whole chunk lies in the open interval
+          if (__any_sync(FULL, valid != 0)) table_add_set<R>(tab, ntab, clo, chi, valid, tagw, tag, s_racy + par, ovf);
+        } else {
+          // intervals end in this chunk: apply it interval by interval (epochs ascend)
+          uint32_t pending = valid;              // this lane's records not applied yet
+          for (;;) {
+            uint32_t m = 0, later = kInf;
+#pragma unroll
+            for (uint32_t j = 0; j < R; ++j) {
+              const uint32_t ep = chi[j] >> 6;
+              if ((pending >> j) & 1u) {
+                if (ep == cur) m |= 1u << j;
+                else if (ep > cur) later = min(later, base + 32u * j + lane);
+                else bad = true;                 // epochs out of order: a corrupt log
+              }
+            }
+            pending &= ~m;
+            if (__any_sync(FULL, m != 0)) table_add_set<R>(tab, ntab, clo, chi, m, tagw, tag, s_racy + par, ovf);
+            later = __reduce_min_sync(FULL, later);
+            if (later == kInf || __any_sync(FULL, bad)) break;   // the open interval goes on
+            close(later);
+            ivs = later;
+            cur = hw[2u * later] >> 6;
+          }
+          if (__any_sync(FULL, bad)) {
+            bad = true;
+            break;
+          }
+        }
+        if (more) {
+#pragma unroll
+          for (uint32_t j = 0; j < R; ++j) {
+            clo[j] = nlo[j];
+            chi[j] = nhi[j];
+          }
+        }
+      }
+      if (bad) break;
+      close(n);
+      if (lane == 0) A.blocks[gb].n_race = race_out;
+    }
+    if (bad) break;
+    uint32_t next = 0;
+    if (lane == 0) next = A.item0 + atomicAdd(A.work_head, 1u);
+    ipar ^= 1u;
+    item_setup(A, __shfl_sync(FULL, next, 0), s_items + ipar * C::ITEM_WORDS, kAheadStages * T);
+    __syncwarp();
+  }
+  if (bad) atomicOr(A.error_flag, kErrCorrupt);
+}
+
+template <uint32_t R>
+struct LeanVariant {
+  static constexpr uint32_t smem(uint32_t table_words) { return RegCfg<32>::smem(table_words); }
+  static cudaError_t init(uint32_t optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_check_lean<R>);
+    if (e != cudaSuccess) return e;
+    if (smem(NB) + fa.sharedSizeBytes > optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k_check_lean<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(NB));
+  }
+  static cudaError_t launch(const CheckArgs& a, uint32_t ctas, cudaStream_t s) {
+    k_check_lean<R><<<ctas, 32, smem(a.table_words), s>>>(a);
+    return cudaGetLastError();
+  }
+};
+
 template <uint32_t NC, uint32_t PER, uint32_t MINB>
 struct RegVariant {
   static constexpr uint32_t smem(uint32_t table_words) { return RegCfg<NC>::smem(table_words); }
@@ -904,6 +1071,8 @@ const VariantEntry kVariants[SR_CHECK_VARIANTS] = {
     entry<RegVariant<128, 4, 4>, 4, kCheckTableCap>(),
     entry<RegVariant<64, 4, 8>, 8, kCheckTableCap>(),
     entry<RegVariant<32, 4, 16>, 16, kCheckTableCap / 2>(),
+    entry<LeanVariant<4>, 20, kCheckTableCap / 2>(),
+    entry<LeanVariant<8>, 20, kCheckTableCap / 2>(),
 };
 constexpr uint32_t kDefaultVariant = 4;
 

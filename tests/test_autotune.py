@@ -22,7 +22,7 @@ def _fake(times_i, times_c, digest="d", fused=(9.0, 0.0)):
 
 def test_picks_fastest_interp_then_fastest_checker_behind_it():
     progs = [fig1.program()]
-    m, calls = _fake({"interp_variant=1": 3.0, "interp_variant=2": 2.0}, {1: 5.0, 2: 4.0, 3: 1.5, 4: 2.5, 5: 3.0})
+    m, calls = _fake({"interp_variant=1": 3.0, "interp_variant=2": 2.0}, {1: 5.0, 2: 4.0, 3: 1.5, 4: 2.5, 5: 3.0, 6: 2.0, 7: 2.2})
     t = autotune.tune(progs, "plain", measure=m, device="fake")
     assert t.options == {"mode": "plain", "interp_variant": 2, "check_variant": 3}
     # checker variants, then the fused check, were all timed behind the chosen interpreter
@@ -37,7 +37,7 @@ def test_picks_fastest_interp_then_fastest_checker_behind_it():
 def test_fused_check_kept_only_when_the_whole_run_is_faster():
     progs = [fig1.program()]
     # interpreter 2.0 + checker 1.5 = 3.5: fused 3.4 wins, 3.6 does not
-    checks = {1: 2.0, 2: 2.0, 3: 1.5, 4: 2.0, 5: 2.0}
+    checks = {1: 2.0, 2: 2.0, 3: 1.5, 4: 2.0, 5: 2.0, 6: 2.0, 7: 2.0}
     m, _ = _fake({"interp_variant=1": 3.0, "interp_variant=2": 2.0}, checks, fused=(3.3, 0.1))
     t = autotune.tune(progs, "plain", measure=m, device="fake")
     assert t.options == {"mode": "plain", "interp_variant": 2, "fused_check": 1}

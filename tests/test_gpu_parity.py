@@ -236,7 +236,7 @@ def test_more_racy_words_than_one_summary_round(B, mode):
     assert len(races) == 2 * (8 + 3 + 12) * 1024
 
 
-@pytest.mark.parametrize("variant", range(1, 6))
+@pytest.mark.parametrize("variant", range(1, 8))
 def test_every_check_variant(B, variant):
     """Each race-check kernel shape on its own: the table sized to small and large shared
     arrays, intervals with more racy words than a summary round holds, intervals spanning
@@ -453,7 +453,7 @@ def tag_wrap_program(iters: int = 300000) -> ir.Program:
     return Program(a.assemble(), [0], [Launch(0, 1, 2, 3, ())], np.zeros(4, np.int32), name=f"tag_wrap_{iters}")
 
 
-@pytest.mark.parametrize("variant", [0, 1, 5])
+@pytest.mark.parametrize("variant", [0, 1, 5, 6, 7])
 def test_checker_interval_tags_wrap(B, variant):
     p = tag_wrap_program()
     got, want = assert_parity(B, [p], "plain", check_variant=variant, loop_log_records=1 << 20)
