@@ -81,8 +81,10 @@ def parse():
     ap.add_argument("--no-global-leg", action="store_true",
                     help="skip the global-memory race check leg (measured on the plain reduction)")
     ap.add_argument("--cpu-sample-blocks", type=int, default=0, help="oracle sample (blocks per launch; 0 = auto)")
-    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving trace length (s)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving trace length (s)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving arrival rate (jobs/s)")
+    ap.add_argument("--serve-runs", type=int, default=3, help="serving: runs of the trace (median reported)")
+    ap.add_argument("--serve-inflight", type=int, default=4, help="serving: worker threads (streams)")
     ap.add_argument("--blocks", type=int, default=16384,
                     help="blocks of the reduction (default: the full workload; smaller only for profiling)")
     ap.add_argument("--shard", action="store_true",
@@ -284,28 +286,37 @@ def run_serving(args):
     arrivals = serving.poisson_trace(args.serve_rate, args.serve_seconds, seed=5 + rank)
     jobs = [serving.Job(k, pool[k % len(pool)], t) for k, t in enumerate(arrivals)]
     shapes = {"check_variant": args.check_variant} if args.check_variant else {}
-    warm = serving.Server(log_budget_bytes=120 << 30, max_inflight=4, **shapes)
-    warm.serve([serving.Job(k, pool[k], 0.0) for k in range(16)])      # load kernels, warm the allocator
-    warm.close()
-    srv = serving.Server(log_budget_bytes=120 << 30, max_inflight=4, **shapes)
+    srv = serving.Server(log_budget_bytes=120 << 30, max_inflight=args.serve_inflight, **shapes)
+    # warm-up: load the kernels, then two seconds of the trace (fills the page-locked host cache
+    # and the contexts' device pools with the sizes the runs will ask for)
+    srv.serve([serving.Job(k, pool[k], 0.0) for k in range(16)])
+    srv.serve([serving.Job(j.jid, j.program, j.arrival) for j in jobs if j.arrival < 2.0])
+    runs = []
     with ClockSampler(local) as clocks:
-        torch.cuda.synchronize()
-        _, st = srv.serve(jobs, on_result=lambda jid, r: None)      # latency recorded, result dropped
-        torch.cuda.synchronize()
+        for _ in range(args.serve_runs):
+            torch.cuda.synchronize()
+            _, st = srv.serve(jobs, on_result=lambda jid, r: None)  # latency recorded, result dropped
+            torch.cuda.synchronize()
+            runs.append(st)
     srv.close()
+    med = sorted(runs, key=lambda r: r.accesses_per_s)[len(runs) // 2]
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": st.accesses_per_s * world, "unit": UNIT, "n_gpus": world, "steps": 1,
-            "warmup": 1, "ms_per_step": st.seconds * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "metric": METRIC, "value": med.accesses_per_s * world, "unit": UNIT, "n_gpus": world,
+            "steps": len(runs), "warmup": 1, "ms_per_step": med.seconds * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOADS["serving"].replace("2000 jobs/s", f"{args.serve_rate:g} jobs/s"),
-                       "trace_seconds": args.serve_seconds, "jobs": st.jobs, "shapes": shapes or "library default",
-                       "inputs": "page-locked host memory"},
-            "serving": {"p50_latency_ms": st.p50_ms, "p99_latency_ms": st.p99_ms, "jobs_per_s": st.jobs_per_s,
-                        "batches": st.batches, "mean_batch_jobs": st.mean_batch_jobs,
-                        "max_inflight_batches": st.max_inflight_seen, "peak_log_bytes": st.peak_log_bytes,
-                        "host_load_s": st.host_load_s, "host_fetch_s": st.host_fetch_s,
-                        "mean_batch_gpu_ms": st.mean_batch_gpu_ms},
+                       "trace_seconds": args.serve_seconds, "jobs": med.jobs, "runs": len(runs),
+                       "workers": args.serve_inflight, "shapes": shapes or "library default",
+                       "inputs": "page-locked host memory", "value": "the run with the median throughput"},
+            "serving": {"p50_latency_ms": med.p50_ms, "p99_latency_ms": med.p99_ms, "jobs_per_s": med.jobs_per_s,
+                        "p50_latency_ms_runs": [r.p50_ms for r in runs],
+                        "p99_latency_ms_runs": [r.p99_ms for r in runs],
+                        "jobs_per_s_runs": [r.jobs_per_s for r in runs],
+                        "batches": med.batches, "mean_batch_jobs": med.mean_batch_jobs,
+                        "max_inflight_batches": med.max_inflight_seen, "peak_log_bytes": med.peak_log_bytes,
+                        "worker_load_s": med.host_load_s, "worker_fetch_s": med.host_fetch_s,
+                        "mean_batch_gpu_ms": med.mean_batch_gpu_ms},
             "clocks": clocks.summary()}), flush=True)
 
 
