@@ -985,8 +985,9 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_plain(RunArgs A, uint32_t
                            threadIdx.x >> 5, blockDim.x >> 5, 1);
 }
 
-// Persistent: CTAs pop (launch, first block) items from a device queue; an item runs
-// `groups` simulated blocks side by side, each on its own warps and named barrier.
+// Persistent: CTAs pop (launch, first block) items from a device queue; an item's
+// `item_blocks` simulated blocks run `groups` at a time side by side, each group on its own
+// warps and named barrier, a group taking the item's next unclaimed block when it finishes one.
 // Items are ordered launch-wave by launch-wave, and an item waits (bounded) until every
 // block of the launches it follows (the previous launch of its stream, the one it waits
 // for) has completed; launches of other streams run meanwhile.
@@ -995,7 +996,7 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_batched(RunArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LaunchDev Ls;
   __shared__ __align__(8) unsigned long long mbar;
-  __shared__ uint32_t s_item, s_skip;
+  __shared__ uint32_t s_item, s_skip, s_next, s_claim[32];
   uint32_t phase = 0;
   if (threadIdx.x == 0) mbar_init(&mbar);
   __syncthreads();
@@ -1028,18 +1029,28 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_batched(RunArgs A) {
       if (skip) atomicOr(&A.launch_dead[Ls.index], 1u);
       if (!skip) bulk_load(smem, A.code + Ls.code_off, Ls.ir_bytes, &mbar);
       s_skip = skip;
+      s_next = Ls.groups;
     }
     __syncthreads();
-    const uint32_t nblk = min(Ls.groups, Ls.grid - it.y);
+    const uint32_t nblk = min(Ls.item_blocks, Ls.grid - it.y);
     bool drained = true;
     if (!s_skip) {
       const bool ok = stage_wait(&mbar, phase, drained);
       phase ^= 1u;
       const uint32_t nw = (Ls.bdim + 31) >> 5;
       const uint32_t wid = threadIdx.x >> 5, g = wid / nw;
-      if (ok && g < nblk)
-        run_block<Fused, Global>(A, &Ls, it.y + g, reinterpret_cast<const uint2*>(smem),
-                                 smem + Ls.ir_bytes + g * Ls.group_bytes, wid - g * nw, nw, 1 + g);
+      if (ok && g < Ls.groups) {
+        // block j of the item: the first `groups` one per group, the rest claimed in turn; the
+        // group barrier after each block also keeps the next block's set-up behind the last
+        // reads of this one
+        for (uint32_t j = g; j < nblk;) {
+          run_block<Fused, Global>(A, &Ls, it.y + j, reinterpret_cast<const uint2*>(smem),
+                                   smem + Ls.ir_bytes + g * Ls.group_bytes, wid - g * nw, nw, 1 + g);
+          if (wid == g * nw && (threadIdx.x & 31) == 0) s_claim[g] = atomicAdd(&s_next, 1u);
+          group_sync(1 + g, nw * 32);
+          j = s_claim[g];
+        }
+      }
       if (!ok && threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
     }
     __syncthreads();

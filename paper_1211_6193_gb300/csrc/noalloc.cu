@@ -137,6 +137,7 @@ extern "C" int sr_check_program_noalloc(const sr_program* prog, int32_t* d_arena
     const uint32_t nw = (pl.block_dim + 31) / 32;
     d.group_bytes = sr::group_layout(nw * 32, pl.shmem_words, ncode, rm.nrows, 0, 0).total;
     d.groups = 1;
+    d.item_blocks = 1;
     d.check_group = sr::check_group_for(d.log_cap);
     d.check_item = (uint32_t)check_items;
     check_items += (d.grid + d.check_group - 1) / d.check_group;

@@ -490,6 +490,12 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       uint32_t g = std::min<uint32_t>(32 / nw, (smem_budget - d.ir_bytes) / d.group_bytes);
       if (nw >= 2) g = std::min<uint32_t>(g, 15);
       d.groups = std::max<uint32_t>(1, std::min<uint32_t>(g, d.grid));
+      // blocks per work item: up to 8 rounds of `groups` while the launch still makes two
+      // items per SM, so that a group that finishes early takes another block of the item
+      // instead of waiting for the item's slowest block
+      const uint32_t rounds = std::max<uint32_t>(1, std::min<uint32_t>(
+          8, d.grid / std::max<uint32_t>(1, d.groups * 2u * (uint32_t)c->sms)));
+      d.item_blocks = d.groups * rounds;
       d.check_group = sr::check_group_for(d.log_cap);
       d.check_item = (uint32_t)check_items;
       check_items += (d.grid + d.check_group - 1) / d.check_group;
@@ -562,7 +568,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   b->glog_records = gwave_max;
   b->entry_cap = std::max<uint64_t>(1024, std::min<uint64_t>(gwave_max, o.report_cap ? o.report_cap : 1u << 20));
 
-  // ---- batched work items: per wave, launch-index order, blocks in chunks of `groups`
+  // ---- batched work items: per wave, launch-index order, blocks in chunks of `item_blocks`
   b->batched_smem = 0;
   for (Wave& w : b->waves) {
     w.item0 = (uint32_t)b->items.size();
@@ -572,7 +578,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       for (uint32_t li = w.li0; li < w.li1; ++li) {
         const LaunchDev& d = b->launches[li];
         if (d.launch != lv) continue;
-        for (uint32_t blk = 0; blk < d.grid; blk += d.groups) b->items.push_back(make_uint2(li, blk));
+        for (uint32_t blk = 0; blk < d.grid; blk += d.item_blocks) b->items.push_back(make_uint2(li, blk));
         b->batched_smem = std::max(b->batched_smem, d.ir_bytes + d.groups * d.group_bytes);
       }
     w.item1 = (uint32_t)b->items.size();

@@ -94,6 +94,9 @@ struct LaunchDev {
   // the blocks run are [block_off, block_off + grid) of a grid of gdim blocks (S2R BID and
   // reports add block_off; S2R GDIM reads gdim)
   uint32_t block_off, gdim;
+  // batched mode: blocks per work item, a multiple of `groups` (a group that finishes its block
+  // claims the item's next one)
+  uint32_t item_blocks;
 };
 constexpr uint32_t kNoDep = 0xFFFFFFFFu;
 
