@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="library default shapes instead of the autotuner")
     ap.add_argument("--tune-cache", default=None, help="JSON file caching tuned shapes per workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--global-check", action="store_true",
+                    help="measure the workload with the global-memory race check on (sr_opts.check_global)")
     ap.add_argument("--no-global-leg", action="store_true",
                     help="skip the global-memory race check leg (measured on the plain reduction)")
     ap.add_argument("--cpu-sample-blocks", type=int, default=0, help="oracle sample (blocks per launch; 0 = auto)")
@@ -367,6 +369,8 @@ def run_native(args):
                                                            "fused_ms": t.fused_ms})
 
     opts, tuning = shapes(mode)
+    if args.global_check:
+        opts["check_global"] = 1
     with ClockSampler(local) as clocks:
         barrier()
         t_wall = time.perf_counter()
@@ -439,7 +443,7 @@ def run_native(args):
     global_leg = None
     if args.workload == "batched" and not args.no_global_leg:
         gprogs = workload("reduction", rank)
-        gopts = {"mode": "plain", "interp_variant": 2, "check_variant": 5, "check_global": 1}
+        gopts = {"mode": "plain", "interp_variant": 2, "check_variant": 6, "check_global": 1}
         gst, gn, gper, gstage = measure(binding, torch, gprogs, gopts, 3, 1, flush, stream)
         ms_g = gstage["global"]
         gbs = 32 * gst.global_records / (ms_g / 1e3) / 1e9 if ms_g > 0 else 0.0

@@ -53,13 +53,15 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
 }
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+// A look-back status word carries its whole payload (flag and count), and nothing else is
+// read on the strength of it, so relaxed GPU-scope accesses suffice.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
   asm volatile("mbarrier.init.shared.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
@@ -206,7 +208,11 @@ __global__ void __launch_bounds__(256) k_ggather(const LaunchDev* launches, uint
 }
 
 // ---------------------------------------------------------------- 2. radix sort
-// Digit histograms of every pass in one read of the records (warp-aggregated shared atomics).
+// Digit histograms of every pass in one read of the records.  Each warp reads UP_ITEMS rows
+// of 32 consecutive records; per pass and row, a digit that all 32 lanes share (the upper
+// digits of nearly sorted input) is counted by one shared atomic, other rows by one atomic
+// per lane.
+constexpr uint32_t UP_ITEMS = 8;
 template <class Rec, class Digit>
 __global__ void __launch_bounds__(RS_T) k_rs_upsweep(const Rec* in, const unsigned long long* n_ptr,
                                                      unsigned long long cap, uint32_t npasses,
@@ -216,16 +222,31 @@ __global__ void __launch_bounds__(RS_T) k_rs_upsweep(const Rec* in, const unsign
   __syncthreads();
   const unsigned long long n = min(*n_ptr, cap);
   const uint32_t lane = threadIdx.x & 31;
-  const unsigned long long stride = (unsigned long long)gridDim.x * RS_T;
-  for (unsigned long long base = (unsigned long long)blockIdx.x * RS_T; base < n; base += stride) {
-    const unsigned long long i = base + threadIdx.x;
-    const bool valid = i < n;
-    Rec r{};
-    if (valid) r = in[i];
+  constexpr uint32_t CHUNK = RS_T * UP_ITEMS;
+  const unsigned long long stride = (unsigned long long)gridDim.x * CHUNK;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * CHUNK + (threadIdx.x >> 5) * (32 * UP_ITEMS);
+       base < n; base += stride) {
+    Rec r[UP_ITEMS];
+#pragma unroll
+    for (uint32_t j = 0; j < UP_ITEMS; ++j) {
+      const unsigned long long i = base + 32u * j + lane;
+      r[j] = i < n ? in[i] : Rec{};
+    }
     for (uint32_t p = 0; p < npasses; ++p) {
-      const uint32_t d = valid ? Digit()(r, p) : 0u;
-      const uint32_t peers = __match_any_sync(FULL, valid ? d : 0x100u | lane);
-      if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[p * RADIX + d], (uint32_t)__popc(peers));
+#pragma unroll
+      for (uint32_t j = 0; j < UP_ITEMS; ++j) {
+        const unsigned long long i0 = base + 32u * j;
+        if (i0 >= n) break;                                  // (warp-uniform)
+        const bool valid = i0 + lane < n;
+        const uint32_t d = Digit()(r[j], p);
+        const uint32_t lo = __reduce_min_sync(FULL, valid ? d : RADIX);
+        const uint32_t hi = __reduce_max_sync(FULL, valid ? d : 0u);
+        if (lo == hi) {
+          if (lane == 0) atomicAdd(&h[p * RADIX + lo], (uint32_t)min(32ull, n - i0));
+        } else if (valid) {
+          atomicAdd(&h[p * RADIX + d], 1u);
+        }
+      }
     }
   }
   __syncthreads();
@@ -255,67 +276,98 @@ __global__ void __launch_bounds__(RADIX) k_rs_bins(unsigned long long* hist, uin
 }
 
 // One pass of the stable LSD radix sort (onesweep): persistent CTAs claim tiles in order from
-// a counter, so every tile's predecessors are claimed by running CTAs and the look-back ends.
+// a counter, so every tile's predecessors are claimed by running CTAs and the look-back ends
+// (a CTA also holds the tile it prefetches, but that one comes after its current tile, so the
+// lowest unfinished tile is always some CTA's current tile).
 // status[tile * RADIX + d] holds ST_AGG | the tile's count of digit d, then ST_INC | the count
 // of digit d in tiles 0..tile (zero: not yet known); it is cleared before every pass.
+// Two tile buffers: while a tile is ranked, placed and written from one, the CTA's next tile
+// streams into the other by a TMA bulk copy.  The tile's records are held in registers after
+// ranking, so it is placed in digit order in its own buffer.
+// (one thread) claim the next tile, and start its copy into `dst` if it exists
+template <class Rec>
+__device__ __forceinline__ void claim_tile(const Rec* in, Rec* dst, unsigned long long n, unsigned long long ntiles,
+                                           uint32_t* tile_ctr, uint32_t* s_tile, unsigned long long* bar) {
+  const uint32_t t = atomicAdd(tile_ctr, 1u);
+  *s_tile = t;
+  if (t < ntiles) {
+    const unsigned long long t0 = (unsigned long long)t * RS_TILE;
+    const uint32_t tn = (uint32_t)min((unsigned long long)RS_TILE, n - t0);
+    // generic-proxy accesses to the buffer (its last write-out) before the async-proxy copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    bulk_load(dst, in + t0, tn * (uint32_t)sizeof(Rec), bar);
+  }
+}
+
 template <class Rec, class Digit>
-__global__ void __launch_bounds__(RS_T) k_rs_pass(const Rec* __restrict__ in, Rec* __restrict__ out,
-                                                  const unsigned long long* n_ptr, unsigned long long cap,
-                                                  uint32_t pass, const unsigned long long* bins,
-                                                  unsigned long long* status, uint32_t* tile_ctr,
-                                                  uint32_t* err, uint32_t spin_limit) {
+__global__ void __launch_bounds__(RS_T, sizeof(Rec) == 16 ? 3 : 1)
+    k_rs_pass(const Rec* __restrict__ in, Rec* __restrict__ out, const unsigned long long* n_ptr,
+              unsigned long long cap, uint32_t pass, const unsigned long long* bins, unsigned long long* status,
+              uint32_t* tile_ctr, uint32_t* err, uint32_t spin_limit) {
   extern __shared__ __align__(16) unsigned char smem[];
-  Rec* stage = reinterpret_cast<Rec*>(smem);                 // the tile as loaded
-  Rec* sorted = stage + RS_TILE;                             // the tile in digit order
-  __shared__ uint32_t whist[RS_WARPS][RADIX];                // per warp and digit: count, then offset
-  __shared__ uint32_t tstart[RADIX];                         // tile-local start of each digit
+  Rec* const buf0 = reinterpret_cast<Rec*>(smem);
+  __shared__ uint16_t whist[RS_WARPS][RADIX];                // per warp and digit: count, then offset
+  __shared__ uint16_t tstart[RADIX];                         // tile-local start of each digit
   __shared__ unsigned long long gdst[RADIX];                 // output index of tile position 0 per digit
   __shared__ uint32_t wsum[RS_WARPS];
-  __shared__ __align__(8) unsigned long long mbar;
-  __shared__ uint32_t s_tile;
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ uint32_t s_tile[2];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
   const unsigned long long n = min(*n_ptr, cap);
   const unsigned long long ntiles = (n + RS_TILE - 1) / RS_TILE;
-  if (tid == 0) mbar_init(&mbar);
+  if (tid == 0) {
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
+    claim_tile(in, buf0, n, ntiles, tile_ctr, &s_tile[0], &mbar[0]);
+  }
   __syncthreads();
-  uint32_t phase = 0;
+  uint32_t cur = 0, phases = 0;                              // bit b: buffer b's mbarrier parity
   for (;;) {
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-    for (uint32_t i = tid; i < RS_WARPS * RADIX; i += RS_T) (&whist[0][0])[i] = 0;
-    __syncthreads();
-    const unsigned long long tile = s_tile;
+    const unsigned long long tile = s_tile[cur];
     if (tile >= ntiles) break;
+    Rec* const stage = buf0 + cur * RS_TILE;
+    if (tid == 0)                                            // the next tile streams in meanwhile
+      claim_tile(in, buf0 + (cur ^ 1u) * RS_TILE, n, ntiles, tile_ctr, &s_tile[cur ^ 1u], &mbar[cur ^ 1u]);
+    for (uint32_t i = tid; i < RS_WARPS * RADIX; i += RS_T) (&whist[0][0])[i] = 0;
     const unsigned long long t0 = tile * RS_TILE;
     const uint32_t tn = (uint32_t)min((unsigned long long)RS_TILE, n - t0);
-    if (tid == 0) bulk_load(stage, in + t0, tn * (uint32_t)sizeof(Rec), &mbar);
-    // the CTA's own copy: bounded independently of spin_limit, drained before giving up
-    const bool ok = !__syncthreads_or(!mbar_wait(&mbar, phase, kCopyWaitLimit));
+    // the CTA's own copies: bounded independently of spin_limit; on a timeout both buffers'
+    // copies are drained before the CTA stops taking tiles
+    const bool ok = !__syncthreads_or(!mbar_wait(&mbar[cur], (phases >> cur) & 1u, kCopyWaitLimit));
     if (!ok) {
       if (tid == 0) atomicOr(err, 1u);
-      const bool drained = !__syncthreads_or(!mbar_wait(&mbar, phase, kCopyWaitLimit));
-      if (!drained) break;          // a copy still owns the buffer: take no further tile
+      __syncthreads_or(!mbar_wait(&mbar[cur], (phases >> cur) & 1u, kCopyWaitLimit));
+      if (s_tile[cur ^ 1u] < ntiles)
+        __syncthreads_or(!mbar_wait(&mbar[cur ^ 1u], (phases >> (cur ^ 1u)) & 1u, kCopyWaitLimit));
+      break;
     }
-    phase ^= 1u;
+    phases ^= 1u << cur;
 
     // rank: warp w takes records [256 w, 256 w + 256) in 8 steps of 32 consecutive records;
     // a group of lanes with one digit adds itself to the warp's count in one step, in lane
     // order, so ranks follow the input order (stability)
-    uint32_t dg[RS_ITEMS], rk[RS_ITEMS];
+    Rec rec[RS_ITEMS];
+    uint32_t pk[RS_ITEMS];                                   // rank in the warp's digit group << 8 | digit
 #pragma unroll
-    for (uint32_t s = 0; s < RS_ITEMS; ++s) {
-      const uint32_t i = w * (RS_ITEMS * 32) + s * 32 + lane;
+    for (uint32_t s2 = 0; s2 < RS_ITEMS; ++s2) {
+      const uint32_t i = w * (RS_ITEMS * 32) + s2 * 32 + lane;
       const bool valid = i < tn;
-      const uint32_t d = valid ? Digit()(stage[i], pass) : 0u;
-      const uint32_t peers = __match_any_sync(FULL, valid ? d : 0x100u | lane);
+      if (valid) rec[s2] = stage[i];
+      const uint32_t d = valid ? Digit()(rec[s2], pass) : 0u;
+      // one digit across the valid lanes (upper digits of nearly sorted input): no match needed
+      const uint32_t lo = __reduce_min_sync(FULL, valid ? d : RADIX);
+      const uint32_t hi = __reduce_max_sync(FULL, valid ? d : 0u);
+      const uint32_t vm = __ballot_sync(FULL, valid);
+      const uint32_t peers = lo == hi ? (valid ? vm : 1u << lane)
+                                      : __match_any_sync(FULL, valid ? d : 0x100u | lane);
       const uint32_t leader = __ffs(peers) - 1;
       uint32_t base = 0;
       if (valid && lane == leader) {
         base = whist[w][d];
-        whist[w][d] = base + __popc(peers);
+        whist[w][d] = (uint16_t)(base + __popc(peers));
       }
       base = __shfl_sync(FULL, base, leader);
-      dg[s] = d;
-      rk[s] = base + __popc(peers & lanemask_lt());
+      pk[s2] = (base + __popc(peers & lanemask_lt())) << 8 | d;
       __syncwarp();
     }
     __syncthreads();
@@ -325,7 +377,7 @@ __global__ void __launch_bounds__(RS_T) k_rs_pass(const Rec* __restrict__ in, Re
 #pragma unroll
     for (uint32_t ww = 0; ww < RS_WARPS; ++ww) {
       const uint32_t c = whist[ww][d];
-      whist[ww][d] = cnt;
+      whist[ww][d] = (uint16_t)cnt;
       cnt += c;
     }
     // tile-local start of each digit: exclusive scan of the counts over the digits
@@ -341,48 +393,64 @@ __global__ void __launch_bounds__(RS_T) k_rs_pass(const Rec* __restrict__ in, Re
     unsigned long long* st = status + tile * RADIX + d;
     unsigned long long excl = 0;
     if (tile == 0) {
-      st_release_u64(st, ST_INC | cnt);
+      st_relaxed_u64(st, ST_INC | cnt);
     } else {
-      st_release_u64(st, ST_AGG | cnt);
-      bool waited_out = false;
-      for (unsigned long long p = tile; p-- > 0;) {
-        const unsigned long long* sp = status + p * RADIX + d;
-        unsigned long long v = ld_acquire_u64(sp);
-        for (uint32_t it = 0; !(v & (ST_AGG | ST_INC)); ++it) {
-          if (it >= spin_limit) {
-            waited_out = true;
-            break;
+      st_relaxed_u64(st, ST_AGG | cnt);
+      // the predecessors' words for digit d, LB tiles at a time (independent loads in flight
+      // together), then summed in order until one whose inclusive prefix is known; a word not
+      // yet published is polled (bounded)
+      constexpr uint32_t LB = 4;
+      bool waited_out = false, found = false;
+      for (unsigned long long top = tile; top > 0 && !found && !waited_out;) {
+        const uint32_t k = (uint32_t)min((unsigned long long)LB, top);
+        unsigned long long v[LB];
+#pragma unroll
+        for (uint32_t q = 0; q < LB; ++q)
+          if (q < k) v[q] = ld_relaxed_u64(status + (top - 1 - q) * RADIX + d);
+#pragma unroll
+        for (uint32_t q = 0; q < LB; ++q) {
+          if (q >= k || found || waited_out) break;
+          const unsigned long long* sp = status + (top - 1 - q) * RADIX + d;
+          unsigned long long y = v[q];
+          for (uint32_t it = 0; !(y & (ST_AGG | ST_INC)); ++it) {
+            if (it >= spin_limit) {
+              waited_out = true;
+              break;
+            }
+            __nanosleep(64);
+            y = ld_relaxed_u64(sp);
           }
-          __nanosleep(64);
-          v = ld_acquire_u64(sp);
+          if (waited_out) break;
+          excl += y & ST_VAL;
+          found = (y & ST_INC) != 0;
         }
-        if (waited_out) break;
-        excl += v & ST_VAL;
-        if (v & ST_INC) break;
+        top -= k;
       }
       if (waited_out) atomicOr(err, 1u);
-      st_release_u64(st, ST_INC | (excl + cnt));
+      st_relaxed_u64(st, ST_INC | (excl + cnt));
     }
     __syncthreads();
     uint32_t before = 0;
     for (uint32_t ww = 0; ww < w; ++ww) before += wsum[ww];
-    tstart[d] = before + x - cnt;
+    tstart[d] = (uint16_t)(before + x - cnt);
     gdst[d] = bins[d] + excl - (before + x - cnt);     // output index = gdst[d] + tile position
     __syncthreads();
-    // the tile in digit order in shared memory, then out: consecutive positions of one digit
-    // go to consecutive output records
+    // the tile in digit order, in its own buffer (every record was read above), then out:
+    // consecutive positions of one digit go to consecutive output records
 #pragma unroll
-    for (uint32_t s = 0; s < RS_ITEMS; ++s) {
-      const uint32_t i = w * (RS_ITEMS * 32) + s * 32 + lane;
-      if (i < tn) sorted[tstart[dg[s]] + whist[w][dg[s]] + rk[s]] = stage[i];
+    for (uint32_t s2 = 0; s2 < RS_ITEMS; ++s2) {
+      const uint32_t i = w * (RS_ITEMS * 32) + s2 * 32 + lane;
+      const uint32_t dd = pk[s2] & 0xFFu;
+      if (i < tn) stage[tstart[dd] + whist[w][dd] + (pk[s2] >> 8)] = rec[s2];
     }
     __syncthreads();
     for (uint32_t i = tid; i < tn; i += RS_T) {
-      const Rec r = sorted[i];
+      const Rec r = stage[i];
       const unsigned long long o = gdst[Digit()(r, pass)] + i;
       if (o < n) out[o] = r;        // (only a look-back that gave up can miss: the error flag is set)
     }
-    __syncthreads();
+    __syncthreads();                 // the buffer is free for the copy issued next iteration
+    cur ^= 1u;
   }
 }
 
