@@ -549,6 +549,12 @@ __global__ void __launch_bounds__(256) k_grun(GrunArgs A) {
       const uint4 q = A.rec[i - 1];
       if (q.x == r0.x && A.launches[find_launch(A, q.w)].prog == prog) continue;   // not a run start
     }
+    // a run of one record holds no pair: nothing to decide
+    if (i + 1 >= n) continue;
+    {
+      const uint4 q = A.rec[i + 1];
+      if (q.x != r0.x || A.launches[find_launch(A, q.w)].prog != prog) continue;
+    }
     const uint32_t word = r0.x;
     const LaunchDev& P0 = A.launches[A.launches[li].first_launch];    // the program's launch 0
     const bool pairs = P0.ord_off != kNoDep;                          // unordered launches exist
