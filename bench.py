@@ -242,7 +242,11 @@ def check_kernel(variant: int) -> str:
 
 
 def measure(binding, torch, progs, opts, steps, warmup, flush, stream):
-    """Time `steps` runs of run_and_check on resident programs (L2 flushed between steps)."""
+    """Time `steps` runs of run_and_check on resident programs (L2 flushed between steps).
+    Every leg starts with PyTorch's cached device blocks released, so that the library's log
+    budget (half the free memory by default) and its waves are the same whichever leg ran
+    before."""
+    torch.cuda.empty_cache()
     ctx = binding.Context(profile=True, use_graph=False, **opts)
     batch = ctx.load_programs(progs)
     for _ in range(max(3, warmup)):
@@ -396,7 +400,7 @@ def run_native(args):
         pst, _, pper, pstage = measure(binding, torch, progs, popts, max(2, args.steps // 2), 1, flush, stream)
         pms = sum(pper) / len(pper)
         plain = {"value": pst.shared_accesses / (pms / 1e3), "ms_per_step": pms, "stage_ms": pstage,
-                 "batched_speedup": pms / (dev_ms / args.steps), "shapes": popts}
+                 "batched_speedup": pms / (dev_ms / args.steps), "shapes": popts, "waves": pst.waves}
 
     # ---- roofline of the whole hot path (HBM): the algorithmic bytes of one step, over the
     # dominant kernel's (the interpreter's) CUDA-event time, against the measured copy bandwidth
@@ -469,6 +473,7 @@ def run_native(args):
     h2d = sum(p.global_init.nbytes + p.code.nbytes for p in progs)
     d2h = 4 * sum((n + 3) & ~3 for n in sizes) + 32 * n_reports
     times = []
+    torch.cuda.empty_cache()
     ctx_e2e = binding.Context(report_cap=max(16, n_reports), **opts)
     for i in range(1 + min(args.steps, 5)):
         barrier()
