@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(RS_T, sizeof(Rec) == 16 ? 3 : 1)
   Rec* const buf0 = reinterpret_cast<Rec*>(smem);
   __shared__ uint16_t whist[RS_WARPS][RADIX];                // per warp and digit: count, then offset
   __shared__ uint16_t tstart[RADIX];                         // tile-local start of each digit
+  __shared__ uint32_t thist[RADIX];                          // the tile's count of each digit
   __shared__ unsigned long long gdst[RADIX];                 // output index of tile position 0 per digit
   __shared__ uint32_t wsum[RS_WARPS];
   __shared__ __align__(8) unsigned long long mbar[2];
@@ -329,6 +330,7 @@ __global__ void __launch_bounds__(RS_T, sizeof(Rec) == 16 ? 3 : 1)
     if (tid == 0)                                            // the next tile streams in meanwhile
       claim_tile(in, buf0 + (cur ^ 1u) * RS_TILE, n, ntiles, tile_ctr, &s_tile[cur ^ 1u], &mbar[cur ^ 1u]);
     for (uint32_t i = tid; i < RS_WARPS * RADIX; i += RS_T) (&whist[0][0])[i] = 0;
+    thist[tid] = 0;                                          // (RS_T == RADIX)
     const unsigned long long t0 = tile * RS_TILE;
     const uint32_t tn = (uint32_t)min((unsigned long long)RS_TILE, n - t0);
     // the CTA's own copies: bounded independently of spin_limit; on a timeout both buffers'
@@ -342,6 +344,27 @@ __global__ void __launch_bounds__(RS_T, sizeof(Rec) == 16 ? 3 : 1)
       break;
     }
     phases ^= 1u << cur;
+
+    // the tile's digit counts, published before the tile is ranked, so that tiles reaching
+    // their look-back meanwhile find them (a warp whose 32 records share a digit adds once);
+    // the look-back itself comes after the ranking, which gives the predecessors time to
+    // publish their inclusive prefixes
+#pragma unroll
+    for (uint32_t s2 = 0; s2 < RS_ITEMS; ++s2) {
+      const uint32_t i = w * (RS_ITEMS * 32) + s2 * 32 + lane;
+      const bool valid = i < tn;
+      const uint32_t dd = valid ? Digit()(stage[i], pass) : 0u;
+      const uint32_t lo = __reduce_min_sync(FULL, valid ? dd : RADIX);
+      const uint32_t hi = __reduce_max_sync(FULL, valid ? dd : 0u);
+      const uint32_t vm = __ballot_sync(FULL, valid);
+      if (lo == hi) {
+        if (lane == 0 && vm) atomicAdd(&thist[lo], (uint32_t)__popc(vm));
+      } else if (valid) {
+        atomicAdd(&thist[dd], 1u);
+      }
+    }
+    __syncthreads();
+    st_relaxed_u64(status + tile * RADIX + tid, (tile == 0 ? ST_INC : ST_AGG) | thist[tid]);   // digit tid
 
     // rank: warp w takes records [256 w, 256 w + 256) in 8 steps of 32 consecutive records;
     // a group of lanes with one digit adds itself to the warp's count in one step, in lane
@@ -388,14 +411,11 @@ __global__ void __launch_bounds__(RS_T, sizeof(Rec) == 16 ? 3 : 1)
       if (lane >= (uint32_t)o) x += y;
     }
     if (lane == 31) wsum[w] = x;
-    // decoupled look-back for digit d: publish this tile's count, add the predecessors'
-    // counts until one whose inclusive prefix is known, publish the inclusive prefix
+    // decoupled look-back for digit d: add the predecessors' counts until one whose inclusive
+    // prefix is known, publish the inclusive prefix
     unsigned long long* st = status + tile * RADIX + d;
     unsigned long long excl = 0;
-    if (tile == 0) {
-      st_relaxed_u64(st, ST_INC | cnt);
-    } else {
-      st_relaxed_u64(st, ST_AGG | cnt);
+    if (tile != 0) {                 // (the tile's count went out before the ranking)
       // the predecessors' words for digit d, LB tiles at a time (independent loads in flight
       // together), then summed in order until one whose inclusive prefix is known; a word not
       // yet published is polled (bounded)
