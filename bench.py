@@ -174,10 +174,11 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle
-def oracle_rate(progs, sample_blocks: int):
-    """Oracle on `sample_blocks` blocks of every launch, all host cores."""
+def oracle_rate(progs, sample_blocks: int, nthreads: int = 0):
+    """Oracle on `sample_blocks` blocks of every launch, on `nthreads` host threads (0 = all
+    cores)."""
     import oracle
-    cores = os.cpu_count() or 1
+    cores = nthreads or os.cpu_count() or 1
     t0 = time.perf_counter()
     r = oracle.run(progs, max_blocks=sample_blocks, nthreads=cores)
     dt = time.perf_counter() - t0
@@ -499,9 +500,14 @@ def run_native(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = args.cpu_sample_blocks or default_sample(args.workload)
         rate, irate, cores, dt, n = oracle_rate(progs, sample)
+        # and on one thread, on a quarter of that sample (the oracle as written, no threads)
+        s1 = max(1, sample // 4)
+        rate1, _, _, dt1, n1 = oracle_rate(progs, s1, nthreads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {sample} blocks of every launch ({n} accesses, {dt:.1f} s)",
-               "thread_instrs_per_s": irate}
+               "thread_instrs_per_s": irate,
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": f"first {s1} blocks of every launch ({n1} accesses, {dt1:.1f} s)"}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
