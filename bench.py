@@ -174,6 +174,10 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle
+# the end-to-end leg splits a batch into this many parts, each on its own context and stream
+E2E_PARTS = 4
+
+
 def oracle_rate(progs, sample_blocks: int, nthreads: int = 0):
     """Oracle on `sample_blocks` blocks of every launch, on `nthreads` host threads (0 = all
     cores)."""
@@ -463,9 +467,9 @@ def run_native(args):
     # ---- end to end through the C ABI from page-locked host buffers, per step: load_programs
     # (code and initial arenas host -> device), run_and_check, fetch_reports and one fetch of
     # every final arena (device -> host).  Timed two ways: the whole batch as one call sequence,
-    # and split in two halves (balanced by reserved log bytes) on two contexts and streams, each
-    # half's uploads, downloads and host work overlapping the other half's kernels - the `e2e`
-    # figure.  Device memory from the contexts' stream-ordered pools (the C ABI default).
+    # and split in E2E_PARTS parts (balanced by reserved log bytes) on as many contexts and
+    # streams, each part's uploads, downloads and host work overlapping the others' kernels -
+    # the `e2e` figure.  Device memory from the contexts' stream-ordered pools (the C ABI default).
     sizes = [p.global_init.size for p in progs]
     pin = torch.empty(max(1, sum(sizes)), dtype=torch.int32, pin_memory=True).numpy()
     progs_pinned, off = [], 0
@@ -509,15 +513,15 @@ def run_native(args):
     t_single = e2e_time([progs_pinned])
     e2e = {"value": all_acc / t_single, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "form": "one batch"}
-    if len(progs_pinned) >= 2:
+    if len(progs_pinned) >= E2E_PARTS:
         from paper_1211_6193_gb300 import dist as sdist
-        halves = [[progs_pinned[i] for i in idx] for idx in sdist.shard(progs, 2)]
+        parts = [[progs_pinned[i] for i in idx] for idx in sdist.shard(progs, E2E_PARTS)]
         torch.cuda.empty_cache()
-        t_pipe = e2e_time(halves)
+        t_pipe = e2e_time(parts)
         e2e = {"value": all_acc / t_pipe, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h),
-               "form": "two half-batches on two streams (copies and host work of one overlap the other's "
-                       "kernels)", "one_batch_value": all_acc / t_single}
+               "form": f"{E2E_PARTS} part-batches on {E2E_PARTS} streams (the copies and host work of each "
+                       "overlap the others' kernels)", "one_batch_value": all_acc / t_single}
     del pin, progs_pinned
 
     cpu = None
