@@ -154,12 +154,6 @@ __device__ __forceinline__ int32_t alu(uint32_t op, int32_t x, int32_t y, bool& 
   }
 }
 
-// The ALU out of line, for the tight loop's rare operations (its body stays small).
-__device__ __noinline__ uint32_t alu_slow(uint32_t o, uint32_t a, uint32_t b) {
-  bool dz = false;
-  return (uint32_t)alu(o, (int32_t)a, (int32_t)b, dz);
-}
-
 // Wait until every other warp of the block has published a clock >= need.  With
 // `order` (store stage), also wait for lower warps whose store of this same round
 // (clock == need) touches an overlapping range of the same memory space.
@@ -521,7 +515,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
       const uint2 ins = ir[p];
       const uint32_t op = ins.x & 0x3Fu;
       if (conv && pk_run(ins.x)) {
-        // Converged warp at a run of plain ALU instructions (the bulk of straight-line code):
+        // Converged warp at a run of MOV / ADD / MUL instructions (the bulk of straight-line code):
         // every runnable lane is at p and the run touches no memory, so its last round can be
         // published at once (other warps wait on a clock only for memory effects), and the
         // run executes in this tight loop, one instruction per round.
@@ -540,9 +534,7 @@ __device__ void run_block(const RunArgs& A, const LaunchDev* Ls, uint32_t block,
           }
           const uint32_t a = lds_u32(rs + pk_a(in.x) * rstride);
           const uint32_t b = pk_imm(in.x) ? in.y : lds_u32(rs + pk_b(in.x) * rstride);
-          // ADD and MUL (the common filler) by selection, the others through the ALU
-          uint32_t r = o == SR_OP_ADD ? a + b : a * b;
-          if (o != SR_OP_ADD && o != SR_OP_MUL) r = alu_slow(o, a, b);
+          const uint32_t r = o == SR_OP_ADD ? a + b : o == SR_OP_MUL ? a * b : b;   // ADD, MUL, MOV
           if (runl && dd != kNoDest) sts_u32(rs + dd * rstride, r);
           ++q;
           if (++i == len) break;

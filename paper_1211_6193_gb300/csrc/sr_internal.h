@@ -12,8 +12,9 @@ namespace sr {
 // run:10, y word: the immediate.  Register fields are rows of the program's compacted
 // register file (only the registers the program uses, plus one zero row last); a destination
 // of kNoDest drops the write (RZ or an opcode without a result).  `run` is the number of
-// consecutive plain ALU instructions (MOV..SNE except DIV and REM, which can fail) starting
-// at this one, at most kRunMax, 0 for any other instruction: such a run touches no memory.
+// consecutive MOV, ADD and MUL instructions starting at this one, at most kRunMax, 0 for any
+// other instruction: such a run touches no memory and needs no ALU dispatch (the interpreter's
+// tight loop selects among the three; every other operation takes the general path).
 constexpr uint32_t kNoDest = 31;
 constexpr uint32_t kRunMax = 1023;
 __host__ __device__ constexpr uint32_t pk_op(uint32_t x) { return x & 0x3Fu; }
@@ -27,7 +28,7 @@ __host__ __device__ constexpr uint32_t pk_make(uint32_t op, uint32_t imm, uint32
   return op | imm << 6 | d << 7 | a << 12 | b << 17 | run << 22;
 }
 __host__ __device__ constexpr bool pk_plain_alu(uint32_t op) {
-  return op >= SR_OP_MOV && op <= SR_OP_SNE && op != SR_OP_DIV && op != SR_OP_REM;
+  return op == SR_OP_MOV || op == SR_OP_ADD || op == SR_OP_MUL;
 }
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kMaxBudget = 1u << 26;  // epochs and rounds stay below 2^26
