@@ -297,9 +297,10 @@ __device__ __forceinline__ void slot_add(uint32_t* sl, unsigned long long r) {
 
 // Exact pass over a racy interval [s, e) of the block whose region is `region` (the
 // consumers are synchronised on entry and on return).  Returns the number of race
-// entries written at region (as 16-byte entries) + race_out.
+// entries written at region (as 16-byte entries) + race_out.  Inlined: as a call, the
+// registers live across the call site were spilled in the main loop.
 template <uint32_t NC>
-__device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t ntab, uint32_t* bm, uint32_t* pre,
+__device__ __forceinline__ uint32_t racy_interval(uint32_t* tab, uint32_t ntab, uint32_t* bm, uint32_t* pre,
                                                uint32_t* wtot, uint4* stage_out, unsigned long long* region,
                                                uint32_t race_out, uint32_t shw, uint32_t tagw, uint32_t epoch,
                                                uint32_t s, uint32_t e) {
@@ -358,7 +359,7 @@ __device__ __noinline__ uint32_t racy_interval(uint32_t* tab, uint32_t ntab, uin
 // address past the shared array there is a corrupt record.  Consumers synchronised on
 // entry and on return.
 template <uint32_t NC>
-__device__ __noinline__ void spill_interval(uint32_t* gtab, uint32_t shw, const unsigned long long* region,
+__device__ __forceinline__ void spill_interval(uint32_t* gtab, uint32_t shw, const unsigned long long* region,
                                             uint32_t s, uint32_t e, uint32_t tagw, uint32_t tag,
                                             volatile uint32_t* racy, bool& bad, bool& g_ready) {
   if (!g_ready) {
