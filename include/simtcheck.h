@@ -178,7 +178,13 @@ typedef struct {
   uint32_t check_races;      /* 1 = log + race check (default), 0 = interpreter + barrier check only */
   uint32_t round_budget;     /* rounds per block before STEP_LIMIT; 0 = 1 << 24 (max 1 << 26) */
   uint32_t mode;             /* SR_MODE_* */
-  uint32_t ctas_per_sm;      /* batched interpreter CTAs per SM; 0 = 1 */
+  uint32_t ctas_per_sm;      /* batched mode: 1 (0) = every launch in the persistent interpreter, one
+                                1024-thread CTA per SM; 2 = the programs whose every launch would take
+                                one group per persistent CTA (blocks of more than 512 threads, or
+                                shared arrays that leave room for one) and whose blocks fit two CTAs
+                                per SM run one simulated block per CTA, two CTAs per SM, all such
+                                launches of a wave in one grid; the other programs stay persistent.
+                                Without effect with fused_check or check_global */
   uint32_t loop_log_records; /* log region (records per block) for kernels with loops; 0 = 65536 */
   uint32_t interp_variant;   /* plain-mode interpreter: 1 = one 1024-thread CTA per SM budget,
                                 2 = registers capped for two per SM, 0 = pick by occupancy */
@@ -223,6 +229,7 @@ typedef struct {
   uint32_t kernels;          /* kernel launches of the library enqueued by the last run */
   float ms_global;           /* last run, when opts.profile: the global-memory race check */
   uint64_t global_records;   /* global accesses logged for the global-memory race check (last run) */
+  uint64_t one_per_cta_blocks; /* batched mode, ctas_per_sm 2: blocks run one per CTA in a run */
 } sr_stats;
 
 /* Create a context on the current CUDA device.  opts may be NULL (defaults). */
@@ -295,8 +302,8 @@ const char* sr_last_error(sr_ctx* ctx);
  * device memory - frameworks that own every byte of the GPU through their own allocator
  * (a second allocator would fight theirs for memory), or processes that forbid cudaMalloc
  * after start-up (allocation can synchronise the device and stall other work).  It is
- * not for use while a CUDA graph is being captured: it copies from host stack memory and
- * synchronises the stream, so on a capturing stream it returns SR_E_INVAL at once and
+ * not for use while a CUDA graph is being captured: it copies from pageable host staging
+ * memory and synchronises the stream, so on a capturing stream it returns SR_E_INVAL at once and
  * leaves the capture untouched.  It runs the whole check of one program (the same kernels
  * as load_programs + run_and_check + fetch_reports, plain mode, default options) and
  * allocates nothing: every intermediate buffer lives in one file-scope __device__ array

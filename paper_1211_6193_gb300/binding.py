@@ -75,7 +75,7 @@ class sr_stats(C.Structure):
                 ("reports", C.c_uint64), ("log_bytes", C.c_uint64), ("blocks", C.c_uint64),
                 ("ms_reset", C.c_float), ("ms_interp", C.c_float), ("ms_check", C.c_float),
                 ("ms_compact", C.c_float), ("waves", C.c_uint32), ("kernels", C.c_uint32),
-                ("ms_global", C.c_float), ("global_records", C.c_uint64)]
+                ("ms_global", C.c_float), ("global_records", C.c_uint64), ("one_per_cta_blocks", C.c_uint64)]
 
 
 EXPORTS = ["sr_create", "sr_destroy", "sr_validate_program", "load_programs", "run_and_check", "fetch_reports",
@@ -211,6 +211,7 @@ class Stats:
     kernels: int
     ms_global: float
     global_records: int
+    one_per_cta_blocks: int
 
 
 class Context:

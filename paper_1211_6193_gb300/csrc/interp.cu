@@ -946,6 +946,32 @@ __device__ __forceinline__ bool deps_dead(const RunArgs& A, const LaunchDev& L) 
   return (L.dep_prev != kNoDep && dead[L.dep_prev]) || (L.dep_wait != kNoDep && dead[L.dep_wait]);
 }
 
+// Thread 0 of a CTA, batched mode: wait (bounded) until every block of the launches L follows
+// (the previous launch of its stream, the one it waits for) has completed - they hold earlier
+// places in the queue, so CTAs that never wait on L's blocks run them - and decide whether L is
+// skipped: a wait that gave up marks the program SR_ST_INTERNAL, and a launch that stopped or
+// was skipped skips L (deps_dead).  A skipped launch is marked in launch_dead.
+__device__ __forceinline__ bool wait_deps(const RunArgs& A, const LaunchDev& L) {
+  bool skip = false;
+  const uint32_t deps[2] = {L.dep_prev, L.dep_wait};
+  for (uint32_t j = 0; j < 2 && !skip; ++j) {
+    if (deps[j] == kNoDep) continue;
+    const uint32_t need = A.launches[deps[j]].grid;
+    bool ok = false;
+    for (uint32_t s = 0; s < A.spin_limit; ++s) {
+      if (ld_acquire_gpu(&A.launch_done[deps[j]]) >= need) { ok = true; break; }
+      __nanosleep(128);
+    }
+    if (!ok) {
+      skip = true;
+      atomicOr(&A.prog_status[L.prog], (uint32_t)SR_ST_INTERNAL);
+    }
+  }
+  if (!skip && deps_dead(A, L)) skip = true;
+  if (skip) atomicOr(&A.launch_dead[L.index], 1u);
+  return skip;
+}
+
 // One CTA per simulated block; one kernel launch per (program, launch), in an order that
 // respects every stream and wait.  MINB = 2 caps registers so that two 1024-thread CTAs fit
 // an SM.
@@ -1000,25 +1026,7 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_batched(RunArgs A) {
     const uint2 it = A.items[item];
     if (threadIdx.x == 0) {
       Ls = A.launches[it.x];
-      uint32_t skip = 0;
-      // wait (bounded) until every block of the launches this one follows has completed;
-      // they are earlier in the queue, so CTAs that never wait on this item hold them
-      const uint32_t deps[2] = {Ls.dep_prev, Ls.dep_wait};
-      for (uint32_t j = 0; j < 2 && !skip; ++j) {
-        if (deps[j] == kNoDep) continue;
-        const uint32_t need = A.launches[deps[j]].grid;
-        bool ok = false;
-        for (uint32_t s = 0; s < A.spin_limit; ++s) {
-          if (ld_acquire_gpu(&A.launch_done[deps[j]]) >= need) { ok = true; break; }
-          __nanosleep(128);
-        }
-        if (!ok) {
-          skip = 1;
-          atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
-        }
-      }
-      if (!skip && deps_dead(A, Ls)) skip = 1;
-      if (skip) atomicOr(&A.launch_dead[Ls.index], 1u);
+      const uint32_t skip = wait_deps(A, Ls) ? 1u : 0u;
       if (!skip) bulk_load(smem, A.code + Ls.code_off, Ls.ir_bytes, &mbar);
       s_skip = skip;
       s_next = Ls.groups;
@@ -1056,6 +1064,63 @@ __global__ void __launch_bounds__(1024, MINB) k_interp_batched(RunArgs A) {
   }
 }
 
+// Batched mode with two CTAs per SM: the programs whose every launch would take one group per
+// persistent CTA (blocks of more than 512 threads, or blocks whose shared memory leaves room for
+// one) run here, one simulated block per 1024-thread CTA and two CTAs per SM, the blocks of all
+// such launches of a wave in one grid - the occupancy of the plain kernel without a launch per
+// (program, launch).  Each CTA takes the next ticket of the wave's queue; tickets follow launch
+// level, then launch index, then block, so the launches a block's launch follows hold smaller
+// tickets, taken by CTAs that are already running, and the CTA waits for them (bounded) as the
+// persistent kernel does.  No loop surrounds the block and its warps are chosen by a warp vote:
+// the block then runs with the plain kernel's register allocation (a persistent loop around it,
+// or a branch the compiler cannot see to be warp-uniform, costs several times its spills).
+__global__ void __launch_bounds__(1024, 2) k_interp_blocks(RunArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ LaunchDev Ls;
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t s_skip, s_block, s_li;
+  if (threadIdx.x == 0) {
+    const uint32_t t = atomicAdd(A.bq_head, 1u);    // one ticket per CTA: t < the grid size
+    // the queue entry holding ticket t: the last one whose first ticket is <= t
+    uint32_t lo = 0, hi = A.bq_n;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (A.bq_first[mid] <= t) lo = mid; else hi = mid;
+    }
+    const uint32_t li = A.bq_launch[lo];
+    Ls = A.launches[li];
+    s_li = li;
+    s_block = t - A.bq_first[lo];
+    bool skip = wait_deps(A, Ls);
+    if (!skip && s_block >= Ls.grid) {              // (a corrupt queue: never from load_programs)
+      skip = true;
+      atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
+    }
+    if (!skip) {
+      mbar_init(&mbar);
+      bulk_load(smem, A.code + Ls.code_off, Ls.ir_bytes, &mbar);
+    }
+    s_skip = skip ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_skip) {
+    bool drained;
+    if (!stage_wait(&mbar, 0, drained)) {
+      if (threadIdx.x == 0) atomicOr(&A.prog_status[Ls.prog], (uint32_t)SR_ST_INTERNAL);
+    } else {
+      const uint32_t nw = (Ls.bdim + 31) >> 5;
+      if (__all_sync(FULL, (threadIdx.x >> 5) < nw))
+        run_block<false, false>(A, &Ls, s_block, reinterpret_cast<const uint2*>(smem), smem + Ls.ir_bytes,
+                                threadIdx.x >> 5, nw, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&A.launch_done[s_li], 1u);
+  }
+}
+
 }  // namespace
 
 uint32_t interp_plain_smem(const LaunchDev& L) {
@@ -1081,7 +1146,11 @@ cudaError_t init_interp_attributes(uint32_t smem_optin) {
   if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<1, false, true>, smem_optin);
   if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_plain<2, false, true>, smem_optin);
   if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<1, false, false>, smem_optin);
-  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<2, false, false>, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_blocks, smem_optin);
+  // (two CTAs of up to half the SM's shared memory each: the largest shared-memory carveout)
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_interp_blocks, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess) e = allow_dynamic_smem(k_interp_batched<1, true, false>, smem_optin);
   return e == cudaSuccess ? allow_dynamic_smem(k_interp_batched<1, false, true>, smem_optin) : e;
 }
@@ -1113,15 +1182,29 @@ cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& 
   return cudaGetLastError();
 }
 
-// two_per_sm: registers capped so that two 1024-thread CTAs share an SM (the default kernel
-// without the fused check or the global log only)
 cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, bool global,
-                                  bool two_per_sm, cudaStream_t s) {
+                                  cudaStream_t s) {
   auto k = global ? k_interp_batched<1, false, true>
-           : fused ? k_interp_batched<1, true, false>
-           : two_per_sm ? k_interp_batched<2, false, false> : k_interp_batched<1, false, false>;
+           : fused ? k_interp_batched<1, true, false> : k_interp_batched<1, false, false>;
   k<<<ctas, 1024, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_interp_blocks(const RunArgs& a, uint32_t nblocks, uint32_t smem, cudaStream_t s) {
+  k_interp_blocks<<<nblocks, 1024, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Two CTAs per SM: each may use half the SM's shared memory, less the 1 KB the hardware reserves
+// per CTA and the kernel's static shared memory.
+uint32_t interp_blocks_smem_cap(uint32_t smem_per_sm) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_interp_blocks) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const uint32_t half = smem_per_sm / 2u, fixed = 1024u + (uint32_t)fa.sharedSizeBytes;
+  return half > fixed ? half - fixed : 0u;
 }
 
 }  // namespace sr

@@ -33,6 +33,8 @@ struct Wave {
   uint32_t li0, li1;      // launch index range
   uint32_t gb0, gb1;      // global block range
   uint32_t item0, item1;  // batched work items
+  uint32_t bq0, bq1;      // batched mode, two CTAs per SM: entries of the block queue
+  uint32_t bq_blocks;     // and the blocks (tickets) they hold
   uint64_t log_records;
   uint64_t glog_records;  // global-memory race check: records of the wave's global logs
   uint32_t addr_bits;     // and the bits of its largest global word address
@@ -48,6 +50,7 @@ struct sr_ctx {
   int device = 0;
   int sms = 0;
   size_t smem_optin = 0;
+  size_t smem_per_sm = 0;
   cudaMemPool_t pool = nullptr;   // without a caller allocator: this context's own memory pool
 };
 
@@ -57,6 +60,12 @@ struct sr_batch {
   std::vector<uint64_t> arena_off, arena_words;
   std::vector<uint2> items;
   std::vector<uint32_t> item_launch;       // race check: launch of every work item
+  // batched mode, two CTAs per SM: the launches run one block per CTA (k_interp_blocks), per
+  // wave in ticket order, and the first ticket of each
+  std::vector<uint8_t> one_per_cta;        // per launch
+  std::vector<uint32_t> bq_launch, bq_first;
+  uint32_t blocks_smem = 0;
+  uint64_t bq_blocks = 0;                  // blocks of all waves run one per CTA
   std::vector<Wave> waves;
   uint32_t nblocks = 0;
   uint32_t check_items = 0;                // race-check work items of all waves
@@ -64,7 +73,8 @@ struct sr_batch {
   uint32_t batched_smem = 0;
   uint64_t total_code = 0, total_arena = 0, log_records = 0;
   DevBuf code, launches_d, arena_init, arena_work, log, blocks, prog_status, launch_dead, counters, items_d,
-      queue_head, launch_done, scratch, work_head, err_flag, offsets, partials, out, total, item_launch_d;
+      queue_head, launch_done, scratch, work_head, err_flag, offsets, partials, out, total, item_launch_d,
+      bq_launch_d, bq_first_d, bq_head;
   uint64_t out_cap = 0;
   // global-memory race check (opts.check_global)
   DevBuf glog, glog_n, goff, gpartials, gtotal, sort_a, sort_b, hist, status, tile_ctr, ord_bits, entries_a, entries_b,
@@ -138,7 +148,8 @@ void free_batch_buffers(sr_ctx* c, sr_batch* b, cudaStream_t s) {
                    &b->launch_done, &b->scratch, &b->work_head, &b->err_flag, &b->offsets, &b->partials,
                    &b->out, &b->total, &b->item_launch_d, &b->glog, &b->glog_n, &b->goff, &b->gpartials,
                    &b->gtotal, &b->sort_a, &b->sort_b, &b->hist, &b->status, &b->tile_ctr, &b->ord_bits,
-                   &b->entries_a, &b->entries_b, &b->gn, &b->gcount, &b->gstart, &b->gn_sorted};
+                   &b->entries_a, &b->entries_b, &b->gn, &b->gcount, &b->gstart, &b->gn_sorted,
+                   &b->bq_launch_d, &b->bq_first_d, &b->bq_head};
   for (DevBuf* d : all) dev_free(c, *d, s);
 }
 
@@ -254,15 +265,24 @@ int enqueue_run(sr_ctx* c, sr_batch* b, cudaStream_t s, bool profile) {
   for (size_t wi = 0; wi < b->waves.size(); ++wi) {
     const Wave& w = b->waves[wi];
     if (o.mode == SR_MODE_BATCHED) {
+      if (w.bq_blocks) {         // (two CTAs per SM) the wave's launches that run one block per CTA
+        ra.bq_launch = (const uint32_t*)b->bq_launch_d.p + w.bq0;
+        ra.bq_first = (const uint32_t*)b->bq_first_d.p + w.bq0;
+        ra.bq_n = w.bq1 - w.bq0;
+        ra.bq_head = (uint32_t*)b->bq_head.p + wi;
+        CUDA_TRY(c, cudaMemsetAsync(ra.bq_head, 0, 4, s));
+        CUDA_TRY(c, sr::launch_interp_blocks(ra, w.bq_blocks, b->blocks_smem, s));
+        b->kernels += 1;
+      }
       ra.items = (const uint2*)b->items_d.p + w.item0;
       ra.nitems = w.item1 - w.item0;
       ra.queue_head = (uint32_t*)b->queue_head.p + wi;
       CUDA_TRY(c, cudaMemsetAsync(ra.queue_head, 0, 4, s));
-      const uint32_t ctas = std::min<uint32_t>(ra.nitems, (uint32_t)c->sms * std::max(1u, o.ctas_per_sm));
+      const uint32_t ctas = std::min<uint32_t>(ra.nitems, (uint32_t)c->sms);
       if (ctas)
         CUDA_TRY(c, sr::launch_interp_batched(ra, ctas, b->batched_smem,
                                               o.fused_check && o.check_races && !o.check_global, o.check_global != 0,
-                                              o.ctas_per_sm >= 2, s));
+                                              s));
       b->kernels += ctas ? 1 : 0;
     } else {
       for (uint32_t li = w.li0; li < w.li1; ++li)
@@ -335,6 +355,9 @@ int sr_create(sr_ctx** out, const sr_opts* opts) {
   int optin = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   c->smem_optin = (size_t)optin;
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
+  c->smem_per_sm = (size_t)per_sm;
   if (e == cudaSuccess) e = sr::init_kernel_attributes((uint32_t)optin);
   if (e == cudaSuccess && !c->custom_alloc) {
     // a pool of its own that keeps freed memory (batch after batch reuses it instead of
@@ -398,9 +421,14 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   b->arena_words.resize(n);
   uint64_t arena_total = 0;
   uint64_t nblocks = 0, check_items = 0;
-  const uint32_t smem_budget = (uint32_t)std::min<size_t>(c->smem_optin ? c->smem_optin : 227 * 1024, 227 * 1024) /
-                                   std::max(1u, o.ctas_per_sm) -
-                               1024;
+  // shared memory of a CTA of the plain or the persistent batched kernel (one per SM)
+  const uint32_t smem_budget =
+      (uint32_t)std::min<size_t>(c->smem_optin ? c->smem_optin : 227 * 1024, 227 * 1024) - 1024;
+  // batched mode with two CTAs per SM: a program whose every launch takes one group per
+  // persistent CTA, and whose blocks fit two CTAs per SM, runs one block per CTA instead
+  const bool hybrid = o.mode == SR_MODE_BATCHED && o.ctas_per_sm >= 2 && !o.fused_check && !o.check_global;
+  const uint32_t blocks_cap =
+      hybrid ? std::min<uint32_t>(smem_budget, sr::interp_blocks_smem_cap((uint32_t)c->smem_per_sm)) : 0u;
   for (uint32_t i = 0; i < n; ++i) {
     const sr_program& P = progs[i];
     code_off[i] = (uint32_t)code.size();
@@ -420,6 +448,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       for (uint32_t k = 0; k < P.nkernels; ++k) kb[k] = bound_kernel(P.code, P.ncode, P.kernel_entry[k], ws);
     }
     const uint32_t first_launch = (uint32_t)b->launches.size();   // the program's launches are contiguous
+    bool one_all = P.nlaunches > 0;            // every launch of the program runs one block per CTA
     // the global-memory race check of a program whose launches are not all ordered needs its
     // launch-order matrix (and all its launches in one wave)
     uint32_t ord_off = sr::kNoDep;
@@ -488,6 +517,7 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
                     d.ir_bytes + d.group_bytes, smem_budget);
       }
       uint32_t g = std::min<uint32_t>(32 / nw, (smem_budget - d.ir_bytes) / d.group_bytes);
+      one_all = one_all && hybrid && g == 1 && d.ir_bytes + d.group_bytes <= blocks_cap;
       if (nw >= 2) g = std::min<uint32_t>(g, 15);
       d.groups = std::max<uint32_t>(1, std::min<uint32_t>(g, d.grid));
       // blocks per work item: up to 8 rounds of `groups` while the launch still makes two
@@ -507,6 +537,9 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       }
       b->launches.push_back(d);
     }
+    // (a program as a whole: the launches a launch follows are of its own program, and each of
+    // the two kernels waits only on launches that it runs itself)
+    b->one_per_cta.resize(b->launches.size(), one_all ? 1 : 0);
   }
   b->nblocks = (uint32_t)nblocks;
   b->check_items = (uint32_t)check_items;
@@ -568,20 +601,35 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   b->glog_records = gwave_max;
   b->entry_cap = std::max<uint64_t>(1024, std::min<uint64_t>(gwave_max, o.report_cap ? o.report_cap : 1u << 20));
 
-  // ---- batched work items: per wave, launch-index order, blocks in chunks of `item_blocks`
+  // ---- batched work items: per wave, launch-index order, blocks in chunks of `item_blocks`;
+  // with two CTAs per SM the launches that run one block per CTA go to the wave's block queue
+  // instead, in the same order
   b->batched_smem = 0;
+  b->blocks_smem = 0;
+  b->bq_blocks = 0;
   for (Wave& w : b->waves) {
     w.item0 = (uint32_t)b->items.size();
+    w.bq0 = (uint32_t)b->bq_launch.size();
+    w.bq_blocks = 0;
     uint32_t maxl = 0;
     for (uint32_t li = w.li0; li < w.li1; ++li) maxl = std::max(maxl, b->launches[li].launch);
     for (uint32_t lv = 0; lv <= maxl; ++lv)
       for (uint32_t li = w.li0; li < w.li1; ++li) {
         const LaunchDev& d = b->launches[li];
-        if (d.launch != lv) continue;
+        if (d.launch != lv || d.grid == 0) continue;
+        if (b->one_per_cta[li]) {
+          b->bq_launch.push_back(li);
+          b->bq_first.push_back(w.bq_blocks);
+          w.bq_blocks += d.grid;
+          b->blocks_smem = std::max(b->blocks_smem, d.ir_bytes + d.group_bytes);
+          continue;
+        }
         for (uint32_t blk = 0; blk < d.grid; blk += d.item_blocks) b->items.push_back(make_uint2(li, blk));
         b->batched_smem = std::max(b->batched_smem, d.ir_bytes + d.groups * d.group_bytes);
       }
     w.item1 = (uint32_t)b->items.size();
+    w.bq1 = (uint32_t)b->bq_launch.size();
+    b->bq_blocks += w.bq_blocks;
   }
   b->check_ctas = (uint32_t)c->sms * sr::check_ctas_per_sm(o.check_variant);
 
@@ -611,6 +659,9 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
       {&b->out, b->out_cap * sizeof(sr_report), "reports"},
       {&b->total, 8, "report total"},
       {&b->item_launch_d, std::max<size_t>(1, b->item_launch.size()) * 4, "check item table"},
+      {&b->bq_launch_d, std::max<size_t>(1, b->bq_launch.size()) * 4, "block queue launches"},
+      {&b->bq_first_d, std::max<size_t>(1, b->bq_first.size()) * 4, "block queue tickets"},
+      {&b->bq_head, (size_t)nwaves * 4, "block queue heads"},
       // global-memory race check (16-byte stand-ins when off)
       {&b->glog, (size_t)b->glog_records * 16, "global logs"},
       {&b->glog_n, o.check_global ? (size_t)b->nblocks * 4 : 0, "global log counts"},
@@ -646,6 +697,8 @@ int load_programs(sr_ctx* c, const sr_program* progs, uint32_t n, void* stream, 
   if (e == cudaSuccess) e = up(b->launches_d, b->launches.data(), nl * sizeof(LaunchDev));
   if (e == cudaSuccess) e = up(b->items_d, b->items.data(), b->items.size() * 8);
   if (e == cudaSuccess) e = up(b->item_launch_d, b->item_launch.data(), b->item_launch.size() * 4);
+  if (e == cudaSuccess) e = up(b->bq_launch_d, b->bq_launch.data(), b->bq_launch.size() * 4);
+  if (e == cudaSuccess) e = up(b->bq_first_d, b->bq_first.data(), b->bq_first.size() * 4);
   if (e == cudaSuccess) e = up(b->ord_bits, b->ord_bits_h.data(), b->ord_bits_h.size() * 4);
   // every arena starts on a 16-byte boundary; the up to three padding words after it are
   // zeroed by copies too, not by a memset: a memset is a kernel, which would wait for SMs that
@@ -809,6 +862,7 @@ int sr_batch_stats(sr_ctx* c, sr_batch* b, sr_stats* out) {
   out->blocks = b->nblocks;
   out->waves = (uint32_t)b->waves.size();
   out->kernels = b->kernels;
+  out->one_per_cta_blocks = b->bq_blocks;
   out->global_records = k.global_records;
   if (c->opts.profile && b->nevents_used >= 2) {
     float ms = 0;

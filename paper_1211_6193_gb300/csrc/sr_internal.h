@@ -128,6 +128,13 @@ struct RunArgs {
   // global-memory race check: per-block global-log regions and per-block record counts
   uint4* glog;
   uint32_t* glog_n;
+  // batched mode, two CTAs per SM: the wave's block queue of the one-block-per-CTA kernel -
+  // its launches in ticket order and the first ticket of each (bq_first[0] = 0), and the
+  // ticket counter
+  const uint32_t* bq_launch;
+  const uint32_t* bq_first;
+  uint32_t bq_n;
+  uint32_t* bq_head;
 };
 
 // Shared-memory footprint of one simulated block in the interpreter.
@@ -185,7 +192,12 @@ cudaError_t launch_interp_plain(const RunArgs& a, uint32_t li, const LaunchDev& 
 // log their accesses in it); global: the instantiation that logs global accesses (launches
 // whose glog_cap is 0 log none in it; it has no fused race check)
 cudaError_t launch_interp_batched(const RunArgs& a, uint32_t ctas, uint32_t smem, bool fused, bool global,
-                                  bool two_per_sm, cudaStream_t s);
+                                  cudaStream_t s);
+// batched mode, two CTAs per SM: one simulated block per 1024-thread CTA for the wave's block
+// queue (a.bq_*), `nblocks` CTAs, `smem` bytes of dynamic shared memory each
+cudaError_t launch_interp_blocks(const RunArgs& a, uint32_t nblocks, uint32_t smem, cudaStream_t s);
+// dynamic shared memory of one CTA of the one-block-per-CTA kernel that still lets two share an SM
+uint32_t interp_blocks_smem_cap(uint32_t smem_optin);
 
 // Global-log record (16 bytes): x = word address in the program's arena, y = epoch (barrier
 // interval of the block), z = tid << 16 | kind << 12 | pc (kind 1 = store, 0 = load),

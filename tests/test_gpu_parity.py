@@ -463,9 +463,41 @@ def test_checker_interval_tags_wrap(B, variant):
 
 
 def test_batched_two_ctas_per_sm(B):
-    """The batched interpreter capped for two 1024-thread CTAs per SM (ctas_per_sm 2) gives the
-    same results."""
+    """Batched mode with two CTAs per SM (ctas_per_sm 2): the programs of large blocks run one
+    block per CTA, the others in the persistent kernel - both kernels in one run, the stencil's
+    four dependent launches in the first - with the same results."""
     progs = families.batch(n_programs=48, seed=3, max_grid=6, bug_rate=0.5)
     progs += [stencil2d.program(log2w=7, steps=4, buggy_launch=2, seed=4)]
-    assert_parity(B, progs, "batched", ctas_per_sm=2)
-    assert_parity(B, progs, "batched", ctas_per_sm=2, use_graph=True)
+    got, _ = assert_parity(B, progs, "batched", ctas_per_sm=2)
+    assert 0 < got.stats.one_per_cta_blocks < got.stats.blocks, got.stats
+    got, _ = assert_parity(B, progs, "batched", ctas_per_sm=2, use_graph=True)
+    assert 0 < got.stats.one_per_cta_blocks < got.stats.blocks
+    one, _ = assert_parity(B, progs, "batched", ctas_per_sm=1)
+    assert one.stats.one_per_cta_blocks == 0
+
+
+def _wide_stream_programs(seed, count, bdim=1024):
+    """The seeded stream programs with blocks of `bdim` threads; launch l's words move to
+    [bdim l, bdim (l + 1)), so that unordered launches still share none."""
+    import stream_programs as sp
+    out = []
+    for p in sp.random_programs(seed, count):
+        ls = []
+        for l in p.launches:
+            pr = tuple(l.params)
+            if l.kernel == sp.WRITE:
+                pr = (pr[0] // 4 * bdim, pr[1])
+            elif l.kernel == sp.COPY:
+                pr = (pr[0] // 4 * bdim, pr[1] // 4 * bdim)
+            ls.append(ir.Launch(l.kernel, 1, bdim, 0, pr, stream=l.stream, wait=l.wait))
+        out.append(ir.Program(p.code, p.kernel_entry, ls, np.full(bdim * len(ls), -1, np.int32),
+                              name=p.name + f"_b{bdim}"))
+    return out
+
+
+def test_one_block_per_cta_streams_and_deadlocks(B):
+    """Streams, event waits and deadlocking launches in the one-block-per-CTA kernel: its CTAs
+    wait (bounded) for the launches their launch follows and skip what a stop skips."""
+    progs = _wide_stream_programs(11, 24)
+    got, _ = assert_parity(B, progs, "batched", ctas_per_sm=2)
+    assert got.stats.one_per_cta_blocks == got.stats.blocks == sum(len(p.launches) for p in progs)
