@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
     ap.add_argument("--interp-variant", type=int, default=0, choices=[0, 1, 2],
                     help="plain interpreter kernel: 1 = one CTA/SM register budget, 2 = two CTAs/SM, 0 = auto")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, choices=[0, 1, 2],
+                    help="batched mode: 1 = every launch in the persistent interpreter (one CTA per SM), 2 = "
+                         "programs of one-group blocks one block per CTA, two CTAs per SM (0 = autotuner)")
     ap.add_argument("--check-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7],
                     help="race-check kernel shape (0 = default); setting a shape flag skips the autotuner")
     ap.add_argument("--fused-check", action="store_true",
@@ -367,8 +370,10 @@ def run_native(args):
 
     def shapes(m):
         """Kernel shapes for mode m: fixed by the flags, else picked by the autotuner (untimed)."""
-        if args.interp_variant or args.check_variant or args.no_tune or args.fused_check:
+        if args.interp_variant or args.check_variant or args.ctas_per_sm or args.no_tune or args.fused_check:
             o = {"mode": m, "interp_variant": args.interp_variant, "check_variant": args.check_variant}
+            if args.ctas_per_sm:
+                o["ctas_per_sm"] = args.ctas_per_sm
             if args.fused_check:
                 o["fused_check"] = 1
             return o, "flags"
@@ -413,7 +418,10 @@ def run_native(args):
     alg = {"checked_shared_access": 16, "simulated_global_access": 4, "report": 32, "arena_word": 8}
     step_bytes = (alg["checked_shared_access"] * st.shared_accesses + alg["simulated_global_access"] *
                   st.global_accesses + alg["report"] * n_reports + alg["arena_word"] * arena_words)
-    interp_kernel = "k_interp_plain" if mode == "plain" else "k_interp_batched"
+    # (batched mode with two CTAs per SM: the interpreter stage is two kernels, the one-block-per-CTA
+    # grid of the programs of one-group blocks, then the persistent kernel for the rest)
+    interp_kernel = ("k_interp_plain" if mode == "plain" else
+                     "k_interp_blocks + k_interp_batched" if opts.get("ctas_per_sm") == 2 else "k_interp_batched")
     achieved = step_bytes / (stage["interp"] / 1e3) / 1e9
     isha, csha = src_sha("interp.cu", "sr_internal.h"), src_sha("check.cu", "sr_internal.h")
     fused = bool(opts.get("fused_check"))

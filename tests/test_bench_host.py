@@ -13,7 +13,8 @@ def test_committed_traffic_file_is_well_formed():
     assert t["captures"]
     for c in t["captures"]:
         assert c["workload"] in bench.WORKLOADS
-        assert c["kernel"] in ("k_interp_plain", "k_interp_batched", "k_check", "k_check_reg", "k_check_lean")
+        assert c["kernel"] in ("k_interp_plain", "k_interp_batched", "k_interp_blocks + k_interp_batched", "k_check",
+                               "k_check_reg", "k_check_lean")
         assert c["unit"] in ("block", "record") and c["units"] > 0
         assert c["dram_read"] > 0 and c["dram_write"] >= 0
         assert "--clock-control none" in c["command"] and len(c["src_sha1"]) == 16
