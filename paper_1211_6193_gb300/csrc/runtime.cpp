@@ -4,9 +4,10 @@
 //                fields remapped so RZ and unused operands read the zero row), bounds
 //                every launch's per-block access log statically, groups launches into
 //                waves whose logs fit the log budget, and uploads everything.
-// run_and_check  per wave: interpreter (one launch per (program, launch) in plain mode,
-//                one persistent launch in batched mode), race check, report scan and
-//                emission.  Everything is enqueued on the caller's stream.
+// run_and_check  per wave: interpreter (one launch per (program, launch) in plain mode;
+//                in batched mode one persistent launch, preceded with two CTAs per SM by
+//                one grid of the programs that run one block per CTA), race check, report
+//                scan and emission.  Everything is enqueued on the caller's stream.
 // fetch_*        synchronise the stream and copy results to the host.
 #include <algorithm>
 #include <cstdarg>
